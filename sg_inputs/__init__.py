@@ -1,0 +1,131 @@
+"""Seeded synthetic instance generators shared by the tests, the bench and the smoke run.
+
+This module only draws random *data*: graphs, coupling bit-planes, coupling matrices and
+size lists.  It holds none of the simulation method's arithmetic (no colouring, no Metropolis
+rule, no random numbers drawn by the dynamics, no measurement), so both the CPU oracle and the
+CUDA path can consume its output without sharing any method code.
+
+Instance families (paper workloads, restated):
+  * Viana-Bray on a Poissonian random graph with mean degree c, J = +-1 equiprobable
+    (Eq. 3; the paper itself uses a random regular graph of degree 4).  Couplings are stored
+    as 64-bit lane words: bit k = 1 means J = -1 for disorder sample k (SI section 2,
+    multispin coding, Table 1 caption: 64 coupling sets per graph).
+  * Random regular graph of degree z (the paper's own ensemble, main text after Eq. 3).
+  * Sherrington-Kirkpatrick with binary symmetric couplings J_ij = +-1, J_ii = 0
+    (SI section 1; the 1/sqrt(N) scale is folded into the inverse temperature).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "poisson_graph",
+    "regular_graph",
+    "vb_lane_couplings",
+    "sk_couplings",
+    "log_uniform_sizes",
+    "csr_from_edges",
+]
+
+
+def csr_from_edges(n: int, ei: np.ndarray, ej: np.ndarray):
+    """Symmetric CSR (row_ptr int32[n+1], col int32[2M]) of an undirected simple edge list.
+
+    Each row's neighbours are sorted ascending.  Also returns, for every directed entry, the
+    index of its undirected edge (int64[2M]) so that per-edge data can be mirrored.
+    """
+    ei = np.asarray(ei, dtype=np.int64)
+    ej = np.asarray(ej, dtype=np.int64)
+    m = ei.size
+    src = np.concatenate([ei, ej])
+    dst = np.concatenate([ej, ei])
+    eid = np.concatenate([np.arange(m), np.arange(m)])
+    order = np.lexsort((dst, src))
+    src, dst, eid = src[order], dst[order], eid[order]
+    counts = np.bincount(src, minlength=n)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    if row_ptr[-1] >= 2**31:
+        raise ValueError("too many edges for int32 CSR")
+    return row_ptr.astype(np.int32), dst.astype(np.int32), eid
+
+
+def poisson_graph(n: int, c: float, seed: int):
+    """Erdos-Renyi G(N, M) graph with M = round(c*N/2) distinct edges, no self-loops.
+
+    The degree distribution is Poisson(c) for large N (the Viana-Bray ensemble).  Returns
+    (row_ptr, col, edge_id) as in csr_from_edges.
+    """
+    if n < 2:
+        raise ValueError("need N >= 2")
+    m = int(round(c * n / 2.0))
+    maxm = n * (n - 1) // 2
+    if m > maxm:
+        raise ValueError("too many edges requested")
+    rng = np.random.default_rng(np.random.SeedSequence([0x5EED_0001, seed]))
+    keys = np.empty(0, dtype=np.int64)
+    while keys.size < m:
+        need = m - keys.size
+        k = max(need + need // 8 + 16, 64)
+        a = rng.integers(0, n, size=k, dtype=np.int64)
+        b = rng.integers(0, n, size=k, dtype=np.int64)
+        ok = a != b
+        a, b = a[ok], b[ok]
+        lo, hi = np.minimum(a, b), np.maximum(a, b)
+        new = lo * n + hi
+        # keep the first occurrence of each new key, in draw order, then drop known ones
+        _, first = np.unique(new, return_index=True)
+        new = new[np.sort(first)]
+        new = new[~np.isin(new, keys)]
+        keys = np.concatenate([keys, new[:need]])
+    ei, ej = keys // n, keys % n
+    return csr_from_edges(n, ei, ej)
+
+
+def regular_graph(n: int, z: int, seed: int, max_tries: int = 200):
+    """Random z-regular simple graph by the configuration model with rejection of bad pairings.
+
+    Stub pairings that produce a self-loop or a multi-edge are redrawn as a whole; the
+    accepted graph is uniform over simple z-regular graphs.  Intended for small-to-moderate N.
+    """
+    if (n * z) % 2:
+        raise ValueError("N*z must be even")
+    rng = np.random.default_rng(np.random.SeedSequence([0x5EED_0002, seed]))
+    stubs = np.repeat(np.arange(n, dtype=np.int64), z)
+    for _ in range(max_tries):
+        perm = rng.permutation(stubs)
+        a, b = perm[0::2], perm[1::2]
+        if np.any(a == b):
+            continue
+        lo, hi = np.minimum(a, b), np.maximum(a, b)
+        keys = lo * n + hi
+        if np.unique(keys).size != keys.size:
+            continue
+        return csr_from_edges(n, lo, hi)
+    raise RuntimeError("could not draw a simple regular graph; raise max_tries")
+
+
+def vb_lane_couplings(edge_id: np.ndarray, n_edges: int, seed: int) -> np.ndarray:
+    """+-1 couplings for 64 disorder samples per edge, as one uint64 word per directed entry.
+
+    Bit k of the word is 1 when J_ij = -1 in sample k; both directions of an edge carry the
+    same word (J is symmetric).
+    """
+    rng = np.random.default_rng(np.random.SeedSequence([0x5EED_0003, seed]))
+    words = rng.integers(0, 2**64, size=n_edges, dtype=np.uint64, endpoint=False)
+    return words[np.asarray(edge_id, dtype=np.int64)]
+
+
+def sk_couplings(n: int, seed: int) -> np.ndarray:
+    """Dense symmetric +-1 coupling matrix (int8, row-major N x N) with a zero diagonal."""
+    rng = np.random.default_rng(np.random.SeedSequence([0x5EED_0004, seed]))
+    bits = rng.integers(0, 2, size=(n, n), dtype=np.int8)
+    upper = np.triu(1 - 2 * bits, k=1).astype(np.int8)
+    return (upper + upper.T).astype(np.int8)
+
+
+def log_uniform_sizes(count: int, lo_exp: float, hi_exp: float, seed: int) -> np.ndarray:
+    """count sizes N = round(2**U) with U ~ Uniform[lo_exp, hi_exp] (uneven-batch workloads)."""
+    rng = np.random.default_rng(np.random.SeedSequence([0x5EED_0005, seed]))
+    u = rng.uniform(lo_exp, hi_exp, size=count)
+    return np.round(2.0 ** u).astype(np.int64)

@@ -1,0 +1,62 @@
+"""The oracle's pins are sensitive: plant plausible mistakes in a copy of the oracle (on the CPU)
+and check that the brute-force and limit pins reject every one of them."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import sg_inputs
+from test_oracle_sk import brute_sk
+from test_oracle_vb import brute_vb, unpack
+
+VB_MUTATIONS = {
+    "zero_move_rejected": ("int flip = (m <= 0) || (r32 < th[m]);", "int flip = (m < 0) || (m > 0 && r32 < th[m]);"),
+    "wrong_sign_of_field": ("int32_t m = sl[i] * field;", "int32_t m = -sl[i] * field;"),
+    "missing_factor_two": ("thr[m] = threshold_from_exponent(-2.0 * beta * m);",
+                           "thr[m] = threshold_from_exponent(-1.0 * beta * m);"),
+    "coupling_ignored": ("field += J * sl[col[e]];", "field += sl[col[e]];"),
+    "rng_word_shared": ("(uint32_t)(r / 4), 0, r % 4);", "(uint32_t)(r / 4), 0, 0);"),
+    "sweep_not_in_counter": ("draw_word(seed, (uint32_t)i, t,", "draw_word(seed, (uint32_t)i, 0,"),
+    "colour_order_reversed": ("for (int32_t c = 0; c < ncol; ++c)", "for (int32_t c = ncol - 1; c >= 0; --c)"),
+    "lane_init_high_word_dropped": ("| ((uint64_t)draw_word(seed, (uint32_t)i, 0, (uint32_t)r, 1, 1) << 32);", ";"),
+}
+
+SK_MUTATIONS = {
+    "field_update_wrong_sign": ("hr[j] += 2 * (int32_t)J[(size_t)j * N + i] * sr[i];",
+                                "hr[j] -= 2 * (int32_t)J[(size_t)j * N + i] * sr[i];"),
+    "field_update_no_factor_two": ("hr[j] += 2 * (int32_t)J[(size_t)j * N + i] * sr[i];",
+                                   "hr[j] += (int32_t)J[(size_t)j * N + i] * sr[i];"),
+    "no_sqrt_n_scale": ("thr[k] = threshold_from_exponent(-(2.0 * beta * k) / sqrt((double)N));",
+                        "thr[k] = threshold_from_exponent(-(2.0 * beta * k));"),
+    "transposed_coupling_in_field": ("acc += (int32_t)J[(size_t)i * N + j] * s[(size_t)rl * N + j];",
+                                     "acc += (int32_t)J[(size_t)j * N + i] * s[(size_t)rl * N + i];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(VB_MUTATIONS))
+def test_vb_pins_catch_planted_mistake(name, tmp_path):
+    old, new = VB_MUTATIONS[name]
+    src = oracle.source()
+    assert src.count(old) >= 1, name
+    variant = oracle.compile_variant(src.replace(old, new), str(tmp_path))
+    rp, col, eid = sg_inputs.poisson_graph(9, 3.0, 11)
+    jb = sg_inputs.vb_lane_couplings(eid, eid.max() + 1, 11)
+    temps, L, sweeps = [0.7, 1.0, 2.0, 0.45, 1.3], 64, 5
+    res = variant.vb_run(rp, col, jb, L, temps, 99, sweeps, trajectory=True)
+    want = brute_vb(rp, col, jb, L, temps, 99, sweeps)
+    got = np.array([[unpack(res["traj"][t, r], L) for r in range(len(temps))]
+                    for t in range(sweeps + 1)])
+    assert not np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("name", sorted(SK_MUTATIONS))
+def test_sk_pins_catch_planted_mistake(name, tmp_path):
+    old, new = SK_MUTATIONS[name]
+    src = oracle.source()
+    assert src.count(old) >= 1, name
+    variant = oracle.compile_variant(src.replace(old, new), str(tmp_path))
+    n, temps = 10, [0.4, 0.6, 1.0, 2.0, 0.5, 0.4]
+    J = sg_inputs.sk_couplings(n, 77 + n)
+    res = variant.sk_run(J, temps, 3, 5, trajectory=True)
+    assert not np.array_equal(res["traj"], brute_sk(J, temps, 3, 5))
