@@ -1,0 +1,374 @@
+#!/usr/bin/env python3
+"""Throughput of the Viana-Bray bit-packed Metropolis sweep on GB300, in spin updates per ns.
+
+Workload (one "step" = one sweep of both temperature instances, measurements included when the
+schedule falls inside the timed window):
+  Poissonian random graph, N = 2^22, mean degree c = 4, J = +-1, 64 disorder samples packed per
+  uint64 lane word, two replicas, temperatures T = 1.0 and T = 0.6 (two instances on the same
+  graph and couplings), snapshots at t_w = 2^4..2^15 and measurements of C(t_w, t_w + 2^k), q, E
+  on the log schedule up to 2^16 sweeps.  Spin updates per step = 2 * N * 64 * 2.
+
+Under torchrun (N > 1 GPUs) every rank runs its own independent instance (its own graph seed):
+weak scaling with no collective on the data path; rank 0 prints the one JSON line.
+
+--impl reference times the plain CPU oracle (single thread) on a bounded sample of the same
+workload instead (the test oracle as it stands).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import sg_inputs  # noqa: E402
+
+N_VERTS = 1 << 22
+MEAN_DEGREE = 4.0
+LANES = 64
+REPLICAS = 2
+TEMPS = (1.0, 0.6)
+T_MAX = 1 << 16
+TW = [1 << k for k in range(4, 16)]
+WORKLOAD = "vb_packed_poisson_c4_N4194304_lanes64_R2_T1.0+0.6"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def instance(rank: int):
+    rp, col, eid = sg_inputs.poisson_graph(N_VERTS, MEAN_DEGREE, 2 + 1000 * rank)
+    jb = sg_inputs.vb_lane_couplings(eid, eid.max() + 1, 2 + 1000 * rank)
+    return rp, col, jb
+
+
+def algorithmic_bytes_per_sweep(n, n_entries_directed, R):
+    """vinfo 4 B/vertex + (col 4 B + J 8 B) per directed entry + own R words read and written."""
+    return 4 * n + 12 * n_entries_directed + 16 * n * R
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("vb_kernels.cu", "sg_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1906_11195_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per sweep of the colour kernel from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "vb_packed_colour_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("source_sha") != kernel_source_hash():
+        return None
+    return float(d["dram_bytes_per_sweep"])
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 7:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[3:7]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline_sample(rp, col, jb, budget_lanes=16):
+    """The CPU oracle (single thread) on one sweep of the same graph at T = 1.0, R = 2."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.vb_run(rp, col, jb, budget_lanes, [TEMPS[0]] * REPLICAS, 1, 1)
+    dt = time.perf_counter() - t0
+    updates = N_VERTS * budget_lanes * REPLICAS
+    return {"value": updates / (dt * 1e9), "unit": "spin updates/ns", "cores": 1, "kind": "oracle",
+            "sample": f"1 sweep of the N=2^22 graph at T=1.0, {budget_lanes} lanes x {REPLICAS} "
+                      f"replicas ({updates} spin updates, {dt:.1f} s, initial draw included)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    rp, col, jb = instance(0)
+    # each step: one oracle sweep of the full graph at T = 1.0, R = 2, with a lane count sized so
+    # that warm-up + timed steps stay within about three minutes
+    per_update_ns = 1.0 / 0.0115
+    budget_s = min(4.0, 170.0 / max(1, args.steps + args.warmup))
+    lanes = int(max(1, min(64, budget_s * 1e9 / per_update_ns / (N_VERTS * REPLICAS))))
+    for _ in range(args.warmup):
+        oracle.vb_run(rp, col, jb, lanes, [TEMPS[0]] * REPLICAS, 1, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.vb_run(rp, col, jb, lanes, [TEMPS[0]] * REPLICAS, 1, 1)
+    dt = time.perf_counter() - t0
+    updates = args.steps * N_VERTS * lanes * REPLICAS
+    value = updates / (dt * 1e9)
+    line = {
+        "impl": "reference", "metric": "spin updates/ns", "value": value, "unit": "spin updates/ns",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"1 sweep, {lanes} lanes, T=1.0, R=2 per step"},
+        "cpu_baseline": {"value": value, "unit": "spin updates/ns", "cores": 1, "kind": "oracle",
+                         "sample": f"per step: 1 sweep of the N=2^22 graph, {lanes} lanes x 2 replicas"},
+        "e2e": {"value": value, "unit": "spin updates/ns", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_1906_11195_gb300 as sg
+    from paper_1906_11195_gb300 import _build
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        _build.build()
+    if ws > 1:
+        dist.barrier()
+    _build.build()
+
+    rp, col, jb = instance(rank)
+    tw, tm = sg_inputs.log_schedule(TW, T_MAX)
+    graphs = [dict(row_ptr=rp, col=col, jbits=jb, seed=1 + rank, temps=[T] * REPLICAS) for T in TEMPS]
+    stream = torch.cuda.current_stream(dev)
+
+    runs = [sg.VBRun([g], n_lanes=LANES, n_replicas=REPLICAS, kernel=sg.SG_VB_PACKED, tw=tw, tm=tm,
+                     device=dev, stream=stream) for g in graphs]
+    for r in runs:
+        r.sweep(args.warmup)
+    torch.cuda.synchronize()
+    launches0 = sum(r.launches for r in runs)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for r in runs:
+        r.sweep(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    launches = sum(r.launches for r in runs) - launches0
+    for r in runs:
+        r.synchronize()
+    if ws > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    updates_per_step = len(TEMPS) * N_VERTS * LANES * REPLICAS
+    value = ws * updates_per_step * args.steps / (ms * 1e6)
+    for r in runs:
+        r.close()
+
+    # roofline of the colour kernel: a handle with no measurement schedule times pure sweeps
+    kr = max(20, min(args.steps, 200))
+    rl = sg.VBRun([graphs[0]], n_lanes=LANES, n_replicas=REPLICAS, kernel=sg.SG_VB_PACKED,
+                  device=dev, stream=stream)
+    rl.sweep(3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rl.sweep(kr)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sweep_ms = e0.elapsed_time(e1) / kr
+    rl.close()
+    bytes_sweep = algorithmic_bytes_per_sweep(N_VERTS, int(rp[-1]), REPLICAS)
+    peak, peak_kind = peaks()
+    achieved = bytes_sweep / (sweep_ms * 1e-3) / 1e9
+    traffic = recorded_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                "kernel": "k_vb_packed_colour<2> (one sweep = all colour classes)",
+                "algorithmic_bytes_per_sweep": bytes_sweep, "ms_per_sweep": sweep_ms}
+
+    # the plain one-thread-per-(vertex, lane, replica) kernel on the same graph, T = 1.0
+    plain = None
+    if not args.skip_plain:
+        pr = sg.VBRun([graphs[0]], n_lanes=LANES, n_replicas=REPLICAS, kernel=sg.SG_VB_PLAIN,
+                      device=dev, stream=stream)
+        pr.sweep(1)
+        torch.cuda.synchronize()
+        kp = 3
+        e0.record(stream)
+        pr.sweep(kp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / kp
+        pr.close()
+        plain = {"value": N_VERTS * LANES * REPLICAS / (pms * 1e6), "unit": "spin updates/ns",
+                 "ms_per_sweep": pms, "sweeps": kp}
+
+    # end to end through the public API: H2D of the prepared instances, K sweeps each, D2H of
+    # the measurement counts; host-side instance preparation (validation, colouring, layout)
+    # happens before the timed region
+    handles, bufs = [], []
+    for g in graphs:
+        h = sg.sg_create_vb([g], LANES, REPLICAS, sg.SG_VB_PACKED, tw, tm)
+        nb = sg.sg_workspace_bytes(h)
+        handles.append((h, nb))
+        bufs.append(torch.empty(nb, dtype=torch.uint8, device=dev))
+    h2d = sum(nb for _, nb in handles)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for (h, nb), buf in zip(handles, bufs):
+        sg.sg_attach(h, buf.data_ptr(), nb, stream.cuda_stream)
+    for h, _ in handles:
+        sg.sg_sweep(h, args.warmup + args.steps)
+    d2h = 0
+    for h, _ in handles:
+        C, q, E = sg.sg_read_results(h)
+        d2h += C.nbytes + q.nbytes + E.nbytes
+    e2e_s = time.perf_counter() - t0
+    for h, _ in handles:
+        sg.sg_destroy(h)
+    e2e_steps = args.warmup + args.steps
+    e2e = {"value": ws * updates_per_step * e2e_steps / (e2e_s * 1e9), "unit": "spin updates/ns",
+           "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
+           "note": "H2D of the device image of both instances + sweeps + D2H of all counts, "
+                   "bytes spread over the steps"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        cpu = cpu_baseline_sample(rp, col, jb)
+
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "spin updates/ns", "value": value, "unit": "spin updates/ns", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N_VERTS, "mean_degree": MEAN_DEGREE, "lanes": LANES,
+                   "replicas": REPLICAS, "temps": list(TEMPS), "step": "1 sweep of each temperature",
+                   "schedule": f"tw=2^4..2^15, log-spaced measurements to 2^16 ({len(tm)} times)",
+                   "l2": "inputs larger than L2: 201 MB of graph streamed per sweep (spins, 64 MiB, "
+                         "are meant to stay in L2)",
+                   "parallelism": f"replicas only, {ws} independent instance(s)"},
+        "roofline": roofline,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "plain_kernel": plain,
+        "speedup_vs_plain": (value / ws) / plain["value"] if plain else None,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("warning: fewer than 3 warm-up steps")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,181 @@
+/*
+ * sg.h -- C ABI of libsg, a GB300 (sm_103a) library for Metropolis aging dynamics of mean-field
+ * spin glasses after a quench (arXiv:1906.11195, "Strong ergodicity breaking in aging of mean
+ * field spin glasses").
+ *
+ * Models
+ *   Viana-Bray (VB):  H = -sum_{(ij) in E} J_ij s_i s_j on a sparse graph, J_ij = +-1 (Eq. 3).
+ *                     64 disorder samples ("lanes") share one graph, each with its own couplings
+ *                     and initial spins, packed one bit per lane in 64-bit words (multispin
+ *                     coding, SI section 2 and the caption of Table 1).
+ *   Sherrington-Kirkpatrick (SK): H = -sum_{i<j} J_ij s_i s_j / sqrt(N), J_ij = +-1 (Eq. 1 with
+ *                     the binary couplings of SI section 1).  R replicas share J.
+ * Dynamics: single-spin-flip Metropolis at fixed temperature from a random start (Methods; SI
+ * sections 1-2).  Time unit = one sweep (every spin visited once).  VB visits one graph colour
+ * class at a time (the independent-set update of SI section 3, generalised from the bipartite
+ * halves to a greedy colouring); SK visits i = 0..N-1 in order (SI section 1, "fixed order").
+ * Observables (integer counts; divide by N): two-time correlation C(t_w+t, t_w) = sum_i
+ * s_i(t_w+t) s_i(t_w) (the definition after Eq. 1 and Eq. formula1), the overlap of replica
+ * pairs (2p, 2p+1) (the "two clones" of SI section 1), and the energy.
+ *
+ * Random numbers (the paper names none): Philox4x32-10, key = (seed_lo, seed_hi).
+ *   update draw of replica r, sweep t (0-based), vertex i: word (r mod 4) of counter (i, t, r/4, 0)
+ *   initial spins of replica r, vertex i: lane bits = w0 | w1 << 32 of counter (i, 0, r, 1),
+ *   bit = 1 means s = -1 (SK uses lane bit 0).  One draw is shared by the 64 lanes of a word.
+ * Acceptance: flip iff dE <= 0 or r32 < thr(dE), thr = min(2^32-1, floor(2^32 exp(-dE/T))) in
+ * double precision; VB dE = 2m with m = s_i sum_j J_ij s_j, thr[m] = f(-2.0*beta*m);
+ * SK dE = 2k/sqrt(N), thr[k] = f(-(2.0*beta*k)/sqrt((double)N)), beta = 1.0/T.
+ * Results are bit-exact functions of (instance, temperatures, seed, schedule): the kernel choice,
+ * block size and launch shapes never change them.
+ *
+ * Memory and ownership
+ *   - Host arrays passed to sg_create_* are read during the call only; the caller keeps them.
+ *   - The library allocates no device memory.  The caller allocates one device workspace of
+ *     sg_workspace_bytes() bytes (e.g. a PyTorch uint8 tensor) and lends it through sg_attach()
+ *     until sg_destroy(); it must be 256-byte aligned.
+ *   - The CUDA stream given to sg_attach() is borrowed; all device work of the handle is queued
+ *     on it.  Calls on one handle must not overlap from several host threads.
+ * Errors: every call returns SG_OK (0) or a negative code; sg_last_error() gives a message for
+ * the calling thread.  No C++ exception crosses this interface.
+ */
+#ifndef SG_H
+#define SG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SG_OK 0
+#define SG_EINVAL (-1)   /* bad argument or instance (asymmetric J, self-loop, bad schedule...) */
+#define SG_ENOMEM (-2)   /* workspace too small or misaligned, or host allocation failed */
+#define SG_ECUDA (-3)    /* CUDA runtime error; the message names the call */
+#define SG_ETIMEOUT (-4) /* a bounded device-side wait expired; the handle must be destroyed */
+#define SG_ESTATE (-5)   /* call out of order (e.g. sweep before attach) */
+
+/* kernel selection */
+#define SG_VB_PLAIN 0    /* baseline: one thread per (vertex, lane, replica), int8 spins, CSR */
+#define SG_VB_PACKED 1   /* 64 lanes per uint64, bit-sliced field count, sliced-ELL graph */
+#define SG_SK_PLAIN 2    /* baseline: sequential order, one thread block per replica */
+#define SG_SK_BLOCKED 3  /* blocked sweep: in-block update + tensor-core off-block field update */
+
+#define SG_VB_MAX_DEGREE 63      /* VB vertex degree limit */
+#define SG_VB_MAX_N ((1 << 26) - 1) /* VB vertices per graph */
+
+typedef struct sg_ctx *sg_handle;
+
+/* One Viana-Bray graph with 64 coupling sets (Eq. 3; SI section 2).
+ *   n         number of vertices, 2 <= n <= SG_VB_MAX_N
+ *   row_ptr   int32[n+1] CSR row offsets (host)
+ *   col       int32[row_ptr[n]] neighbour lists (host); simple undirected graph: symmetric, no
+ *             self-loop, no duplicate, degree <= SG_VB_MAX_DEGREE
+ *   jbits     uint64[row_ptr[n]] couplings per directed entry (host): bit k = 1 iff J_ij = -1
+ *             in lane k; the entries (i,j) and (j,i) must hold the same word
+ *   seed      Philox key of this graph's random numbers
+ *   temps     double[n_replicas] temperatures of the replicas (host); 0 and +inf are allowed */
+typedef struct {
+    int32_t n;
+    const int32_t *row_ptr;
+    const int32_t *col;
+    const uint64_t *jbits;
+    uint64_t seed;
+    const double *temps;
+} sg_vb_graph;
+
+/* Message of the last failed call on this thread ("" if none).  Owned by the library. */
+const char *sg_last_error(void);
+
+/* Create a batch of Viana-Bray instances that evolve in lock-step (one sweep of the batch =
+ * one sweep of every graph; the batched persistent form of the uneven workloads).
+ *   graphs[n_graphs]  the instances (host)
+ *   n_lanes           lanes reported in the results, 1..64 (the packed kernel always simulates
+ *                     all 64; the plain kernel simulates only these)
+ *   n_replicas        R >= 1 replicas per graph (R <= 4 for SG_VB_PACKED)
+ *   kernel            SG_VB_PLAIN or SG_VB_PACKED (SG_VB_PLAIN requires n_graphs == 1)
+ *   tw[n_tw]          strictly increasing snapshot times t_w >= 0 (sweeps)
+ *   tm[n_tm]          strictly increasing measurement times >= 0 (sweeps)
+ *   out               receives the handle; nothing is on the device until sg_attach()
+ * Host-side work: validation, greedy colouring (vertex order), relabelling of each graph into
+ * colour classes, construction of the device layout. */
+int sg_create_vb(const sg_vb_graph *graphs, int32_t n_graphs, int32_t n_lanes,
+                 int32_t n_replicas, int32_t kernel, const int64_t *tw, int32_t n_tw,
+                 const int64_t *tm, int32_t n_tm, sg_handle *out);
+
+/* Create an SK instance (Eq. 1; SI section 1).
+ *   n          spins, 2 <= n <= 32768
+ *   J          int8[n*n] row-major couplings (host): +-1 off the diagonal, 0 on it, symmetric
+ *   n_replicas R >= 1 replicas sharing J (a multiple of 16 for SG_SK_BLOCKED)
+ *   temps      double[R] replica temperatures (host)
+ *   seed       Philox key
+ *   kernel     SG_SK_PLAIN or SG_SK_BLOCKED
+ *   block      spins per block B for SG_SK_BLOCKED (multiple of 32, divides the padded size);
+ *              ignored by SG_SK_PLAIN
+ *   tw, tm     schedule, as for sg_create_vb */
+int sg_create_sk(int32_t n, const int8_t *J, int32_t n_replicas, const double *temps,
+                 uint64_t seed, int32_t kernel, int32_t block, const int64_t *tw, int32_t n_tw,
+                 const int64_t *tm, int32_t n_tm, sg_handle *out);
+
+/* Device workspace size the handle needs (bytes). */
+int sg_workspace_bytes(sg_handle h, size_t *bytes);
+
+/* Bind the caller's device workspace and CUDA stream (cudaStream_t, may be NULL for the legacy
+ * default stream), copy the instance to the device, draw the initial spins (tau = 0) and take the
+ * tau = 0 snapshot/measurement if scheduled.  Returns after the copies have completed. */
+int sg_attach(sg_handle h, void *dev_workspace, size_t bytes, void *cuda_stream);
+
+/* Advance by n >= 0 sweeps, asynchronously on the handle's stream.  Snapshots and measurements
+ * due at the times passed are taken on the device on the way. */
+int sg_sweep(sg_handle h, int64_t n);
+
+/* Current time tau (completed sweeps), as queued. */
+int sg_time(sg_handle h, int64_t *tau);
+
+/* Wait for the handle's queued work; reports device-side errors (SG_ECUDA, SG_ETIMEOUT). */
+int sg_synchronize(sg_handle h);
+
+/* Shapes of the result arrays: n_inst, n_replicas, n_lanes, n_tw, n_tm (5 int32). */
+int sg_result_shape(sg_handle h, int32_t *shape5);
+
+/* Copy the scheduled measurements to the host (synchronises).  Layouts (int64):
+ *   C[n_inst][R][L][n_tw][n_tm]  sum_i s_i(tm) s_i(tw) for tw <= tm <= tau, else 0
+ *   q[n_inst][R/2][L][n_tm]      sum_i s_i^(2p)(tm) s_i^(2p+1)(tm)
+ *   E[n_inst][R][L][n_tm]        VB: sum_{(ij) in E} J_ij s_i s_j;  SK: sum_{i<j} J_ij s_i s_j
+ * (SK has L = 1.)  Entries whose time has not been reached are 0.  Each *_len is the capacity
+ * in elements; a NULL pointer skips that array. */
+int sg_read_results(sg_handle h, int64_t *C, size_t C_len, int64_t *q, size_t q_len,
+                    int64_t *E, size_t E_len);
+
+/* Measure now, at the current tau, against every snapshot taken so far (synchronises).
+ * C[n_inst][R][L][n_tw] (0 for snapshots not yet taken), q[n_inst][R/2][L], E[n_inst][R][L]. */
+int sg_measure(sg_handle h, int64_t *C, size_t C_len, int64_t *q, size_t q_len, int64_t *E,
+               size_t E_len);
+
+/* Current spins in the caller's vertex order (synchronises).
+ *   VB: uint64[n_inst][R][n_g] concatenated over graphs, bit k = 1 iff s = -1 in lane k (bits
+ *       >= n_lanes are 0 for SG_VB_PLAIN);  SK: int8[R][n] of +-1.
+ * bytes must equal the exact size. */
+int sg_get_spins(sg_handle h, void *host_dst, size_t bytes);
+
+/* The acceptance threshold tables in use: VB uint32[n_inst][R][SG_VB_MAX_DEGREE+1] (entry m),
+ * SK uint32[R][n] (entry k).  Entry 0 is 2^32-1. */
+int sg_get_thresholds(sg_handle h, uint32_t *dst, size_t len);
+
+/* Checkpoint: the full dynamic state (tau, spins, snapshots, counts) as an opaque host blob.
+ * sg_state_bytes gives its size; sg_load_state restores it into an attached handle created
+ * from the same instance. */
+int sg_state_bytes(sg_handle h, size_t *bytes);
+int sg_save_state(sg_handle h, void *host_dst, size_t bytes);
+int sg_load_state(sg_handle h, const void *host_src, size_t bytes);
+
+/* Release the handle (the workspace and stream stay the caller's). */
+int sg_destroy(sg_handle h);
+
+/* Number of kernel launches the handle has queued since creation (for launch accounting). */
+int sg_launch_count(sg_handle h, int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SG_H */

@@ -1,0 +1,349 @@
+// sg_api.cu -- the extern "C" boundary of libsg (declared in include/sg.h): argument checking,
+// the measurement schedule and the sweep clock, error codes and messages.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/sg.h"
+#include "sg_model.h"
+
+namespace sg {
+
+[[noreturn]] void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+
+void check_cuda(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) fail(SG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+uint32_t metropolis_threshold(double x) {
+    const double v = ldexp(exp(x), 32);
+    if (!(v < 4294967295.0)) return 0xFFFFFFFFu;
+    return (uint32_t)floor(v);
+}
+
+}  // namespace sg
+
+struct sg_ctx {
+    std::unique_ptr<sg::Model> model;
+    std::vector<int64_t> tw, tm;
+    int64_t tau = 0;
+    bool attached = false;
+    cudaStream_t stream = nullptr;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    size_t next_tw = 0, next_tm = 0;  // first schedule entries with time > tau
+};
+
+static thread_local std::string g_last_error;
+
+static int set_error(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+template <class F>
+static int guarded(F&& f) {
+    try {
+        g_last_error.clear();
+        f();
+        return SG_OK;
+    } catch (const sg::Error& e) {
+        return set_error(e.code, e.msg);
+    } catch (const std::bad_alloc&) {
+        return set_error(SG_ENOMEM, "host allocation failed");
+    } catch (const std::exception& e) {
+        return set_error(SG_EINVAL, e.what());
+    } catch (...) {
+        return set_error(SG_EINVAL, "unknown error");
+    }
+}
+
+static std::vector<int64_t> read_schedule(const int64_t* a, int32_t n, const char* name) {
+    if (n < 0 || (n > 0 && !a)) sg::fail(SG_EINVAL, std::string(name) + ": bad array");
+    std::vector<int64_t> v(a, a + n);
+    for (int32_t i = 0; i < n; ++i) {
+        if (v[i] < 0) sg::fail(SG_EINVAL, std::string(name) + ": negative time");
+        if (v[i] >= (int64_t(1) << 32)) sg::fail(SG_EINVAL, std::string(name) + ": time >= 2^32");
+        if (i && v[i] <= v[i - 1]) sg::fail(SG_EINVAL, std::string(name) + ": not strictly increasing");
+    }
+    return v;
+}
+
+static void require_attached(sg_handle h) {
+    if (!h) sg::fail(SG_EINVAL, "null handle");
+    if (!h->attached) sg::fail(SG_ESTATE, "handle has no workspace (call sg_attach first)");
+}
+
+// snapshot/measure at the current tau if the schedule says so
+static void events_at_tau(sg_handle h) {
+    sg::Model& m = *h->model;
+    while (h->next_tw < h->tw.size() && h->tw[h->next_tw] == h->tau) {
+        m.snapshot((int)h->next_tw, h->stream);
+        ++h->next_tw;
+    }
+    while (h->next_tm < h->tm.size() && h->tm[h->next_tm] == h->tau) {
+        m.measure_scheduled((int)h->next_tm, h->tau, h->stream);
+        ++h->next_tm;
+    }
+    sg::check_cuda(cudaGetLastError(), "kernel launch");
+}
+
+extern "C" {
+
+const char* sg_last_error(void) { return g_last_error.c_str(); }
+
+int sg_create_vb(const sg_vb_graph* graphs, int32_t n_graphs, int32_t n_lanes, int32_t n_replicas,
+                 int32_t kernel, const int64_t* tw, int32_t n_tw, const int64_t* tm, int32_t n_tm,
+                 sg_handle* out) {
+    return guarded([&] {
+        if (!out) sg::fail(SG_EINVAL, "out is null");
+        *out = nullptr;
+        if (!graphs || n_graphs < 1) sg::fail(SG_EINVAL, "need at least one graph");
+        std::unique_ptr<sg_ctx> h(new sg_ctx());
+        h->tw = read_schedule(tw, n_tw, "tw");
+        h->tm = read_schedule(tm, n_tm, "tm");
+        h->model.reset(sg::make_vb_model(graphs, n_graphs, n_lanes, n_replicas, kernel, h->tw, h->tm));
+        *out = h.release();
+    });
+}
+
+int sg_create_sk(int32_t n, const int8_t* J, int32_t n_replicas, const double* temps, uint64_t seed,
+                 int32_t kernel, int32_t block, const int64_t* tw, int32_t n_tw, const int64_t* tm,
+                 int32_t n_tm, sg_handle* out) {
+    return guarded([&] {
+        if (!out) sg::fail(SG_EINVAL, "out is null");
+        *out = nullptr;
+        std::unique_ptr<sg_ctx> h(new sg_ctx());
+        h->tw = read_schedule(tw, n_tw, "tw");
+        h->tm = read_schedule(tm, n_tm, "tm");
+        h->model.reset(sg::make_sk_model(n, J, n_replicas, temps, seed, kernel, block, h->tw, h->tm));
+        *out = h.release();
+    });
+}
+
+int sg_workspace_bytes(sg_handle h, size_t* bytes) {
+    return guarded([&] {
+        if (!h || !bytes) sg::fail(SG_EINVAL, "null argument");
+        *bytes = h->model->workspace_bytes();
+    });
+}
+
+int sg_attach(sg_handle h, void* dev_workspace, size_t bytes, void* cuda_stream) {
+    return guarded([&] {
+        if (!h) sg::fail(SG_EINVAL, "null handle");
+        if (h->attached) sg::fail(SG_ESTATE, "already attached");
+        const size_t need = h->model->workspace_bytes();
+        if (!dev_workspace || bytes < need)
+            sg::fail(SG_ENOMEM, "workspace too small: need " + std::to_string(need) + " bytes");
+        if (reinterpret_cast<uintptr_t>(dev_workspace) & 255)
+            sg::fail(SG_ENOMEM, "workspace must be 256-byte aligned");
+        cudaPointerAttributes attr;
+        sg::check_cuda(cudaPointerGetAttributes(&attr, dev_workspace), "cudaPointerGetAttributes");
+        if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+            sg::fail(SG_EINVAL, "workspace is not device memory");
+        h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+        h->ws = static_cast<char*>(dev_workspace);
+        h->ws_bytes = bytes;
+        h->model->attach(h->ws, h->stream);
+        h->attached = true;
+        h->tau = 0;
+        h->next_tw = h->next_tm = 0;
+        events_at_tau(h);
+    });
+}
+
+int sg_sweep(sg_handle h, int64_t n) {
+    return guarded([&] {
+        require_attached(h);
+        if (n < 0) sg::fail(SG_EINVAL, "negative sweep count");
+        if (h->tau + n >= (int64_t(1) << 32)) sg::fail(SG_EINVAL, "time would exceed 2^32 sweeps");
+        sg::Model& m = *h->model;
+        const int64_t end = h->tau + n;
+        while (h->tau < end) {
+            int64_t stop = end;
+            if (h->next_tw < h->tw.size()) stop = std::min(stop, h->tw[h->next_tw]);
+            if (h->next_tm < h->tm.size()) stop = std::min(stop, h->tm[h->next_tm]);
+            for (int64_t t = h->tau; t < stop; ++t) m.sweep((uint32_t)t, h->stream);
+            sg::check_cuda(cudaGetLastError(), "sweep launch");
+            h->tau = stop;
+            events_at_tau(h);
+        }
+    });
+}
+
+int sg_time(sg_handle h, int64_t* tau) {
+    return guarded([&] {
+        if (!h || !tau) sg::fail(SG_EINVAL, "null argument");
+        *tau = h->tau;
+    });
+}
+
+int sg_synchronize(sg_handle h) {
+    return guarded([&] {
+        require_attached(h);
+        sg::check_cuda(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+        const int st = h->model->device_status(h->stream);
+        if (st) sg::fail(SG_ETIMEOUT, "device-side wait expired (status " + std::to_string(st) + ")");
+    });
+}
+
+int sg_result_shape(sg_handle h, int32_t* shape5) {
+    return guarded([&] {
+        if (!h || !shape5) sg::fail(SG_EINVAL, "null argument");
+        const sg::Model& m = *h->model;
+        shape5[0] = m.n_inst;
+        shape5[1] = m.R;
+        shape5[2] = m.L;
+        shape5[3] = (int32_t)h->tw.size();
+        shape5[4] = (int32_t)h->tm.size();
+    });
+}
+
+static void check_len(size_t have, size_t need, const char* name) {
+    if (have < need)
+        sg::fail(SG_EINVAL, std::string(name) + ": capacity " + std::to_string(have) + " < " +
+                                std::to_string(need));
+}
+
+int sg_read_results(sg_handle h, int64_t* C, size_t C_len, int64_t* q, size_t q_len, int64_t* E,
+                    size_t E_len) {
+    return guarded([&] {
+        require_attached(h);
+        const sg::Model& m = *h->model;
+        const size_t ntw = h->tw.size(), ntm = h->tm.size();
+        const size_t nC = (size_t)m.n_inst * m.R * m.L * ntw * ntm;
+        const size_t nq = (size_t)m.n_inst * (m.R / 2) * m.L * ntm;
+        const size_t nE = (size_t)m.n_inst * m.R * m.L * ntm;
+        std::vector<int64_t> c(nC), qq(nq), e(nE);
+        h->model->read_scheduled(h->tau, c.data(), qq.data(), e.data(), h->stream);
+        if (C) { check_len(C_len, nC, "C"); std::copy(c.begin(), c.end(), C); }
+        if (q) { check_len(q_len, nq, "q"); std::copy(qq.begin(), qq.end(), q); }
+        if (E) { check_len(E_len, nE, "E"); std::copy(e.begin(), e.end(), E); }
+    });
+}
+
+int sg_measure(sg_handle h, int64_t* C, size_t C_len, int64_t* q, size_t q_len, int64_t* E,
+               size_t E_len) {
+    return guarded([&] {
+        require_attached(h);
+        const sg::Model& m = *h->model;
+        const size_t ntw = h->tw.size();
+        const size_t nC = (size_t)m.n_inst * m.R * m.L * ntw;
+        const size_t nq = (size_t)m.n_inst * (m.R / 2) * m.L;
+        const size_t nE = (size_t)m.n_inst * m.R * m.L;
+        h->model->measure_now(h->tau, h->stream);
+        sg::check_cuda(cudaGetLastError(), "measure launch");
+        std::vector<int64_t> c(nC), qq(nq), e(nE);
+        h->model->read_now(h->tau, c.data(), qq.data(), e.data(), h->stream);
+        if (C) { check_len(C_len, nC, "C"); std::copy(c.begin(), c.end(), C); }
+        if (q) { check_len(q_len, nq, "q"); std::copy(qq.begin(), qq.end(), q); }
+        if (E) { check_len(E_len, nE, "E"); std::copy(e.begin(), e.end(), E); }
+    });
+}
+
+int sg_get_spins(sg_handle h, void* host_dst, size_t bytes) {
+    return guarded([&] {
+        require_attached(h);
+        if (!host_dst) sg::fail(SG_EINVAL, "null destination");
+        if (bytes != h->model->spins_bytes())
+            sg::fail(SG_EINVAL, "spin buffer must be exactly " +
+                                    std::to_string(h->model->spins_bytes()) + " bytes");
+        h->model->get_spins(host_dst, h->stream);
+    });
+}
+
+int sg_get_thresholds(sg_handle h, uint32_t* dst, size_t len) {
+    return guarded([&] {
+        if (!h || !dst) sg::fail(SG_EINVAL, "null argument");
+        const std::vector<uint32_t> t = h->model->thresholds();
+        check_len(len, t.size(), "thresholds");
+        std::copy(t.begin(), t.end(), dst);
+    });
+}
+
+// checkpoint blob: magic, version, tau, next_tw, next_tm, region sizes, region bytes
+static const uint64_t kStateMagic = 0x5347535441544531ull;  // "SGSTATE1"
+
+int sg_state_bytes(sg_handle h, size_t* bytes) {
+    return guarded([&] {
+        require_attached(h);
+        if (!bytes) sg::fail(SG_EINVAL, "null argument");
+        auto regs = h->model->state_regions();
+        size_t total = 8 * 5 + 8 * regs.size();
+        for (auto& r : regs) total += r.second;
+        *bytes = total;
+    });
+}
+
+int sg_save_state(sg_handle h, void* host_dst, size_t bytes) {
+    return guarded([&] {
+        require_attached(h);
+        auto regs = h->model->state_regions();
+        size_t total = 8 * 5 + 8 * regs.size();
+        for (auto& r : regs) total += r.second;
+        if (!host_dst || bytes != total) sg::fail(SG_EINVAL, "state buffer has the wrong size");
+        sg::check_cuda(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+        uint64_t* hdr = static_cast<uint64_t*>(host_dst);
+        hdr[0] = kStateMagic;
+        hdr[1] = regs.size();
+        hdr[2] = (uint64_t)h->tau;
+        hdr[3] = h->next_tw;
+        hdr[4] = h->next_tm;
+        for (size_t i = 0; i < regs.size(); ++i) hdr[5 + i] = regs[i].second;
+        char* p = static_cast<char*>(host_dst) + 8 * (5 + regs.size());
+        for (auto& r : regs) {
+            sg::check_cuda(cudaMemcpyAsync(p, r.first, r.second, cudaMemcpyDeviceToHost, h->stream),
+                           "state copy");
+            p += r.second;
+        }
+        sg::check_cuda(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    });
+}
+
+int sg_load_state(sg_handle h, const void* host_src, size_t bytes) {
+    return guarded([&] {
+        require_attached(h);
+        auto regs = h->model->state_regions();
+        size_t total = 8 * 5 + 8 * regs.size();
+        for (auto& r : regs) total += r.second;
+        if (!host_src || bytes != total) sg::fail(SG_EINVAL, "state blob has the wrong size");
+        const uint64_t* hdr = static_cast<const uint64_t*>(host_src);
+        if (hdr[0] != kStateMagic || hdr[1] != regs.size())
+            sg::fail(SG_EINVAL, "state blob does not match this handle");
+        for (size_t i = 0; i < regs.size(); ++i)
+            if (hdr[5 + i] != regs[i].second) sg::fail(SG_EINVAL, "state blob region size mismatch");
+        const char* p = static_cast<const char*>(host_src) + 8 * (5 + regs.size());
+        for (auto& r : regs) {
+            sg::check_cuda(cudaMemcpyAsync(r.first, p, r.second, cudaMemcpyHostToDevice, h->stream),
+                           "state copy");
+            p += r.second;
+        }
+        sg::check_cuda(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+        h->tau = (int64_t)hdr[2];
+        h->next_tw = hdr[3];
+        h->next_tm = hdr[4];
+    });
+}
+
+int sg_destroy(sg_handle h) {
+    return guarded([&] {
+        if (!h) return;
+        if (h->attached) cudaStreamSynchronize(h->stream);
+        delete h;
+    });
+}
+
+int sg_launch_count(sg_handle h, int64_t* count) {
+    return guarded([&] {
+        if (!h || !count) sg::fail(SG_EINVAL, "null argument");
+        *count = h->model->launches;
+    });
+}
+
+}  // extern "C"

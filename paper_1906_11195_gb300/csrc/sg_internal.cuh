@@ -1,0 +1,96 @@
+// sg_internal.cuh -- declarations shared by the host API (sg_api.cu) and the kernel files:
+// device layouts, the device-side Philox, and the launch wrappers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sg {
+
+// ---------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds; in each, counter words 0 and 2
+// are multiplied by the two round multipliers, the high halves are mixed into words 1 and 3
+// with the round key, and the key advances by the two Weyl increments.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t uint4_word(const uint4& v, int w) {
+    return w == 0 ? v.x : (w == 1 ? v.y : (w == 2 ? v.z : v.w));
+}
+
+constexpr int kVbThrStride = 64;      // thresholds per (graph, replica): m = 0..63
+constexpr uint32_t kInactive = 0xFFFFFFFFu;
+constexpr int kDegShift = 26;         // vinfo = orig | deg << 26
+constexpr uint32_t kOrigMask = (1u << kDegShift) - 1u;
+
+// ---------------------------------------------------------------------------------------------
+// Viana-Bray packed layout (sliced ELL over colour-major slots).
+// Slots are ordered by (colour, graph, degree, original label); every (colour, graph) group is
+// padded to a multiple of 32 slots, so a warp-sized slice has one colour and one graph.
+// ---------------------------------------------------------------------------------------------
+struct VbPackedDev {
+    const uint32_t* vinfo;       // [n_slots] orig | deg << 26, kInactive for padding slots
+    const uint32_t* slice_base;  // [n_slices+1] first entry of each slice (entries of 32 lanes)
+    const uint32_t* slice_graph; // [n_slices] graph index
+    const uint32_t* col;         // [n_entries] neighbour slot (self for padding entries)
+    const uint64_t* jb;          // [n_entries] coupling word (0 for padding entries)
+    const uint64_t* seeds;       // [n_graphs]
+    const uint32_t* thr;         // [n_graphs][R][64]
+    uint64_t* S;                 // [n_slots][R]
+    uint64_t* snap;              // [n_tw][n_slots][R]
+    int64_t n_slots;
+    int32_t n_slices;
+    int32_t R;
+};
+
+// Viana-Bray plain layout (one graph, colour-major CSR, int8 spins per lane).
+struct VbPlainDev {
+    const int32_t* row_ptr;  // [N+1] in colour-major labels
+    const int32_t* col;      // [2M]
+    const uint64_t* jb;      // [2M]
+    const uint32_t* orig;    // [N] original label of each new label
+    const uint32_t* thr;     // [R][64]
+    int8_t* s;               // [R][L][N]
+    int8_t* snap;            // [n_tw][R][L][N]
+    uint64_t seed;
+    int32_t N, R, L;
+};
+
+// A measurement: per-lane counts of differences, accumulated with atomics into
+// dst[g * stride_g + r * stride_r + k * stride_k] (g graph, r replica or pair, k lane).
+//   kind 0: Hamming distance between the spins and snapshot w (all replicas)
+//   kind 1: Hamming distance between replicas 2p and 2p+1 (all pairs)
+//   kind 2: number of unsatisfied directed entries, J_ij s_i s_j = -1 (all replicas)
+struct VbCountJob {
+    int kind;
+    int w;
+    int64_t* dst;
+    int64_t stride_g, stride_r, stride_k;
+};
+
+// launch wrappers (vb_kernels.cu); each returns the number of kernel launches queued
+int vb_packed_init(const VbPackedDev& d, cudaStream_t st);
+int vb_packed_colour(const VbPackedDev& d, uint32_t slice_begin, uint32_t slice_end,
+                     uint32_t t, cudaStream_t st);
+int vb_packed_snapshot(const VbPackedDev& d, int w, cudaStream_t st);
+int vb_packed_count(const VbPackedDev& d, const VbCountJob& job, cudaStream_t st);
+
+int vb_plain_init(const VbPlainDev& d, cudaStream_t st);
+int vb_plain_colour(const VbPlainDev& d, int32_t v_begin, int32_t v_end, uint32_t t,
+                    cudaStream_t st);
+int vb_plain_snapshot(const VbPlainDev& d, int w, cudaStream_t st);
+int vb_plain_count(const VbPlainDev& d, const VbCountJob& job, cudaStream_t st);
+
+}  // namespace sg

@@ -1,0 +1,77 @@
+// sg_model.h -- host-side model interface behind the C ABI.  sg_api.cu owns the handle, the
+// schedule and the clock; a Model owns its device layout and launches its kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+namespace sg {
+
+// Error raised inside the host library; converted to a status code at the ABI boundary.
+struct Error {
+    int code;
+    std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+
+// 256-byte aligned carving of one caller-provided workspace (a null base only measures).
+struct Carver {
+    char* base = nullptr;
+    size_t off = 0;
+    template <class T>
+    T* take(size_t n) {
+        off = (off + 255) & ~size_t(255);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+class Model {
+public:
+    virtual ~Model() = default;
+    // bytes of device workspace
+    virtual size_t workspace_bytes() const = 0;
+    // copy the instance into ws, draw the initial spins, zero the counters (synchronous)
+    virtual void attach(char* ws, cudaStream_t st) = 0;
+    // one sweep with sweep index t (queued)
+    virtual void sweep(uint32_t t, cudaStream_t st) = 0;
+    // snapshot w <- current spins
+    virtual void snapshot(int w, cudaStream_t st) = 0;
+    // scheduled measurement column u at time tau (snapshots with tw <= tau exist)
+    virtual void measure_scheduled(int u, int64_t tau, cudaStream_t st) = 0;
+    // immediate measurement at time tau into the model's own scratch counts
+    virtual void measure_now(int64_t tau, cudaStream_t st) = 0;
+    // copy counts to the host and finalise them into C, q, E (see sg.h for layouts)
+    virtual void read_scheduled(int64_t tau, int64_t* C, int64_t* q, int64_t* E,
+                                cudaStream_t st) = 0;
+    virtual void read_now(int64_t tau, int64_t* C, int64_t* q, int64_t* E, cudaStream_t st) = 0;
+    virtual size_t spins_bytes() const = 0;
+    virtual void get_spins(void* dst, cudaStream_t st) = 0;
+    virtual std::vector<uint32_t> thresholds() const = 0;
+    // device regions that hold the dynamic state (checkpoint/restore)
+    virtual std::vector<std::pair<void*, size_t>> state_regions() = 0;
+    // device-side error word (0 = fine), read after synchronisation
+    virtual int device_status(cudaStream_t st) { (void)st; return 0; }
+
+    int n_inst = 1, R = 1, L = 1;
+    std::vector<int64_t> tw, tm;
+    int64_t launches = 0;
+};
+
+Model* make_vb_model(const void* graphs, int n_graphs, int n_lanes, int n_replicas, int kernel,
+                     const std::vector<int64_t>& tw, const std::vector<int64_t>& tm);
+Model* make_sk_model(int n, const int8_t* J, int n_replicas, const double* temps, uint64_t seed,
+                     int kernel, int block, const std::vector<int64_t>& tw,
+                     const std::vector<int64_t>& tm);
+
+// threshold f(x) = min(2^32-1, floor(2^32 exp(x))) in double precision
+uint32_t metropolis_threshold(double x);
+
+}  // namespace sg

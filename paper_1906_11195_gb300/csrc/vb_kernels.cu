@@ -1,0 +1,421 @@
+// vb_kernels.cu -- Viana-Bray Metropolis kernels for sm_103a.
+//
+// Model (Eq. 3): H = -sum_{(ij) in E} J_ij s_i s_j, J_ij = +-1.  Flipping s_i changes the
+// energy by dE = 2m with m = s_i sum_j J_ij s_j = d_i - 2u_i, u_i the number of unsatisfied
+// edges at i (J_ij s_i s_j = -1).  Metropolis (Methods): flip iff m <= 0 or r32 < thr[m].
+// A sweep updates one colour class (an independent set) at a time, the generalisation of the
+// bipartite half-updates of SI section 3.
+//
+// Packed kernel (multispin coding, SI section 2): bit k of a uint64 spin word is lane k (an
+// independent disorder sample); one thread updates one vertex for all 64 lanes and all R
+// replicas.  Per neighbour, x = S_i ^ S_j ^ J marks the unsatisfied lanes; x is added into a
+// bit-sliced counter (6 planes, degree <= 63).  Because thr[m] is non-increasing in m and the
+// random number is shared by the 64 lanes, the accepted set {m <= m*} is a prefix: with
+// m* = #{m in 1..d : r32 < thr[m]}, a lane flips iff d - 2u <= m*, i.e. u >= ceil((d - m*)/2).
+// That is one bit-sliced compare against a per-thread constant.
+#include "sg_internal.cuh"
+
+namespace sg {
+
+// ---------------------------------------------------------------------------------------------
+// packed: initial spins (quench from a random configuration)
+// ---------------------------------------------------------------------------------------------
+__global__ void k_vb_packed_init(VbPackedDev d) {
+    const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= d.n_slots) return;
+    const uint32_t vi = d.vinfo[slot];
+    const int R = d.R;
+    if (vi == kInactive) {
+        for (int r = 0; r < R; ++r) d.S[slot * R + r] = 0ull;
+        return;
+    }
+    const uint32_t g = d.slice_graph[slot >> 5];
+    const uint64_t seed = d.seeds[g];
+    const uint32_t orig = vi & kOrigMask;
+    for (int r = 0; r < R; ++r) {
+        const uint4 w = philox4x32_10(make_uint4(orig, 0u, (uint32_t)r, 1u), (uint32_t)seed,
+                                      (uint32_t)(seed >> 32));
+        d.S[slot * R + r] = (uint64_t)w.x | ((uint64_t)w.y << 32);
+    }
+}
+
+int vb_packed_init(const VbPackedDev& d, cudaStream_t st) {
+    const int bs = 256;
+    const int64_t nb = (d.n_slots + bs - 1) / bs;
+    k_vb_packed_init<<<(unsigned)nb, bs, 0, st>>>(d);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------------------------
+// packed: one colour class
+// ---------------------------------------------------------------------------------------------
+template <int R>
+struct SpinWords { uint64_t v[R]; };
+
+template <int R>
+__device__ __forceinline__ SpinWords<R> load_words(const uint64_t* p) {
+    SpinWords<R> s;
+    if constexpr (R == 1) {
+        s.v[0] = p[0];
+    } else if constexpr (R == 2) {
+        const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(p);
+        s.v[0] = a.x; s.v[1] = a.y;
+    } else {
+        const ulonglong2 a = reinterpret_cast<const ulonglong2*>(p)[0];
+        const ulonglong2 b = reinterpret_cast<const ulonglong2*>(p)[1];
+        s.v[0] = a.x; s.v[1] = a.y; s.v[2] = b.x; s.v[3] = b.y;
+    }
+    return s;
+}
+
+template <int R>
+__device__ __forceinline__ SpinWords<R> gather_words(const uint64_t* p) {
+    SpinWords<R> s;
+    if constexpr (R == 1) {
+        s.v[0] = __ldg(p);
+    } else if constexpr (R == 2) {
+        const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(p));
+        s.v[0] = a.x; s.v[1] = a.y;
+    } else {
+        const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(p));
+        const ulonglong2 b = __ldg(reinterpret_cast<const ulonglong2*>(p) + 1);
+        s.v[0] = a.x; s.v[1] = a.y; s.v[2] = b.x; s.v[3] = b.y;
+    }
+    return s;
+}
+
+template <int R>
+__device__ __forceinline__ void store_words(uint64_t* p, const SpinWords<R>& s) {
+    if constexpr (R == 1) {
+        p[0] = s.v[0];
+    } else if constexpr (R == 2) {
+        *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(s.v[0], s.v[1]);
+    } else {
+        reinterpret_cast<ulonglong2*>(p)[0] = make_ulonglong2(s.v[0], s.v[1]);
+        reinterpret_cast<ulonglong2*>(p)[1] = make_ulonglong2(s.v[2], s.v[3]);
+    }
+}
+
+constexpr int kPlanes = 6;  // bit-sliced unsatisfied-edge counter, counts up to 63
+
+__device__ __forceinline__ void bitslice_add(uint64_t (&p)[kPlanes], uint64_t x) {
+#pragma unroll
+    for (int b = 0; b < kPlanes; ++b) {
+        const uint64_t c = p[b] & x;
+        p[b] ^= x;
+        x = c;
+    }
+}
+
+// lanes whose counter value is >= k (k a per-thread scalar, 0 <= k <= 63)
+__device__ __forceinline__ uint64_t bitslice_ge(const uint64_t (&p)[kPlanes], int k) {
+    uint64_t gt = 0ull, eq = ~0ull;
+#pragma unroll
+    for (int b = kPlanes - 1; b >= 0; --b) {
+        const uint64_t kb = ((k >> b) & 1) ? ~0ull : 0ull;
+        gt |= eq & p[b] & ~kb;
+        eq &= ~(p[b] ^ kb);
+    }
+    return gt | eq;
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_t slice_begin,
+                                                          uint32_t slice_end, uint32_t t) {
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t slice = slice_begin + warp;
+    if (slice >= slice_end) return;
+    const int64_t slot = (int64_t)slice * 32 + lane;
+    const uint32_t vi = d.vinfo[slot];
+    if (vi == kInactive) return;
+    const uint32_t* __restrict__ col = d.col;
+    const uint64_t* __restrict__ jb = d.jb;
+    const uint64_t* __restrict__ S = d.S;
+
+    const uint32_t g = d.slice_graph[slice];
+    const uint32_t base = d.slice_base[slice];
+    const uint32_t width = (d.slice_base[slice + 1] - base) >> 5;
+    const int deg = (int)(vi >> kDegShift);
+    const uint32_t orig = vi & kOrigMask;
+    const uint64_t seed = d.seeds[g];
+
+    SpinWords<R> si = load_words<R>(S + slot * R);
+
+    // random numbers: one Philox block per (vertex, sweep) serves replicas 0..3
+    const uint4 rnd = philox4x32_10(make_uint4(orig, t, 0u, 0u), (uint32_t)seed,
+                                    (uint32_t)(seed >> 32));
+    const uint32_t* thr = d.thr + (size_t)g * R * kVbThrStride;
+    int kmin[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint32_t r32 = uint4_word(rnd, r);
+        int ms = 0;
+        while (ms < deg && r32 < __ldg(thr + r * kVbThrStride + ms + 1)) ++ms;
+        kmin[r] = (deg - ms + 1) >> 1;
+    }
+
+    uint64_t planes[R][kPlanes];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int b = 0; b < kPlanes; ++b) planes[r][b] = 0ull;
+
+    uint32_t idx = base + lane;
+#pragma unroll 4
+    for (uint32_t e = 0; e < width; ++e, idx += 32) {
+        const uint32_t j = __ldcs(col + idx);
+        const uint64_t J = __ldcs(jb + idx);
+        const SpinWords<R> sj = gather_words<R>(S + (int64_t)j * R);
+#pragma unroll
+        for (int r = 0; r < R; ++r) bitslice_add(planes[r], si.v[r] ^ sj.v[r] ^ J);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) si.v[r] ^= bitslice_ge(planes[r], kmin[r]);
+    store_words<R>(d.S + slot * R, si);
+}
+
+int vb_packed_colour(const VbPackedDev& d, uint32_t slice_begin, uint32_t slice_end, uint32_t t,
+                     cudaStream_t st) {
+    if (slice_end <= slice_begin) return 0;
+    const uint32_t n = slice_end - slice_begin;
+    const int bs = 256;
+    const unsigned nb = (n + (bs / 32) - 1) / (bs / 32);
+    switch (d.R) {
+        case 1: k_vb_packed_colour<1><<<nb, bs, 0, st>>>(d, slice_begin, slice_end, t); break;
+        case 2: k_vb_packed_colour<2><<<nb, bs, 0, st>>>(d, slice_begin, slice_end, t); break;
+        case 4: k_vb_packed_colour<4><<<nb, bs, 0, st>>>(d, slice_begin, slice_end, t); break;
+        default: return -1;
+    }
+    return 1;
+}
+
+// ---------------------------------------------------------------------------------------------
+// snapshot copy (16-byte vectors; the regions are 256-byte aligned and a multiple of 16 bytes)
+// ---------------------------------------------------------------------------------------------
+__global__ void k_copy16(const uint4* __restrict__ src, uint4* __restrict__ dst, int64_t n16) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+static int copy_bytes(const void* src, void* dst, int64_t bytes, cudaStream_t st) {
+    const int64_t n16 = bytes / 16;
+    const int bs = 256;
+    int64_t nb = (n16 + bs - 1) / bs;
+    if (nb > 152 * 16) nb = 152 * 16;
+    if (nb < 1) nb = 1;
+    k_copy16<<<(unsigned)nb, bs, 0, st>>>((const uint4*)src, (uint4*)dst, n16);
+    return 1;
+}
+
+int vb_packed_snapshot(const VbPackedDev& d, int w, cudaStream_t st) {
+    const int64_t words = d.n_slots * d.R;
+    return copy_bytes(d.S, d.snap + (int64_t)w * words, words * 8, st);
+}
+
+// ---------------------------------------------------------------------------------------------
+// packed: per-lane difference counts (C, q, E).  Each warp walks a contiguous run of slices,
+// accumulates bit-sliced per-lane counters (16 planes) and flushes them to global memory when
+// the graph changes and at the end of its run.
+// ---------------------------------------------------------------------------------------------
+constexpr int kCountPlanes = 16;
+constexpr int kCountSlicesPerWarp = 64;
+
+template <int NQ>
+__device__ __forceinline__ void count_add(uint64_t (&p)[NQ][kCountPlanes], int q, uint64_t x) {
+#pragma unroll
+    for (int b = 0; b < kCountPlanes; ++b) {
+        const uint64_t c = p[q][b] & x;
+        p[q][b] ^= x;
+        x = c;
+    }
+}
+
+template <int NQ>
+__device__ __forceinline__ void count_flush(uint64_t (&p)[NQ][kCountPlanes], const VbCountJob& job,
+                                            uint32_t g, int nq, uint32_t lane) {
+    for (int q = 0; q < nq; ++q) {
+        for (int k = 0; k < 64; ++k) {
+            uint32_t c = 0;
+#pragma unroll
+            for (int b = 0; b < kCountPlanes; ++b) c |= (uint32_t)((p[q][b] >> k) & 1ull) << b;
+            const uint32_t tot = __reduce_add_sync(0xFFFFFFFFu, c);
+            if (lane == 0 && tot)
+                atomicAdd((unsigned long long*)(job.dst + g * job.stride_g + q * job.stride_r +
+                                                k * job.stride_k),
+                          (unsigned long long)tot);
+        }
+#pragma unroll
+        for (int b = 0; b < kCountPlanes; ++b) p[q][b] = 0ull;
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) k_vb_packed_count(VbPackedDev d, VbCountJob job) {
+    constexpr int NQ = R;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t s_lo = (int64_t)warp * kCountSlicesPerWarp;
+    int64_t s_hi = s_lo + kCountSlicesPerWarp;
+    if (s_hi > d.n_slices) s_hi = d.n_slices;
+    const int nq = job.kind == 1 ? R / 2 : R;
+    uint64_t p[NQ][kCountPlanes];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int b = 0; b < kCountPlanes; ++b) p[q][b] = 0ull;
+    const int64_t words = d.n_slots * R;
+    const uint64_t* snap = d.snap + (int64_t)(job.kind == 0 ? job.w : 0) * words;
+    int64_t cur_g = -1;
+    for (int64_t s = s_lo; s < s_hi; ++s) {
+        const uint32_t g = d.slice_graph[s];  // warp-uniform
+        if ((int64_t)g != cur_g) {
+            if (cur_g >= 0) count_flush<NQ>(p, job, (uint32_t)cur_g, nq, lane);
+            cur_g = g;
+        }
+        const int64_t slot = s * 32 + lane;
+        if (d.vinfo[slot] == kInactive) continue;
+        const SpinWords<R> si = load_words<R>(d.S + slot * R);
+        if (job.kind == 0) {
+            const SpinWords<R> sw = load_words<R>(snap + slot * R);
+#pragma unroll
+            for (int r = 0; r < R; ++r) count_add<NQ>(p, r, si.v[r] ^ sw.v[r]);
+        } else if (job.kind == 1) {
+#pragma unroll
+            for (int q = 0; q < R / 2; ++q) count_add<NQ>(p, q, si.v[2 * q] ^ si.v[2 * q + 1]);
+        } else {
+            const uint32_t base = d.slice_base[s];
+            const uint32_t width = (d.slice_base[s + 1] - base) >> 5;
+            uint32_t idx = base + lane;
+            for (uint32_t e = 0; e < width; ++e, idx += 32) {
+                const uint32_t j = d.col[idx];
+                const uint64_t J = d.jb[idx];
+                const SpinWords<R> sj = load_words<R>(d.S + (int64_t)j * R);
+#pragma unroll
+                for (int r = 0; r < R; ++r) count_add<NQ>(p, r, si.v[r] ^ sj.v[r] ^ J);
+            }
+        }
+    }
+    if (cur_g >= 0) count_flush<NQ>(p, job, (uint32_t)cur_g, nq, lane);
+}
+
+int vb_packed_count(const VbPackedDev& d, const VbCountJob& job, cudaStream_t st) {
+    const int bs = 256;
+    const int64_t warps = (d.n_slices + kCountSlicesPerWarp - 1) / kCountSlicesPerWarp;
+    const unsigned nb = (unsigned)((warps + (bs / 32) - 1) / (bs / 32));
+    switch (d.R) {
+        case 1: k_vb_packed_count<1><<<nb, bs, 0, st>>>(d, job); break;
+        case 2: k_vb_packed_count<2><<<nb, bs, 0, st>>>(d, job); break;
+        case 4: k_vb_packed_count<4><<<nb, bs, 0, st>>>(d, job); break;
+        default: return -1;
+    }
+    return 1;
+}
+
+// ---------------------------------------------------------------------------------------------
+// plain kernel: one thread per (vertex, lane, replica), int8 spins, CSR in colour-major labels
+// ---------------------------------------------------------------------------------------------
+__global__ void k_vb_plain_init(VbPlainDev d) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)d.N * d.R) return;
+    const int32_t v = (int32_t)(idx % d.N);
+    const int32_t r = (int32_t)(idx / d.N);
+    const uint4 w = philox4x32_10(make_uint4(d.orig[v], 0u, (uint32_t)r, 1u), (uint32_t)d.seed,
+                                  (uint32_t)(d.seed >> 32));
+    const uint64_t bits = (uint64_t)w.x | ((uint64_t)w.y << 32);
+    for (int k = 0; k < d.L; ++k)
+        d.s[((int64_t)r * d.L + k) * d.N + v] = ((bits >> k) & 1ull) ? (int8_t)-1 : (int8_t)1;
+}
+
+int vb_plain_init(const VbPlainDev& d, cudaStream_t st) {
+    const int bs = 256;
+    const int64_t n = (int64_t)d.N * d.R;
+    k_vb_plain_init<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(d);
+    return 1;
+}
+
+__global__ void k_vb_plain_colour(VbPlainDev d, int32_t v0, int32_t nv, uint32_t t) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)nv * d.R * d.L) return;
+    const int32_t v = v0 + (int32_t)(idx % nv);
+    const int32_t rk = (int32_t)(idx / nv);
+    const int32_t r = rk / d.L, k = rk % d.L;
+    const uint4 rnd = philox4x32_10(make_uint4(d.orig[v], t, (uint32_t)(r >> 2), 0u),
+                                    (uint32_t)d.seed, (uint32_t)(d.seed >> 32));
+    const uint32_t r32 = uint4_word(rnd, r & 3);
+    int8_t* s = d.s + (int64_t)rk * d.N;
+    int field = 0;
+    for (int32_t e = d.row_ptr[v]; e < d.row_ptr[v + 1]; ++e) {
+        const int J = ((d.jb[e] >> k) & 1ull) ? -1 : 1;
+        field += J * s[d.col[e]];
+    }
+    const int m = s[v] * field;
+    const bool flip = (m <= 0) || (r32 < d.thr[r * kVbThrStride + m]);
+    if (flip) s[v] = (int8_t)(-s[v]);
+}
+
+int vb_plain_colour(const VbPlainDev& d, int32_t v_begin, int32_t v_end, uint32_t t,
+                    cudaStream_t st) {
+    const int32_t nv = v_end - v_begin;
+    if (nv <= 0) return 0;
+    const int bs = 256;
+    const int64_t n = (int64_t)nv * d.R * d.L;
+    k_vb_plain_colour<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(d, v_begin, nv, t);
+    return 1;
+}
+
+int vb_plain_snapshot(const VbPlainDev& d, int w, cudaStream_t st) {
+    const int64_t bytes = (int64_t)d.R * d.L * d.N;
+    // int8 snapshots are not 16-byte multiples in general: use a byte copy
+    return cudaMemcpyAsync(d.snap + (int64_t)w * bytes, d.s, (size_t)bytes,
+                           cudaMemcpyDeviceToDevice, st) == cudaSuccess ? 0 : -1;
+}
+
+// per-(replica or pair, lane) difference counts over the vertices; blockIdx.y = rq * L + k
+__global__ void k_vb_plain_count(VbPlainDev d, VbCountJob job) {
+    const int32_t rk = blockIdx.y;
+    const int32_t rq = rk / d.L, k = rk % d.L;
+    const int64_t plane = (int64_t)d.R * d.L * d.N;
+    unsigned long long acc = 0;
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < d.N; v += gridDim.x * blockDim.x) {
+        if (job.kind == 0) {
+            const int64_t o = ((int64_t)rq * d.L + k) * d.N + v;
+            acc += d.s[o] != d.snap[(int64_t)job.w * plane + o];
+        } else if (job.kind == 1) {
+            const int64_t a = ((int64_t)(2 * rq) * d.L + k) * d.N + v;
+            const int64_t b = ((int64_t)(2 * rq + 1) * d.L + k) * d.N + v;
+            acc += d.s[a] != d.s[b];
+        } else {
+            const int8_t* s = d.s + ((int64_t)rq * d.L + k) * d.N;
+            for (int32_t e = d.row_ptr[v]; e < d.row_ptr[v + 1]; ++e) {
+                const int J = ((d.jb[e] >> k) & 1ull) ? -1 : 1;
+                acc += (J * s[v] * s[d.col[e]]) < 0;
+            }
+        }
+    }
+    // block reduction
+    __shared__ unsigned long long red[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0ull;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
+        if (threadIdx.x == 0 && acc)
+            atomicAdd((unsigned long long*)(job.dst + rq * job.stride_r + k * job.stride_k), acc);
+    }
+}
+
+int vb_plain_count(const VbPlainDev& d, const VbCountJob& job, cudaStream_t st) {
+    const int nq = job.kind == 1 ? d.R / 2 : d.R;
+    if (nq <= 0) return 0;
+    const int bs = 256;
+    int nb = (d.N + bs - 1) / bs;
+    if (nb > 64) nb = 64;
+    dim3 grid((unsigned)nb, (unsigned)(nq * d.L));
+    k_vb_plain_count<<<grid, bs, 0, st>>>(d, job);
+    return 1;
+}
+
+}  // namespace sg

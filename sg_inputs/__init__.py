@@ -25,6 +25,7 @@ __all__ = [
     "sk_couplings",
     "log_uniform_sizes",
     "csr_from_edges",
+    "log_schedule",
 ]
 
 
@@ -40,7 +41,7 @@ def csr_from_edges(n: int, ei: np.ndarray, ej: np.ndarray):
     src = np.concatenate([ei, ej])
     dst = np.concatenate([ej, ei])
     eid = np.concatenate([np.arange(m), np.arange(m)])
-    order = np.lexsort((dst, src))
+    order = np.argsort(src * n + dst)  # keys are distinct
     src, dst, eid = src[order], dst[order], eid[order]
     counts = np.bincount(src, minlength=n)
     row_ptr = np.zeros(n + 1, dtype=np.int64)
@@ -64,20 +65,18 @@ def poisson_graph(n: int, c: float, seed: int):
         raise ValueError("too many edges requested")
     rng = np.random.default_rng(np.random.SeedSequence([0x5EED_0001, seed]))
     keys = np.empty(0, dtype=np.int64)
-    while keys.size < m:
-        need = m - keys.size
-        k = max(need + need // 8 + 16, 64)
+    while True:
+        # distinct uniform unordered pairs; a uniform m-subset of them is a uniform G(N, M)
+        k = m - keys.size + 64 + (m - keys.size) // 64
         a = rng.integers(0, n, size=k, dtype=np.int64)
         b = rng.integers(0, n, size=k, dtype=np.int64)
         ok = a != b
-        a, b = a[ok], b[ok]
-        lo, hi = np.minimum(a, b), np.maximum(a, b)
-        new = lo * n + hi
-        # keep the first occurrence of each new key, in draw order, then drop known ones
-        _, first = np.unique(new, return_index=True)
-        new = new[np.sort(first)]
-        new = new[~np.isin(new, keys)]
-        keys = np.concatenate([keys, new[:need]])
+        lo, hi = np.minimum(a[ok], b[ok]), np.maximum(a[ok], b[ok])
+        keys = np.sort(np.concatenate([keys, lo * n + hi]))
+        keys = keys[np.concatenate([[True], keys[1:] != keys[:-1]])]
+        if keys.size >= m:
+            break
+    keys = np.sort(rng.choice(keys, size=m, replace=False))
     ei, ej = keys // n, keys % n
     return csr_from_edges(n, ei, ej)
 
@@ -129,3 +128,19 @@ def log_uniform_sizes(count: int, lo_exp: float, hi_exp: float, seed: int) -> np
     rng = np.random.default_rng(np.random.SeedSequence([0x5EED_0005, seed]))
     u = rng.uniform(lo_exp, hi_exp, size=count)
     return np.round(2.0 ** u).astype(np.int64)
+
+
+def log_schedule(tw, t_max: int):
+    """Snapshot times tw and measurement times {t_w + 2^k <= t_max} united with tw itself.
+
+    Measurements at log-spaced times after each waiting time (main text: t_w = 2^2..2^12 and
+    t up to 2^25; SI section 1: t_w = 3).  Returns (tw sorted unique, tm sorted unique).
+    """
+    tw = sorted({int(x) for x in tw if 0 <= int(x) <= t_max})
+    tm = set(tw)
+    for w in tw:
+        k = 0
+        while w + (1 << k) <= t_max:
+            tm.add(w + (1 << k))
+            k += 1
+    return np.array(tw, dtype=np.int64), np.array(sorted(tm), dtype=np.int64)

@@ -1,0 +1,93 @@
+"""The C-ABI library builds, loads and exports every entry point declared in include/sg.h, and
+its host-side logic (argument checking, instance validation, layout sizing) works without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1906_11195_gb300 as sg
+import sg_inputs
+from paper_1906_11195_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return ctypes.CDLL(_build.LIB)
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "sg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sg_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(sg.EXPORTED)
+
+
+def _graph(n=200, c=4.0, seed=3):
+    rp, col, eid = sg_inputs.poisson_graph(n, c, seed)
+    jb = sg_inputs.vb_lane_couplings(eid, eid.max() + 1, seed)
+    return dict(row_ptr=rp, col=col, jbits=jb, seed=5, temps=[1.0, 1.0])
+
+
+def test_create_and_size_without_gpu(lib):
+    g = _graph()
+    for kernel in (sg.SG_VB_PLAIN, sg.SG_VB_PACKED):
+        h = sg.sg_create_vb([g], 8, 2, kernel, [0, 4], [0, 4, 8])
+        assert sg.sg_workspace_bytes(h) > 0
+        assert sg.sg_result_shape(h) == (1, 2, 8, 2, 3)
+        thr = sg.sg_get_thresholds(h, 2 * 64)
+        assert thr[0] == 0xFFFFFFFF and thr[1] == int(np.floor(2.0**32 * np.exp(-2.0)))
+        with pytest.raises(sg.SGError) as e:
+            sg.sg_sweep(h, 1)
+        assert e.value.code == sg.SG_ESTATE
+        sg.sg_destroy(h)
+
+
+@pytest.mark.parametrize("defect", ["asymmetric", "self_loop", "duplicate", "coupling_mismatch",
+                                    "degree", "bad_schedule", "bad_replicas", "bad_temp"])
+def test_invalid_instances_are_rejected(lib, defect):
+    g = _graph()
+    tw, tm, R, kernel = [0], [0, 1], 2, sg.SG_VB_PACKED
+    rp, col, jb = g["row_ptr"].copy(), g["col"].copy(), g["jbits"].copy()
+    if defect == "asymmetric":
+        col[0] = (col[0] + 1) % 200 if (col[0] + 1) % 200 != 0 else 2
+    elif defect == "self_loop":
+        col[rp[5]] = 5
+    elif defect == "duplicate":
+        col[rp[7] + 1] = col[rp[7]]
+    elif defect == "coupling_mismatch":
+        jb[0] ^= np.uint64(1)
+    elif defect == "degree":
+        n = 70
+        ei = np.zeros(n - 1, dtype=np.int64)
+        ej = np.arange(1, n)
+        rp, col, _ = sg_inputs.csr_from_edges(n, ei, ej)
+        jb = np.zeros(col.size, dtype=np.uint64)
+    elif defect == "bad_schedule":
+        tw = [4, 2]
+    elif defect == "bad_replicas":
+        R = 3
+    elif defect == "bad_temp":
+        g["temps"] = [-1.0, 1.0]
+    g2 = dict(g, row_ptr=rp, col=col, jbits=jb)
+    with pytest.raises(sg.SGError) as e:
+        sg.sg_create_vb([g2], 64, R, kernel, tw, tm)
+    assert e.value.code == sg.SG_EINVAL
+    assert sg.sg_last_error()
+
+
+def test_schedule_helper():
+    tw, tm = sg_inputs.log_schedule([0, 1, 4], 10)
+    assert list(tw) == [0, 1, 4]
+    assert list(tm) == [0, 1, 2, 3, 4, 5, 6, 8, 9]

@@ -1,0 +1,229 @@
+"""GPU parity of the Viana-Bray kernels against the CPU oracle (bit-exact integers).
+
+Every comparison is element by element: final spins of every lane and replica, and every
+C(t_w, t_w + t), q and E count of the schedule.  Sizes span many 32-vertex slices with ragged
+tails, several colour classes and graphs of uneven size; the full-size workload
+(N = 2^22, 64 lanes, T = 1.0 and 0.6) is compared on a sweep prefix run in the bench's launch
+configuration, and checked at any length through properties that hold exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import sg_inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+sg = None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    global sg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1906_11195_gb300 import _build
+    _build.build()
+    import paper_1906_11195_gb300 as m
+    sg = m
+
+
+def vb_instance(n, c, gseed, temps, seed):
+    rp, col, eid = sg_inputs.poisson_graph(n, c, gseed)
+    jb = sg_inputs.vb_lane_couplings(eid, eid.max() + 1 if eid.size else 0, gseed)
+    return dict(row_ptr=rp, col=col, jbits=jb, seed=seed, temps=list(temps))
+
+
+def run_gpu(graphs, L, R, kernel, sweeps, tw, tm, chunks=None):
+    run = sg.VBRun(graphs, n_lanes=L, n_replicas=R, kernel=kernel, tw=tw, tm=tm)
+    if chunks is None:
+        run.sweep(sweeps)
+    else:
+        done = 0
+        for ch in chunks:
+            run.sweep(ch)
+            done += ch
+        run.sweep(sweeps - done)
+    run.synchronize()
+    C, q, E = run.results()
+    spins = run.spins()
+    launches = run.launches
+    run.close()
+    return spins, C, q, E, launches
+
+
+def lane_mask(L):
+    return np.uint64(0xFFFFFFFFFFFFFFFF) if L == 64 else np.uint64((1 << L) - 1)
+
+
+def assert_matches_oracle(g, L, R, kernel, sweeps, tw, tm, spins, C, q, E, b=0):
+    """Compare lanes 0..L-1 (the oracle simulates exactly those lanes)."""
+    ref = oracle.vb_run(g["row_ptr"], g["col"], g["jbits"], L, g["temps"], g["seed"], sweeps, tw, tm)
+    mask = lane_mask(L)
+    assert np.array_equal(spins[b] & mask, ref["spins"] & mask)
+    assert np.array_equal(C[b][:, :L], ref["C"][:, :L])
+    assert np.array_equal(q[b][:, :L], ref["q"][:, :L])
+    assert np.array_equal(E[b][:, :L], ref["E"][:, :L])
+
+
+def test_config1_plain_kernel_matches_oracle():
+    """Poisson c=4, N=1024, 8 lanes x 2 replicas, T=1.0, 4096 sweeps, tw,t = 2^k, seed 1."""
+    g = vb_instance(1024, 4.0, 1, [1.0, 1.0], 1)
+    tw, tm = sg_inputs.log_schedule([0] + [2**k for k in range(12)], 4096)
+    spins, C, q, E, _ = run_gpu([g], 8, 2, sg.SG_VB_PLAIN, 4096, tw, tm)
+    assert_matches_oracle(g, 8, 2, sg.SG_VB_PLAIN, 4096, tw, tm, spins, C, q, E)
+
+
+def test_config1_packed_kernel_matches_oracle_all_lanes():
+    g = vb_instance(1024, 4.0, 1, [1.0, 1.0], 1)
+    tw, tm = sg_inputs.log_schedule([0] + [2**k for k in range(12)], 4096)
+    spins, C, q, E, _ = run_gpu([g], 64, 2, sg.SG_VB_PACKED, 4096, tw, tm)
+    assert_matches_oracle(g, 64, 2, sg.SG_VB_PACKED, 4096, tw, tm, spins, C, q, E)
+
+
+def test_plain_and_packed_agree_on_shared_lanes():
+    g = vb_instance(777, 4.0, 5, [0.6, 0.6], 9)
+    tw, tm = sg_inputs.log_schedule([0, 3, 16], 200)
+    a = run_gpu([g], 8, 2, sg.SG_VB_PLAIN, 200, tw, tm)
+    b = run_gpu([g], 8, 2, sg.SG_VB_PACKED, 200, tw, tm)
+    mask = lane_mask(8)
+    assert np.array_equal(a[0][0] & mask, b[0][0] & mask)
+    for x, y in zip(a[1:4], b[1:4]):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("n,c,R,temps,sweeps", [
+    (37, 3.0, 1, [0.8], 50),            # ragged: fewer vertices than one slice per colour
+    (1000, 4.0, 4, [1.0, 1.0, 0.6, 0.6], 64),
+    (4099, 6.0, 2, [0.45, 2.5], 33),     # several slices per degree bucket, ragged tail
+    (2, 1.0, 2, [1.0, 1.0], 17),         # one edge
+])
+def test_packed_various_shapes(n, c, R, temps, sweeps):
+    g = vb_instance(n, c, 100 + n, temps, 2**33 + n)
+    tw, tm = sg_inputs.log_schedule([0, 1, 5], sweeps)
+    spins, C, q, E, _ = run_gpu([g], 64, R, sg.SG_VB_PACKED, sweeps, tw, tm)
+    assert_matches_oracle(g, 64, R, sg.SG_VB_PACKED, sweeps, tw, tm, spins, C, q, E)
+
+
+def test_packed_isolated_vertices_and_max_degree():
+    # a star with 63 leaves (maximum degree), a path, and isolated vertices (always flip: dE = 0)
+    n = 100
+    ei = [0] * 63 + list(range(64, 80))
+    ej = list(range(1, 64)) + list(range(65, 81))
+    rp, col, eid = sg_inputs.csr_from_edges(n, np.array(ei), np.array(ej))
+    jb = sg_inputs.vb_lane_couplings(eid, eid.max() + 1, 3)
+    g = dict(row_ptr=rp, col=col, jbits=jb, seed=4, temps=[0.7, 1.3])
+    tw, tm = sg_inputs.log_schedule([0, 2], 40)
+    spins, C, q, E, _ = run_gpu([g], 64, 2, sg.SG_VB_PACKED, 40, tw, tm)
+    assert_matches_oracle(g, 64, 2, sg.SG_VB_PACKED, 40, tw, tm, spins, C, q, E)
+
+
+@pytest.mark.parametrize("T", [0.0, math.inf])
+def test_packed_zero_and_infinite_temperature(T):
+    g = vb_instance(3000, 4.0, 7, [T, T], 12)
+    tw, tm = sg_inputs.log_schedule([0, 1], 20)
+    spins, C, q, E, _ = run_gpu([g], 64, 2, sg.SG_VB_PACKED, 20, tw, tm)
+    assert_matches_oracle(g, 64, 2, sg.SG_VB_PACKED, 20, tw, tm, spins, C, q, E)
+
+
+def test_batched_uneven_graphs_match_per_graph_oracle():
+    sizes = sg_inputs.log_uniform_sizes(6, 5, 11, 4)
+    graphs = [vb_instance(int(n), 4.0, 500 + i, [1.0, 0.6], 1000 + i) for i, n in enumerate(sizes)]
+    tw, tm = sg_inputs.log_schedule([0, 4], 48)
+    spins, C, q, E, _ = run_gpu(graphs, 64, 2, sg.SG_VB_PACKED, 48, tw, tm)
+    for b, g in enumerate(graphs):
+        assert_matches_oracle(g, 64, 2, sg.SG_VB_PACKED, 48, tw, tm, spins, C, q, E, b=b)
+
+
+def test_sweep_chunking_and_measure_now():
+    g = vb_instance(2000, 4.0, 8, [1.0, 1.0], 3)
+    tw, tm = sg_inputs.log_schedule([0, 8], 64)
+    a = run_gpu([g], 64, 2, sg.SG_VB_PACKED, 64, tw, tm)
+    b = run_gpu([g], 64, 2, sg.SG_VB_PACKED, 64, tw, tm, chunks=[1, 6, 9, 13])
+    for x, y in zip(a[:4], b[:4]):
+        assert np.array_equal(np.asarray(x), np.asarray(y))
+    run = sg.VBRun([g], n_lanes=64, n_replicas=2, kernel=sg.SG_VB_PACKED, tw=tw, tm=tm)
+    run.sweep(21)
+    C, q, E = run.measure()
+    ref = oracle.vb_run(g["row_ptr"], g["col"], g["jbits"], 64, g["temps"], g["seed"], 21, tw, [21])
+    assert np.array_equal(C[0], ref["C"][..., 0])
+    assert np.array_equal(q[0], ref["q"][..., 0])
+    assert np.array_equal(E[0], ref["E"][..., 0])
+    run.close()
+
+
+def test_checkpoint_resume_is_bit_exact():
+    g = vb_instance(1500, 4.0, 9, [0.6, 0.6], 8)
+    tw, tm = sg_inputs.log_schedule([0, 4, 16], 60)
+    straight = run_gpu([g], 64, 2, sg.SG_VB_PACKED, 60, tw, tm)
+    run = sg.VBRun([g], n_lanes=64, n_replicas=2, kernel=sg.SG_VB_PACKED, tw=tw, tm=tm)
+    run.sweep(23)
+    blob = run.save_state()
+    run.close()
+    run2 = sg.VBRun([g], n_lanes=64, n_replicas=2, kernel=sg.SG_VB_PACKED, tw=tw, tm=tm)
+    run2.load_state(blob)
+    assert run2.tau == 23
+    run2.sweep(37)
+    C, q, E = run2.results()
+    assert np.array_equal(run2.spins()[0], straight[0][0])
+    assert np.array_equal(C, straight[1]) and np.array_equal(q, straight[2])
+    assert np.array_equal(E, straight[3])
+    run2.close()
+
+
+def test_thresholds_exported_match_oracle():
+    g = vb_instance(64, 4.0, 2, [1.0, 0.6, 0.0, math.inf], 1)
+    run = sg.VBRun([g], n_lanes=64, n_replicas=4, kernel=sg.SG_VB_PACKED)
+    thr = run.thresholds()[0]
+    for r, T in enumerate(g["temps"]):
+        assert np.array_equal(thr[r], oracle.vb_thresholds(T, 63))
+    run.close()
+
+
+# --------------------------------------------------------------------------------------------
+# full-size workload (N = 2^22, Poisson c = 4, 64 lanes, R = 2 per temperature)
+# --------------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def big_graph():
+    return vb_instance(1 << 22, 4.0, 2, [1.0, 1.0], 1)
+
+
+@pytest.mark.parametrize("T", [1.0, 0.6])
+def test_full_size_prefix_matches_oracle(big_graph, T):
+    """The bench's launch configuration (64 lanes, R = 2) on the full graph; the oracle follows
+    lanes 0..7 (lanes are independent samples), 2 sweeps."""
+    g = dict(big_graph, temps=[T, T])
+    sweeps = 2
+    spins, C, q, E, _ = run_gpu([g], 64, 2, sg.SG_VB_PACKED, sweeps, [0, 1], [0, 1, 2])
+    assert_matches_oracle(g, 8, 2, sg.SG_VB_PACKED, sweeps, [0, 1], [0, 1, 2], spins, C, q, E)
+
+
+def test_full_size_long_run_invariants(big_graph):
+    """300 sweeps with the log schedule: exact properties at any size."""
+    g = dict(big_graph, temps=[0.6, 0.6])
+    n = 1 << 22
+    tw, tm = sg_inputs.log_schedule([16, 32, 64, 128, 256], 300)
+    spins, C, q, E, _ = run_gpu([g], 64, 2, sg.SG_VB_PACKED, 300, tw, tm)
+    C, q, E = C[0], q[0], E[0]
+    for w, t0 in enumerate(tw):
+        for u, t in enumerate(tm):
+            if t0 <= t:
+                assert np.all(np.abs(C[:, :, w, u]) <= n) and np.all((C[:, :, w, u] - n) % 2 == 0)
+            if t0 == t:
+                assert np.all(C[:, :, w, u] == n)
+    # energy at the last time from the returned spins (vectorised over lanes and edges)
+    rp, col, jb = g["row_ptr"], g["col"], g["jbits"]
+    src = np.repeat(np.arange(n), np.diff(rp))
+    keep = col > src
+    for r in range(2):
+        x = spins[0][r][src[keep]] ^ spins[0][r][col[keep]] ^ jb[keep]
+        unsat = np.zeros(64, dtype=np.int64)
+        for k in range(64):
+            unsat[k] = int(((x >> np.uint64(k)) & np.uint64(1)).sum())
+        assert np.array_equal(E[r, :, -1], keep.sum() - 2 * unsat)
+    # aging: correlations decay with t and stay positive at T = 0.6 on these scales
+    u_last = len(tm) - 1
+    assert np.all(C[:, :, 0, u_last].mean() < n)
