@@ -195,6 +195,33 @@ def run_reference(args):
     return 0
 
 
+def run_profile_case(args):
+    """One T = 1.0 instance of the full-size graph with no measurement schedule: W + K sweeps.
+    This is the small case used for detailed ncu captures of the colour kernel (about 0.3 GB on
+    the device, inputs larger than L2).  Prints timing only; not a bench line."""
+    import torch
+
+    import paper_1906_11195_gb300 as sg
+    from paper_1906_11195_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    rp, col, jb = instance(0)
+    g = dict(row_ptr=rp, col=col, jbits=jb, seed=1, temps=[TEMPS[0]] * REPLICAS)
+    run = sg.VBRun([g], n_lanes=LANES, n_replicas=REPLICAS, kernel=sg.SG_VB_PACKED)
+    run.sweep(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    run.sweep(args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(1, args.steps)
+    print(json.dumps({"mode": "profile", "ms_per_sweep": ms, "sweeps": args.steps,
+                      "launches": run.launches}), flush=True)
+    run.close()
+    return 0
+
+
 def run_gpu(args):
     import torch
 
@@ -357,16 +384,20 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run only the single-instance sweep case used for ncu captures")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warning: fewer than 3 warm-up steps")
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return run_profile_case(args)
     return run_gpu(args)
 
 
