@@ -27,7 +27,16 @@ uint32_t metropolis_threshold(double x) {
     return (uint32_t)floor(v);
 }
 
+// the device-side sweep clock read by the sweep kernels (t = *clock + offset)
+__global__ void k_clock_set(uint32_t* c, uint32_t v) { *c = v; }
+__global__ void k_clock_add(uint32_t* c, uint32_t v) { *c += v; }
+
 }  // namespace sg
+
+// Sweeps are replayed from CUDA graphs of 2^k sweeps (k <= kMaxGraphLog), captured lazily on a
+// private stream and launched on the caller's stream; the graph size is also capped in nodes.
+static const int kMaxGraphLog = 6;
+static const int64_t kMaxGraphNodes = 4096;
 
 struct sg_ctx {
     std::unique_ptr<sg::Model> model;
@@ -38,6 +47,15 @@ struct sg_ctx {
     char* ws = nullptr;
     size_t ws_bytes = 0;
     size_t next_tw = 0, next_tm = 0;  // first schedule entries with time > tau
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graphs[kMaxGraphLog + 1] = {};
+    int64_t graph_kernels[kMaxGraphLog + 1] = {};
+    int max_graph_log = -1;  // decided at the first capture
+    ~sg_ctx() {
+        for (auto& g : graphs)
+            if (g) cudaGraphExecDestroy(g);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
 };
 
 static thread_local std::string g_last_error;
@@ -73,6 +91,60 @@ static std::vector<int64_t> read_schedule(const int64_t* a, int32_t n, const cha
         if (i && v[i] <= v[i - 1]) sg::fail(SG_EINVAL, std::string(name) + ": not strictly increasing");
     }
     return v;
+}
+
+// capture (once) a graph running 2^k sweeps at clock offsets 0..2^k-1 and advancing the clock
+static cudaGraphExec_t sweep_graph(sg_handle h, int k) {
+    if (h->graphs[k]) return h->graphs[k];
+    sg::Model& m = *h->model;
+    if (!h->cap_stream)
+        sg::check_cuda(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking),
+                       "cudaStreamCreateWithFlags");
+    const int64_t before = m.launches;
+    const uint32_t n = 1u << k;
+    sg::check_cuda(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal),
+                   "cudaStreamBeginCapture");
+    cudaGraph_t g = nullptr;
+    try {
+        for (uint32_t s = 0; s < n; ++s) m.sweep(s, h->cap_stream);
+        sg::k_clock_add<<<1, 1, 0, h->cap_stream>>>(m.clock_dev, n);
+    } catch (...) {
+        cudaStreamEndCapture(h->cap_stream, &g);
+        if (g) cudaGraphDestroy(g);
+        m.launches = before;
+        throw;
+    }
+    sg::check_cuda(cudaStreamEndCapture(h->cap_stream, &g), "cudaStreamEndCapture");
+    const cudaError_t e = cudaGraphInstantiate(&h->graphs[k], g, 0);
+    cudaGraphDestroy(g);
+    sg::check_cuda(e, "cudaGraphInstantiate");
+    h->graph_kernels[k] = m.launches - before + 1;
+    m.launches = before;
+    return h->graphs[k];
+}
+
+// queue sweeps t0 .. t0+len-1 on the handle's stream
+static void run_sweeps(sg_handle h, int64_t t0, int64_t len) {
+    if (len <= 0) return;
+    sg::Model& m = *h->model;
+    sg::k_clock_set<<<1, 1, 0, h->stream>>>(m.clock_dev, (uint32_t)t0);
+    m.launches += 1;
+    if (h->max_graph_log < 0) {
+        sweep_graph(h, 0);
+        const int64_t per_sweep = std::max<int64_t>(1, h->graph_kernels[0] - 1);
+        int k = 0;
+        while (k < kMaxGraphLog && ((int64_t)2 << k) * per_sweep <= kMaxGraphNodes) ++k;
+        h->max_graph_log = k;
+    }
+    int64_t done = 0;
+    for (int k = h->max_graph_log; k >= 0; --k) {
+        const int64_t g = int64_t(1) << k;
+        while (len - done >= g) {
+            sg::check_cuda(cudaGraphLaunch(sweep_graph(h, k), h->stream), "cudaGraphLaunch");
+            m.launches += h->graph_kernels[k];
+            done += g;
+        }
+    }
 }
 
 static void require_attached(sg_handle h) {
@@ -169,7 +241,7 @@ int sg_sweep(sg_handle h, int64_t n) {
             int64_t stop = end;
             if (h->next_tw < h->tw.size()) stop = std::min(stop, h->tw[h->next_tw]);
             if (h->next_tm < h->tm.size()) stop = std::min(stop, h->tm[h->next_tm]);
-            for (int64_t t = h->tau; t < stop; ++t) m.sweep((uint32_t)t, h->stream);
+            run_sweeps(h, h->tau, stop - h->tau);
             sg::check_cuda(cudaGetLastError(), "sweep launch");
             h->tau = stop;
             events_at_tau(h);

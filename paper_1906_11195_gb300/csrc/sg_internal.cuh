@@ -82,14 +82,16 @@ struct VbCountJob {
 
 // launch wrappers (vb_kernels.cu); each returns the number of kernel launches queued
 int vb_packed_init(const VbPackedDev& d, cudaStream_t st);
+// sweep index t = *clock + t_off (the clock lives in device memory so that captured CUDA graphs
+// can be replayed at any time)
 int vb_packed_colour(const VbPackedDev& d, uint32_t slice_begin, uint32_t slice_end,
-                     uint32_t t, cudaStream_t st);
+                     const uint32_t* clock, uint32_t t_off, cudaStream_t st);
 int vb_packed_snapshot(const VbPackedDev& d, int w, cudaStream_t st);
 int vb_packed_count(const VbPackedDev& d, const VbCountJob& job, cudaStream_t st);
 
 int vb_plain_init(const VbPlainDev& d, cudaStream_t st);
-int vb_plain_colour(const VbPlainDev& d, int32_t v_begin, int32_t v_end, uint32_t t,
-                    cudaStream_t st);
+int vb_plain_colour(const VbPlainDev& d, int32_t v_begin, int32_t v_end, const uint32_t* clock,
+                    uint32_t t_off, cudaStream_t st);
 int vb_plain_snapshot(const VbPlainDev& d, int w, cudaStream_t st);
 int vb_plain_count(const VbPlainDev& d, const VbCountJob& job, cudaStream_t st);
 

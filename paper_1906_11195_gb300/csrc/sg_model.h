@@ -40,8 +40,8 @@ public:
     virtual size_t workspace_bytes() const = 0;
     // copy the instance into ws, draw the initial spins, zero the counters (synchronous)
     virtual void attach(char* ws, cudaStream_t st) = 0;
-    // one sweep with sweep index t (queued)
-    virtual void sweep(uint32_t t, cudaStream_t st) = 0;
+    // one sweep with sweep index *clock_dev + t_off (queued; also used under stream capture)
+    virtual void sweep(uint32_t t_off, cudaStream_t st) = 0;
     // snapshot w <- current spins
     virtual void snapshot(int w, cudaStream_t st) = 0;
     // scheduled measurement column u at time tau (snapshots with tw <= tau exist)
@@ -61,6 +61,7 @@ public:
     virtual int device_status(cudaStream_t st) { (void)st; return 0; }
 
     int n_inst = 1, R = 1, L = 1;
+    uint32_t* clock_dev = nullptr;  // device word holding the index of the next sweep
     std::vector<int64_t> tw, tm;
     int64_t launches = 0;
 };

@@ -1,15 +1,347 @@
-// sg_sk.cu -- Sherrington-Kirkpatrick model, host side.
+// sg_sk.cu -- Sherrington-Kirkpatrick model, host side: validation, padding, threshold tables,
+// tensor maps for the tensor-core field update, launch sequence and measurement bookkeeping.
+//
+// Eq. 1 with the binary couplings of SI section 1: J_ij = +-1 symmetric, J_ii = 0, energy scale
+// 1/sqrt(N) folded into the acceptance table.  Spins are updated in the fixed order i = 0..N-1
+// (SI section 1); the blocked kernel reproduces that order exactly (see sk_kernels.cu).
+#include <cudaTypedefs.h>
+#include <math.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
 #include "../../include/sg.h"
+#include "sg_internal.cuh"
 #include "sg_model.h"
+#include "sk_internal.cuh"
 
 namespace sg {
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        check_cuda(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                     cudaEnableDefault, &q),
+                   "cudaGetDriverEntryPointByVersion(cuTensorMapEncodeTiled)");
+        if (q != cudaDriverEntryPointSuccess || !p) fail(SG_ECUDA, "cuTensorMapEncodeTiled unavailable");
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+void make_map_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer,
+                 uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
+    const cuuint64_t dims[2] = {inner, outer};
+    const cuuint64_t strides[1] = {row_bytes};
+    const cuuint32_t box[2] = {box_inner, box_outer};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUtensorMapSwizzle sw =
+        box_inner == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    const CUresult r = get_encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base),
+                                       dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) fail(SG_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+}
+
+class SkModel : public Model {
+public:
+    SkModel(int n, const int8_t* J, int n_replicas, const double* temps, uint64_t seed, int kernel,
+            int block, const std::vector<int64_t>& tw_, const std::vector<int64_t>& tm_) {
+        if (kernel != SG_SK_PLAIN && kernel != SG_SK_BLOCKED) fail(SG_EINVAL, "unknown SK kernel");
+        if (n < 2 || n > 32768) fail(SG_EINVAL, "SK needs 2 <= n <= 32768");
+        if (!J || !temps) fail(SG_EINVAL, "null array");
+        if (n_replicas < 1) fail(SG_EINVAL, "n_replicas must be >= 1");
+        kernel_ = kernel;
+        n_ = n;
+        R = n_replicas;
+        L = 1;
+        n_inst = 1;
+        tw = tw_;
+        tm = tm_;
+        seed_ = seed;
+        if (kernel == SG_SK_BLOCKED) {
+            if (!(block == 64 || block == 128 || block == 256 || block == 512))
+                fail(SG_EINVAL, "block must be 64, 128, 256 or 512");
+            if (R % 16) fail(SG_EINVAL, "blocked SK needs a multiple of 16 replicas");
+            if (R > 128 && R % 128) fail(SG_EINVAL, "more than 128 replicas must be a multiple of 128");
+            B_ = block;
+            kw_ = block >= 128 ? 128 : 64;
+            NT_ = R <= 128 ? R : 128;
+            const int unit = std::max(128, B_);
+            Np_ = (n + unit - 1) / unit * unit;
+        } else {
+            Np_ = (n + 127) / 128 * 128;
+            if (sk_plain_smem_bytes(Np_) > 227 * 1024) fail(SG_EINVAL, "n too large for the plain SK kernel");
+        }
+        // couplings
+        const int words = Np_ / 32;
+        h_J8_.assign((size_t)Np_ * Np_, 0);
+        h_Jbits_.assign((size_t)Np_ * words, 0);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                const int8_t v = J[(size_t)i * n + j];
+                if (i == j) {
+                    if (v != 0) fail(SG_EINVAL, "J_ii must be 0");
+                    continue;
+                }
+                if (v != 1 && v != -1) fail(SG_EINVAL, "off-diagonal J must be +-1");
+                if (v != J[(size_t)j * n + i]) fail(SG_EINVAL, "J must be symmetric");
+                h_J8_[(size_t)i * Np_ + j] = v > 0 ? 0x38 : 0xB8;
+                if (v < 0) h_Jbits_[(size_t)i * words + j / 32] |= 1u << (j & 31);
+            }
+        // threshold tables, one per distinct temperature
+        std::map<double, int> idx;
+        for (int r = 0; r < R; ++r) {
+            const double T = temps[r];
+            if (!(T >= 0.0)) fail(SG_EINVAL, "temperature must be >= 0 (or +inf)");
+            auto it = idx.find(T);
+            if (it == idx.end()) {
+                const int k0 = (int)idx.size();
+                idx[T] = k0;
+                const double beta = 1.0 / T;
+                const size_t off = h_thr_.size();
+                h_thr_.resize(off + n);
+                h_thr_[off] = 0xFFFFFFFFu;
+                for (int k = 1; k < n; ++k)
+                    h_thr_[off + k] = metropolis_threshold(-(2.0 * beta * k) / sqrt((double)n));
+                for (int k = 1; k < n; ++k)
+                    if (h_thr_[off + k] > h_thr_[off + k - 1]) fail(SG_EINVAL, "threshold table not monotone");
+                it = idx.find(T);
+            }
+            h_tidx_.push_back(it->second);
+            h_coef_.push_back((float)(sqrt((double)n) * T / 2.0));
+        }
+    }
+
+    size_t workspace_bytes() const override {
+        Carver c;
+        const_cast<SkModel*>(this)->carve(c);
+        return c.off;
+    }
+
+    void attach(char* ws, cudaStream_t st) override {
+        Carver c;
+        c.base = ws;
+        carve(c);
+        auto up = [&](void* dst, const void* src, size_t bytes) {
+            if (bytes) check_cuda(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), "H2D copy");
+        };
+        up((void*)d_.Jbits, h_Jbits_.data(), h_Jbits_.size() * 4);
+        up((void*)d_.J8, h_J8_.data(), h_J8_.size());
+        up((void*)d_.thr, h_thr_.data(), h_thr_.size() * 4);
+        up((void*)d_.temp_index, h_tidx_.data(), h_tidx_.size() * 4);
+        up((void*)d_.coef, h_coef_.data(), h_coef_.size() * 4);
+        check_cuda(cudaMemsetAsync(d_.H, 0, (size_t)R * Np_ * 4, st), "memset");
+        check_cuda(cudaMemsetAsync(d_.err, 0, 4, st), "memset");
+        check_cuda(cudaMemsetAsync(dC_, 0, nC() * 8, st), "memset");
+        check_cuda(cudaMemsetAsync(dQ_, 0, nQ() * 8, st), "memset");
+        check_cuda(cudaMemsetAsync(dE_, 0, nE() * 8, st), "memset");
+        launches += sk_init(d_, st);
+        if (kernel_ == SG_SK_BLOCKED) {
+            if (sk_field_prepare() != 0) fail(SG_ECUDA, "cannot raise the field kernel's shared memory limit");
+            make_map_2d(&mapJ_, d_.J8, Np_, Np_, Np_, kw_, 128);
+            make_map_2d(&mapD_, d_.D, Np_, R, Np_, kw_, NT_);
+            // initial fields h = J s, one block of columns at a time (D holds s)
+            for (int b0 = 0; b0 < Np_; b0 += B_)
+                launches += sk_field_update(d_, mapJ_, mapD_, b0, B_, kw_, NT_, 1, st);
+        } else {
+            if (sk_plain_prepare() != 0) fail(SG_ECUDA, "cannot raise the plain kernel's shared memory limit");
+            // the plain path computes its initial fields with the same GEMM-free rule: h = J s
+            fields_direct(st);
+        }
+        check_cuda(cudaGetLastError(), "init launch");
+        check_cuda(cudaStreamSynchronize(st), "attach");
+        if (device_status(st)) fail(SG_ETIMEOUT, "device wait expired during initialisation");
+    }
+
+    void sweep(uint32_t t_off, cudaStream_t st) override {
+        if (kernel_ == SG_SK_PLAIN) {
+            launches += sk_plain_sweep(d_, clock_dev, t_off, st);
+            return;
+        }
+        for (int b0 = 0; b0 < n_; b0 += B_) {
+            if (sk_inblock(d_, b0, B_, clock_dev, t_off, st) < 0) fail(SG_EINVAL, "unsupported block size");
+            ++launches;
+            launches += sk_field_update(d_, mapJ_, mapD_, b0, B_, kw_, NT_, 2, st);
+        }
+    }
+
+    void snapshot(int w, cudaStream_t st) override { launches += sk_snapshot(d_, w, st); }
+
+    void measure_scheduled(int u, int64_t tau, cudaStream_t st) override {
+        const int64_t ntw = (int64_t)tw.size(), ntm = (int64_t)tm.size();
+        int active = 0;
+        while (active < (int)ntw && tw[active] <= tau) ++active;
+        launches += sk_measure(d_, active, dC_ + u, ntw * ntm, ntm, R >= 2 ? dQ_ + u : nullptr, ntm,
+                               dE_ + u, ntm, st);
+    }
+
+    void measure_now(int64_t tau, cudaStream_t st) override {
+        const int64_t ntw = (int64_t)tw.size();
+        int active = 0;
+        while (active < (int)ntw && tw[active] <= tau) ++active;
+        check_cuda(cudaMemsetAsync(mC_, 0, nmC() * 8, st), "memset");
+        launches += sk_measure(d_, active, mC_, ntw, 1, R >= 2 ? mQ_ : nullptr, 1, mE_, 1, st);
+    }
+
+    void read_scheduled(int64_t tau, int64_t* C, int64_t* q, int64_t* E, cudaStream_t st) override {
+        std::vector<int64_t> c(nC()), qq(nQ()), e(nE());
+        down(c.data(), dC_, c.size() * 8, st);
+        down(qq.data(), dQ_, qq.size() * 8, st);
+        down(e.data(), dE_, e.size() * 8, st);
+        check_cuda(cudaStreamSynchronize(st), "read results");
+        const int64_t ntw = (int64_t)tw.size(), ntm = (int64_t)tm.size();
+        for (int r = 0; r < R; ++r)
+            for (int64_t u = 0; u < ntm; ++u) {
+                const bool done = tm[u] <= tau;
+                for (int64_t w = 0; w < ntw; ++w) {
+                    const int64_t k = ((int64_t)r * ntw + w) * ntm + u;
+                    C[k] = (done && tw[w] <= tm[u]) ? n_ - 2 * c[k] : 0;
+                }
+                E[(int64_t)r * ntm + u] = done ? e[(int64_t)r * ntm + u] : 0;
+                if (r < R / 2) q[(int64_t)r * ntm + u] = done ? n_ - 2 * qq[(int64_t)r * ntm + u] : 0;
+            }
+    }
+
+    void read_now(int64_t tau, int64_t* C, int64_t* q, int64_t* E, cudaStream_t st) override {
+        std::vector<int64_t> c(nmC()), qq(nmQ()), e(nmE());
+        down(c.data(), mC_, c.size() * 8, st);
+        down(qq.data(), mQ_, qq.size() * 8, st);
+        down(e.data(), mE_, e.size() * 8, st);
+        check_cuda(cudaStreamSynchronize(st), "read measurement");
+        const int64_t ntw = (int64_t)tw.size();
+        for (int r = 0; r < R; ++r) {
+            for (int64_t w = 0; w < ntw; ++w)
+                C[r * ntw + w] = tw[w] <= tau ? n_ - 2 * c[r * ntw + w] : 0;
+            E[r] = e[r];
+            if (r < R / 2) q[r] = n_ - 2 * qq[r];
+        }
+    }
+
+    size_t spins_bytes() const override { return (size_t)R * n_; }
+
+    void get_spins(void* dst, cudaStream_t st) override {
+        const int words = Np_ / 32;
+        std::vector<uint32_t> S((size_t)R * words);
+        down(S.data(), d_.S, S.size() * 4, st);
+        check_cuda(cudaStreamSynchronize(st), "read spins");
+        int8_t* out = static_cast<int8_t*>(dst);
+        for (int r = 0; r < R; ++r)
+            for (int i = 0; i < n_; ++i)
+                out[(size_t)r * n_ + i] = ((S[(size_t)r * words + i / 32] >> (i & 31)) & 1u) ? -1 : 1;
+    }
+
+    std::vector<uint32_t> thresholds() const override {
+        std::vector<uint32_t> t((size_t)R * n_);
+        for (int r = 0; r < R; ++r)
+            std::copy(h_thr_.begin() + (size_t)h_tidx_[r] * n_, h_thr_.begin() + (size_t)(h_tidx_[r] + 1) * n_,
+                      t.begin() + (size_t)r * n_);
+        return t;
+    }
+
+    std::vector<std::pair<void*, size_t>> state_regions() override {
+        const size_t sw = (size_t)R * (Np_ / 32) * 4;
+        return {{d_.S, sw}, {d_.H, (size_t)R * Np_ * 4}, {d_.snap, tw.size() * sw},
+                {dC_, nC() * 8}, {dQ_, nQ() * 8}, {dE_, nE() * 8}};
+    }
+
+    int device_status(cudaStream_t st) override {
+        int v = 0;
+        if (d_.err) {
+            check_cuda(cudaMemcpyAsync(&v, d_.err, 4, cudaMemcpyDeviceToHost, st), "status copy");
+            check_cuda(cudaStreamSynchronize(st), "status");
+        }
+        return v;
+    }
+
+private:
+    size_t nC() const { return (size_t)R * tw.size() * tm.size(); }
+    size_t nQ() const { return (size_t)(R / 2) * tm.size(); }
+    size_t nE() const { return (size_t)R * tm.size(); }
+    size_t nmC() const { return (size_t)R * tw.size(); }
+    size_t nmQ() const { return (size_t)(R / 2); }
+    size_t nmE() const { return (size_t)R; }
+
+    static void down(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+        if (bytes) check_cuda(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st), "D2H copy");
+    }
+
+    void fields_direct(cudaStream_t st);
+
+    void carve(Carver& c) {
+        const int words = Np_ / 32;
+        clock_dev = c.take<uint32_t>(1);
+        d_.Jbits = c.take<uint32_t>(h_Jbits_.size());
+        d_.J8 = c.take<uint8_t>(h_J8_.size());
+        d_.thr = c.take<uint32_t>(h_thr_.size());
+        d_.temp_index = c.take<int32_t>(h_tidx_.size());
+        d_.coef = c.take<float>(h_coef_.size());
+        d_.S = c.take<uint32_t>((size_t)R * words);
+        d_.D = c.take<uint8_t>((size_t)R * Np_);
+        d_.H = c.take<int32_t>((size_t)R * Np_);
+        d_.snap = c.take<uint32_t>((size_t)R * words * tw.size());
+        d_.err = c.take<int>(1);
+        d_.seed = seed_;
+        d_.N = n_;
+        d_.Np = Np_;
+        d_.R = R;
+        dC_ = c.take<int64_t>(nC());
+        dQ_ = c.take<int64_t>(nQ());
+        dE_ = c.take<int64_t>(nE());
+        mC_ = c.take<int64_t>(nmC());
+        mQ_ = c.take<int64_t>(nmQ());
+        mE_ = c.take<int64_t>(nmE());
+    }
+
+    int kernel_ = SG_SK_BLOCKED;
+    int n_ = 0, Np_ = 0, B_ = 128, kw_ = 128, NT_ = 128;
+    uint64_t seed_ = 0;
+    std::vector<uint8_t> h_J8_;
+    std::vector<uint32_t> h_Jbits_, h_thr_;
+    std::vector<int32_t> h_tidx_;
+    std::vector<float> h_coef_;
+    SkDev d_{};
+    CUtensorMap mapJ_{}, mapD_{};
+    int64_t *dC_ = nullptr, *dQ_ = nullptr, *dE_ = nullptr;
+    int64_t *mC_ = nullptr, *mQ_ = nullptr, *mE_ = nullptr;
+};
+
+// h_i = sum_j J_ij s_j on CUDA cores (initial fields of the plain path)
+__global__ void k_sk_fields_direct(SkDev d) {
+    const int r = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.Np) return;
+    const int words = d.Np / 32;
+    const uint32_t* S = d.S + (int64_t)r * words;
+    const uint8_t* row = d.J8 + (int64_t)i * d.Np;
+    int acc = 0;
+    for (int j = 0; j < d.N; ++j) {
+        const uint8_t b = row[j];
+        const int J = b == 0x38 ? 1 : (b == 0xB8 ? -1 : 0);
+        const int s = ((S[j >> 5] >> (j & 31)) & 1u) ? -1 : 1;
+        acc += J * s;
+    }
+    d.H[(int64_t)r * d.Np + i] = acc;
+}
+
+void SkModel::fields_direct(cudaStream_t st) {
+    dim3 grid((unsigned)((Np_ + 127) / 128), (unsigned)R);
+    k_sk_fields_direct<<<grid, 128, 0, st>>>(d_);
+    ++launches;
+}
+
+}  // namespace
 
 Model* make_sk_model(int n, const int8_t* J, int n_replicas, const double* temps, uint64_t seed,
                      int kernel, int block, const std::vector<int64_t>& tw,
                      const std::vector<int64_t>& tm) {
-    (void)n; (void)J; (void)n_replicas; (void)temps; (void)seed; (void)kernel; (void)block;
-    (void)tw; (void)tm;
-    fail(SG_EINVAL, "SK model not available in this build");
+    return new SkModel(n, J, n_replicas, temps, seed, kernel, block, tw, tm);
 }
 
 }  // namespace sg

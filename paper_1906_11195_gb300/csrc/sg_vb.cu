@@ -183,13 +183,15 @@ public:
         check_cuda(cudaStreamSynchronize(st), "attach");
     }
 
-    void sweep(uint32_t t, cudaStream_t st) override {
+    void sweep(uint32_t t_off, cudaStream_t st) override {
         if (kernel_ == SG_VB_PACKED) {
             for (size_t c = 0; c + 1 < colour_slice_.size(); ++c)
-                launches += vb_packed_colour(pk_, colour_slice_[c], colour_slice_[c + 1], t, st);
+                launches += vb_packed_colour(pk_, colour_slice_[c], colour_slice_[c + 1], clock_dev,
+                                             t_off, st);
         } else {
             for (size_t c = 0; c + 1 < colour_begin_.size(); ++c)
-                launches += vb_plain_colour(pl_, colour_begin_[c], colour_begin_[c + 1], t, st);
+                launches += vb_plain_colour(pl_, colour_begin_[c], colour_begin_[c + 1], clock_dev,
+                                            t_off, st);
         }
     }
 
@@ -359,6 +361,7 @@ private:
     }
 
     void carve(Carver& c) {
+        clock_dev = c.take<uint32_t>(1);
         d_thr_ = c.take<uint32_t>(thr_.size());
         if (kernel_ == SG_VB_PACKED) {
             pk_.vinfo = c.take<uint32_t>(h_vinfo_.size());

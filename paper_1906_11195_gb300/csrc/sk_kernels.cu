@@ -1,0 +1,484 @@
+// sk_kernels.cu -- Sherrington-Kirkpatrick Metropolis kernels for sm_103a.
+//
+// Model (Eq. 1 with the binary couplings of SI section 1): H = -sum_{i<j} J_ij s_i s_j / sqrt(N),
+// J_ij = +-1.  With the local field h_i = sum_j J_ij s_j, flipping s_i costs dE = 2k/sqrt(N),
+// k = s_i h_i; Metropolis accepts iff k <= 0 or r32 < thr[k].  Spins are visited in the fixed
+// order i = 0..N-1 (SI section 1).  Because thr[k] is non-increasing, the accepted set for one
+// random number is a prefix {k <= K*}, K* = max{k : k = 0 or r32 < thr[k]}.
+//
+// Blocked sweep (exact reformulation of the sequential order): the spins are cut into blocks
+// of B.  For block b:
+//   1. in-block kernel: every replica (one warp each) runs the B sequential decisions of the
+//      block on its fields h (exact as of the start of the block) and records the changes
+//      D_j = (s_j' - s_j)/2 in {-1, 0, +1}.  Inside a 32-spin chunk the warp finds the next flip
+//      with a ballot: lanes at or after the resolved prefix evaluate their decision given the
+//      flips found so far (bit-packed couplings, popcount corrections); the first tentative
+//      flip is final, is added, and the rest is re-evaluated.  The number of rounds is the
+//      number of flips in the chunk plus one.
+//   2. field kernel: H[:, R] += 2 J[:, block] D[block, R] for every row, as a tcgen05 tensor-core
+//      GEMM with e4m3 operands (J = +-1, 0 on the diagonal and in padding; D in {-1,0,1}: all
+//      exact) and an FP32 accumulator in tensor memory that starts from zero for every block,
+//      so partial sums stay below B in magnitude and are exact; the epilogue adds 2*acc to the
+//      int32 fields.  Integer arithmetic makes the result identical to the sequential order.
+#include <cuda.h>
+
+#include "sg_internal.cuh"
+#include "sk_internal.cuh"
+
+namespace sg {
+
+// --------------------------------------------------------------------------------------------
+// K* for a replica: largest k in [0, N-1] with k == 0 or r32 < thr[k].  A logarithmic estimate
+// (thr[k] ~ 2^32 exp(-k / coef), coef = sqrt(N) T / 2) is corrected exactly on the table.
+// --------------------------------------------------------------------------------------------
+__device__ __forceinline__ int sk_kstar(uint32_t r32, const uint32_t* __restrict__ thr, int n,
+                                        float coef) {
+    const float u = ((float)r32 + 0.5f) * 2.3283064365386963e-10f;
+    const float est = -__logf(u) * coef;
+    int k;
+    if (!(est < (float)(n - 1))) k = n - 1;
+    else if (!(est > 0.f)) k = 0;
+    else k = (int)est;
+    while (k + 1 <= n - 1 && r32 < __ldg(thr + k + 1)) ++k;
+    while (k >= 1 && !(r32 < __ldg(thr + k))) --k;
+    return k;
+}
+
+__device__ __forceinline__ uint8_t e4m3_of_sign(int v) {  // v in {-1, 0, 1}
+    return v > 0 ? (uint8_t)0x38 : (v < 0 ? (uint8_t)0xB8 : (uint8_t)0x00);
+}
+
+// --------------------------------------------------------------------------------------------
+// initial spins (quench) and D = s for the initial field computation
+// --------------------------------------------------------------------------------------------
+__global__ void k_sk_init(SkDev d) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over R * Np
+    const int64_t total = (int64_t)d.R * d.Np;
+    if (idx >= total) return;  // total is a multiple of 32: whole warps exit together
+    const int r = (int)(idx / d.Np);
+    const int i = (int)(idx % d.Np);
+    int s = 1;
+    if (i < d.N) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)i, 0u, (uint32_t)r, 1u),
+                                      (uint32_t)d.seed, (uint32_t)(d.seed >> 32));
+        s = (w.x & 1u) ? -1 : 1;
+    }
+    d.D[(int64_t)r * d.Np + i] = i < d.N ? e4m3_of_sign(s) : (uint8_t)0;
+    const uint32_t bits = __ballot_sync(0xFFFFFFFFu, s < 0);
+    if ((threadIdx.x & 31) == 0) d.S[(int64_t)r * (d.Np / 32) + i / 32] = bits;
+}
+
+int sk_init(const SkDev& d, cudaStream_t st) {
+    const int64_t total = (int64_t)d.R * d.Np;
+    k_sk_init<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(d);
+    return 1;
+}
+
+// --------------------------------------------------------------------------------------------
+// in-block sequential update, one warp per replica
+// --------------------------------------------------------------------------------------------
+template <int NC>
+__global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0,
+                                                    const uint32_t* __restrict__ clock,
+                                                    uint32_t t_off) {
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= d.R) return;
+    const uint32_t t = __ldg(clock) + t_off;
+    const int words = d.Np / 32;
+    const int wb = b0 / 32;
+    const uint32_t* thr = d.thr + (int64_t)d.temp_index[r] * d.N;
+    const float coef = d.coef[r];
+    int h[NC];
+    int kst[NC];
+    uint32_t sw[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int i = b0 + 32 * c + lane;
+        h[c] = d.H[(int64_t)r * d.Np + i];
+        sw[c] = d.S[(int64_t)r * words + wb + c];
+        if (i < d.N) {
+            const uint4 rnd = philox4x32_10(make_uint4((uint32_t)i, t, (uint32_t)(r >> 2), 0u),
+                                            (uint32_t)d.seed, (uint32_t)(d.seed >> 32));
+            kst[c] = sk_kstar(uint4_word(rnd, r & 3), thr, d.N, coef);
+        } else {
+            kst[c] = -0x7FFFFFFF;  // padding never flips
+        }
+    }
+    const uint32_t* Jb = d.Jbits;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int i = b0 + 32 * c + lane;
+        const uint32_t sbit = (sw[c] >> lane) & 1u;
+        const int x = sbit ? -h[c] : h[c];
+        const uint32_t neg = Jb[(int64_t)i * words + wb + c] ^ sw[c] ^ (sbit ? 0xFFFFFFFFu : 0u);
+        uint32_t F = 0;
+        int resolved = 0;
+        while (resolved < 32) {
+            const int cur = x - 2 * (__popc(F) - 2 * __popc(F & neg));
+            const bool tent = (lane >= resolved) && (cur <= kst[c]);
+            const uint32_t bm = __ballot_sync(0xFFFFFFFFu, tent);
+            if (bm == 0u) break;
+            const int p = __ffs(bm) - 1;
+            F |= 1u << p;
+            resolved = p + 1;
+        }
+        const uint32_t nsw = sw[c] ^ F;
+        // changes D_i = (s' - s)/2 for the field GEMM: -s_old where flipped
+        const int dval = ((F >> lane) & 1u) ? (sbit ? 1 : -1) : 0;
+        d.D[(int64_t)r * d.Np + i] = e4m3_of_sign(dval);
+        if (lane == 0) d.S[(int64_t)r * words + wb + c] = nsw;
+        // fields of the later rows of this block: h += 2 sum_{j in F} J_ij s_j'
+        if (F) {
+            const int pf = __popc(F);
+#pragma unroll
+            for (int c2 = c + 1; c2 < NC; ++c2) {
+                const int i2 = b0 + 32 * c2 + lane;
+                const uint32_t m = Jb[(int64_t)i2 * words + wb + c] ^ nsw;
+                h[c2] += 2 * (pf - 2 * __popc(F & m));
+            }
+        }
+        sw[c] = nsw;
+    }
+}
+
+int sk_inblock(const SkDev& d, int b0, int B, const uint32_t* clock, uint32_t t_off,
+               cudaStream_t st) {
+    const unsigned nb = (unsigned)((d.R + 7) / 8);
+    switch (B / 32) {
+        case 1: k_sk_inblock<1><<<nb, 256, 0, st>>>(d, b0, clock, t_off); break;
+        case 2: k_sk_inblock<2><<<nb, 256, 0, st>>>(d, b0, clock, t_off); break;
+        case 4: k_sk_inblock<4><<<nb, 256, 0, st>>>(d, b0, clock, t_off); break;
+        case 8: k_sk_inblock<8><<<nb, 256, 0, st>>>(d, b0, clock, t_off); break;
+        case 16: k_sk_inblock<16><<<nb, 256, 0, st>>>(d, b0, clock, t_off); break;
+        default: return -1;
+    }
+    return 1;
+}
+
+// --------------------------------------------------------------------------------------------
+// tcgen05 / TMA / mbarrier helpers (inline PTX)
+// --------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: false if the barrier phase did not complete within max_iter polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, uint32_t max_iter) {
+    for (uint32_t it = 0; it < max_iter; ++it)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// shared-memory matrix descriptor, K-major operand in the 128B (kw = 128) or 64B (kw = 64)
+// swizzled layout written by TMA: 8-row groups are kw*8 bytes apart
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, int kw) {
+    const uint64_t sbo = (uint64_t)(kw * 8) >> 4;
+    const uint64_t layout = kw == 128 ? 2ull : 4ull;
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | (sbo << 32) | (1ull << 46) |
+           (layout << 61);
+}
+
+// --------------------------------------------------------------------------------------------
+// field update GEMM: H[n0.., m0..m0+127] += scale * (J[m0.., b0..b0+B) . D[n0.., b0..b0+B)^T)
+// One CTA (4 warps) per 128-row x NT-replica tile; one elected thread issues TMA and MMA.
+// --------------------------------------------------------------------------------------------
+constexpr uint32_t kWaitPolls = 1u << 24;
+
+__global__ void __launch_bounds__(128) k_sk_field_mma(const __grid_constant__ CUtensorMap mapJ,
+                                                      const __grid_constant__ CUtensorMap mapD,
+                                                      SkDev d, int b0, int B, int kw, int NT,
+                                                      int scale) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // 1024-byte aligned operand area
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int nchunks = B / kw;
+    uint8_t* sA = smem;                                  // nchunks x [128][kw]
+    uint8_t* sB = smem + (size_t)nchunks * 128 * kw;     // nchunks x [NT][kw]
+    uint64_t* bars = (uint64_t*)(sB + (size_t)nchunks * NT * kw);
+    uint32_t* tslot = (uint32_t*)(bars + 2);
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * 128;
+    const int n0 = blockIdx.y * NT;
+    const uint32_t ncols = NT <= 32 ? 32u : (NT <= 64 ? 64u : (NT <= 128 ? 128u : 256u));
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(tslot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    bool ok = true;
+    if (tid == 0) {
+        const uint32_t bytes = (uint32_t)(nchunks * (128 + NT) * kw);
+        mbar_expect_tx(&bars[0], bytes);
+        for (int kc = 0; kc < nchunks; ++kc) {
+            tma_load_2d(sA + (size_t)kc * 128 * kw, &mapJ, b0 + kc * kw, m0, &bars[0]);
+            tma_load_2d(sB + (size_t)kc * NT * kw, &mapD, b0 + kc * kw, n0, &bars[0]);
+        }
+        ok = mbar_wait(&bars[0], 0, kWaitPolls);
+        if (ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // instruction descriptor: D = F32, A = B = E4M3, both K-major, M = 128, N = NT
+            const uint32_t idesc = (1u << 4) | ((uint32_t)(NT >> 3) << 17) | ((128u >> 4) << 24);
+            int first = 1;
+            for (int kc = 0; kc < nchunks; ++kc)
+                for (int ks = 0; ks < kw / 32; ++ks) {
+                    const uint64_t ad = smem_desc(smem_addr(sA + (size_t)kc * 128 * kw) + ks * 32, kw);
+                    const uint64_t bd = smem_desc(smem_addr(sB + (size_t)kc * NT * kw) + ks * 32, kw);
+                    const uint32_t acc = first ? 0u : 1u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
+                    first = 0;
+                }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_addr(&bars[1]))
+                : "memory");
+        } else {
+            atomicOr(d.err, 1);
+        }
+    }
+    ok = __syncthreads_and(ok);
+    if (ok) {
+        ok = mbar_wait(&bars[1], 0, kWaitPolls);
+        if (!ok) atomicOr(d.err, 2);
+    }
+    ok = __syncthreads_and(ok);
+    if (ok) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int row = m0 + 32 * warp + lane;
+        for (int c0 = 0; c0 < NT; c0 += 32) {
+            uint32_t v[32];
+            const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                  "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                  "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
+                  "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+                  "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+                  "=r"(v[30]), "=r"(v[31])
+                : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int ncol = NT - c0 < 32 ? NT - c0 : 32;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (j < ncol) {
+                    int* hp = d.H + (int64_t)(n0 + c0 + j) * d.Np + row;
+                    *hp += scale * __float2int_rn(__uint_as_float(v[j]));
+                }
+            }
+        }
+    } else if (tid == 0) {
+        // give any copies still in flight a bounded chance to land before the CTA exits
+        mbar_wait(&bars[0], 0, kWaitPolls);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
+                     : "memory");
+}
+
+size_t sk_field_smem_bytes(int B, int kw, int NT) {
+    const int nchunks = B / kw;
+    return 1024 + (size_t)nchunks * (128 + NT) * kw + 64;
+}
+
+int sk_field_update(const SkDev& d, const CUtensorMap& mapJ, const CUtensorMap& mapD, int b0,
+                    int B, int kw, int NT, int scale, cudaStream_t st) {
+    const size_t smem = sk_field_smem_bytes(B, kw, NT);
+    dim3 grid((unsigned)(d.Np / 128), (unsigned)(d.R / NT));
+    k_sk_field_mma<<<grid, 128, smem, st>>>(mapJ, mapD, d, b0, B, kw, NT, scale);
+    return 1;
+}
+
+int sk_field_prepare() {
+    const cudaError_t e = cudaFuncSetAttribute(k_sk_field_mma,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               200 * 1024);
+    return e == cudaSuccess ? 0 : -1;
+}
+
+// --------------------------------------------------------------------------------------------
+// plain kernel: one thread block per replica, spins in the fixed order, fields in shared memory
+// --------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_sk_plain_sweep(SkDev d, const uint32_t* clock,
+                                                        uint32_t t_off) {
+    const uint32_t t = *clock + t_off;
+    extern __shared__ int sh[];
+    int* h = sh;                          // [Np]
+    int* kst = sh + d.Np;                 // [Np]
+    uint32_t* sb = (uint32_t*)(kst + d.Np);  // [Np/32]
+    __shared__ int flip_sign;
+    const int r = blockIdx.x;
+    const int words = d.Np / 32;
+    const uint32_t* thr = d.thr + (int64_t)d.temp_index[r] * d.N;
+    for (int i = threadIdx.x; i < d.Np; i += blockDim.x) {
+        h[i] = d.H[(int64_t)r * d.Np + i];
+        if (i < d.N) {
+            const uint4 rnd = philox4x32_10(make_uint4((uint32_t)i, t, (uint32_t)(r >> 2), 0u),
+                                            (uint32_t)d.seed, (uint32_t)(d.seed >> 32));
+            kst[i] = sk_kstar(uint4_word(rnd, r & 3), thr, d.N, d.coef[r]);
+        }
+    }
+    for (int w = threadIdx.x; w < words; w += blockDim.x) sb[w] = d.S[(int64_t)r * words + w];
+    __syncthreads();
+    for (int i = 0; i < d.N; ++i) {
+        if (threadIdx.x == 0) {
+            const int s = ((sb[i >> 5] >> (i & 31)) & 1u) ? -1 : 1;
+            const bool flip = s * h[i] <= kst[i];
+            if (flip) sb[i >> 5] ^= 1u << (i & 31);
+            flip_sign = flip ? -s : 0;  // new spin value, or 0 for no flip
+        }
+        __syncthreads();
+        const int sn = flip_sign;
+        if (sn) {
+            const uint8_t* row = d.J8 + (int64_t)i * d.Np;
+            for (int j = threadIdx.x; j < d.Np; j += blockDim.x) {
+                const uint8_t b = row[j];
+                const int J = b == 0x38 ? 1 : (b == 0xB8 ? -1 : 0);
+                h[j] += 2 * J * sn;
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < d.Np; i += blockDim.x) d.H[(int64_t)r * d.Np + i] = h[i];
+    for (int w = threadIdx.x; w < words; w += blockDim.x) d.S[(int64_t)r * words + w] = sb[w];
+}
+
+size_t sk_plain_smem_bytes(int Np) { return (size_t)Np * 8 + (size_t)Np / 8; }
+
+int sk_plain_prepare() {
+    const cudaError_t e = cudaFuncSetAttribute(k_sk_plain_sweep,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               227 * 1024);
+    return e == cudaSuccess ? 0 : -1;
+}
+
+int sk_plain_sweep(const SkDev& d, const uint32_t* clock, uint32_t t_off, cudaStream_t st) {
+    k_sk_plain_sweep<<<(unsigned)d.R, 256, sk_plain_smem_bytes(d.Np), st>>>(d, clock, t_off);
+    return 1;
+}
+
+// --------------------------------------------------------------------------------------------
+// measurements: per replica, Hamming distances to snapshots, the pair overlap, and the energy
+//   diff_C[r][w] (w < n_active), diff_q[r/2] (even r), E[r] = sum_{i<j} J_ij s_i s_j
+// --------------------------------------------------------------------------------------------
+__device__ __forceinline__ long long block_sum(long long v, long long* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    long long tot = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    return tot;  // valid in thread 0
+}
+
+__global__ void k_sk_measure(SkDev d, int n_active, int64_t* cdst, int64_t c_stride_r,
+                             int64_t c_stride_w, int64_t* qdst, int64_t q_stride_p, int64_t* edst,
+                             int64_t e_stride_r) {
+    __shared__ long long red[32];
+    const int r = blockIdx.x;
+    const int words = d.Np / 32;
+    const uint32_t* S = d.S + (int64_t)r * words;
+    for (int w = 0; w < n_active; ++w) {
+        const uint32_t* P = d.snap + ((int64_t)w * d.R + r) * words;
+        long long acc = 0;
+        for (int k = threadIdx.x; k < words; k += blockDim.x) acc += __popc(S[k] ^ P[k]);
+        const long long tot = block_sum(acc, red);
+        if (threadIdx.x == 0) cdst[r * c_stride_r + w * c_stride_w] = tot;
+    }
+    if ((r & 1) == 0 && r + 1 < d.R && qdst) {
+        const uint32_t* S2 = S + words;
+        long long acc = 0;
+        for (int k = threadIdx.x; k < words; k += blockDim.x) acc += __popc(S[k] ^ S2[k]);
+        const long long tot = block_sum(acc, red);
+        if (threadIdx.x == 0) qdst[(r >> 1) * q_stride_p] = tot;
+    }
+    long long acc = 0;
+    for (int i = threadIdx.x; i < d.N; i += blockDim.x) {
+        const int s = ((S[i >> 5] >> (i & 31)) & 1u) ? -1 : 1;
+        acc += (long long)s * d.H[(int64_t)r * d.Np + i];
+    }
+    const long long tot = block_sum(acc, red);
+    if (threadIdx.x == 0) edst[r * e_stride_r] = tot / 2;
+}
+
+int sk_measure(const SkDev& d, int n_active, int64_t* cdst, int64_t c_stride_r,
+               int64_t c_stride_w, int64_t* qdst, int64_t q_stride_p, int64_t* edst,
+               int64_t e_stride_r, cudaStream_t st) {
+    k_sk_measure<<<(unsigned)d.R, 256, 0, st>>>(d, n_active, cdst, c_stride_r, c_stride_w, qdst,
+                                               q_stride_p, edst, e_stride_r);
+    return 1;
+}
+
+__global__ void k_copy_words(const uint4* __restrict__ src, uint4* __restrict__ dst, int64_t n16) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+int sk_snapshot(const SkDev& d, int w, cudaStream_t st) {
+    const int64_t words = (int64_t)d.R * (d.Np / 32);
+    const int64_t n16 = words / 4;
+    int64_t nb = (n16 + 255) / 256;
+    if (nb > 1024) nb = 1024;
+    if (nb < 1) nb = 1;
+    k_copy_words<<<(unsigned)nb, 256, 0, st>>>((const uint4*)d.S, (uint4*)(d.snap + w * words), n16);
+    return 1;
+}
+
+}  // namespace sg

@@ -121,7 +121,9 @@ __device__ __forceinline__ uint64_t bitslice_ge(const uint64_t (&p)[kPlanes], in
 
 template <int R>
 __global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_t slice_begin,
-                                                          uint32_t slice_end, uint32_t t) {
+                                                          uint32_t slice_end,
+                                                          const uint32_t* __restrict__ clock,
+                                                          uint32_t t_off) {
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t slice = slice_begin + warp;
@@ -139,6 +141,7 @@ __global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_
     const int deg = (int)(vi >> kDegShift);
     const uint32_t orig = vi & kOrigMask;
     const uint64_t seed = d.seeds[g];
+    const uint32_t t = __ldg(clock) + t_off;
 
     SpinWords<R> si = load_words<R>(S + slot * R);
 
@@ -175,16 +178,16 @@ __global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_
     store_words<R>(d.S + slot * R, si);
 }
 
-int vb_packed_colour(const VbPackedDev& d, uint32_t slice_begin, uint32_t slice_end, uint32_t t,
-                     cudaStream_t st) {
+int vb_packed_colour(const VbPackedDev& d, uint32_t slice_begin, uint32_t slice_end,
+                     const uint32_t* clock, uint32_t t_off, cudaStream_t st) {
     if (slice_end <= slice_begin) return 0;
     const uint32_t n = slice_end - slice_begin;
     const int bs = 256;
     const unsigned nb = (n + (bs / 32) - 1) / (bs / 32);
     switch (d.R) {
-        case 1: k_vb_packed_colour<1><<<nb, bs, 0, st>>>(d, slice_begin, slice_end, t); break;
-        case 2: k_vb_packed_colour<2><<<nb, bs, 0, st>>>(d, slice_begin, slice_end, t); break;
-        case 4: k_vb_packed_colour<4><<<nb, bs, 0, st>>>(d, slice_begin, slice_end, t); break;
+        case 1: k_vb_packed_colour<1><<<nb, bs, 0, st>>>(d, slice_begin, slice_end, clock, t_off); break;
+        case 2: k_vb_packed_colour<2><<<nb, bs, 0, st>>>(d, slice_begin, slice_end, clock, t_off); break;
+        case 4: k_vb_packed_colour<4><<<nb, bs, 0, st>>>(d, slice_begin, slice_end, clock, t_off); break;
         default: return -1;
     }
     return 1;
@@ -335,9 +338,11 @@ int vb_plain_init(const VbPlainDev& d, cudaStream_t st) {
     return 1;
 }
 
-__global__ void k_vb_plain_colour(VbPlainDev d, int32_t v0, int32_t nv, uint32_t t) {
+__global__ void k_vb_plain_colour(VbPlainDev d, int32_t v0, int32_t nv, const uint32_t* clock,
+                                  uint32_t t_off) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)nv * d.R * d.L) return;
+    const uint32_t t = *clock + t_off;
     const int32_t v = v0 + (int32_t)(idx % nv);
     const int32_t rk = (int32_t)(idx / nv);
     const int32_t r = rk / d.L, k = rk % d.L;
@@ -355,13 +360,13 @@ __global__ void k_vb_plain_colour(VbPlainDev d, int32_t v0, int32_t nv, uint32_t
     if (flip) s[v] = (int8_t)(-s[v]);
 }
 
-int vb_plain_colour(const VbPlainDev& d, int32_t v_begin, int32_t v_end, uint32_t t,
-                    cudaStream_t st) {
+int vb_plain_colour(const VbPlainDev& d, int32_t v_begin, int32_t v_end, const uint32_t* clock,
+                    uint32_t t_off, cudaStream_t st) {
     const int32_t nv = v_end - v_begin;
     if (nv <= 0) return 0;
     const int bs = 256;
     const int64_t n = (int64_t)nv * d.R * d.L;
-    k_vb_plain_colour<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(d, v_begin, nv, t);
+    k_vb_plain_colour<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(d, v_begin, nv, clock, t_off);
     return 1;
 }
 

@@ -91,3 +91,23 @@ def test_schedule_helper():
     tw, tm = sg_inputs.log_schedule([0, 1, 4], 10)
     assert list(tw) == [0, 1, 4]
     assert list(tm) == [0, 1, 2, 3, 4, 5, 6, 8, 9]
+
+
+def test_sk_create_and_validation_without_gpu(lib):
+    J = sg_inputs.sk_couplings(300, 1)
+    h = sg.sg_create_sk(J, 32, [0.4] * 32, 7, sg.SG_SK_BLOCKED, 128, [0, 3], [0, 3, 5])
+    assert sg.sg_workspace_bytes(h) > 384 * 384
+    assert sg.sg_result_shape(h) == (1, 32, 1, 2, 3)
+    thr = sg.sg_get_thresholds(h, 32 * 300).reshape(32, 300)
+    assert thr[0, 0] == 0xFFFFFFFF
+    assert thr[0, 1] == int(np.floor(2.0**32 * np.exp(-(2.0 / 0.4) / np.sqrt(300))))
+    sg.sg_destroy(h)
+    bad = J.copy()
+    bad[0, 1] = -bad[0, 1]
+    for args in [(bad, 32, sg.SG_SK_BLOCKED, 128),      # asymmetric
+                 (J, 20, sg.SG_SK_BLOCKED, 128),        # replicas not a multiple of 16
+                 (J, 32, sg.SG_SK_BLOCKED, 96),         # unsupported block
+                 (np.eye(300, dtype=np.int8), 32, sg.SG_SK_PLAIN, 0)]:  # nonzero diagonal
+        with pytest.raises(sg.SGError) as e:
+            sg.sg_create_sk(args[0], args[1], [0.4] * args[1], 1, args[2], args[3], [], [])
+        assert e.value.code == sg.SG_EINVAL

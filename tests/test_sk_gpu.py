@@ -1,0 +1,144 @@
+"""GPU parity of the Sherrington-Kirkpatrick kernels against the CPU oracle (bit-exact).
+
+The blocked kernel (in-block sequential update + tcgen05 e4m3 field GEMM) and the plain kernel
+must reproduce the oracle's sequential-order trajectory exactly: spins of every replica and every
+C, q, E count.  Block size, padding and replica tiling must not change any result.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import sg_inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+sg = None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    global sg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1906_11195_gb300 import _build
+    _build.build()
+    import paper_1906_11195_gb300 as m
+    sg = m
+
+
+def run_sk(J, temps, seed, kernel, block, sweeps, tw, tm):
+    run = sg.SKRun(J, temps, seed, kernel=kernel, block=block, tw=tw, tm=tm)
+    run.sweep(sweeps)
+    run.synchronize()
+    C, q, E = run.results()
+    spins = run.spins()
+    run.close()
+    return spins, C[0, :, 0], q[0, :, 0], E[0, :, 0]
+
+
+def check(J, temps, seed, sweeps, tw, tm, got, r_first=0, r_count=None):
+    spins, C, q, E = got
+    R = len(temps)
+    rc = R - r_first if r_count is None else r_count
+    ref = oracle.sk_run(J, temps, seed, sweeps, tw, tm, r_first=r_first, r_count=rc)
+    sl = slice(r_first, r_first + rc)
+    assert np.array_equal(spins[sl], ref["spins"])
+    assert np.array_equal(C[sl], ref["C"])
+    assert np.array_equal(E[sl], ref["E"])
+    if rc >= 2:
+        assert np.array_equal(q[r_first // 2:r_first // 2 + rc // 2], ref["q"])
+
+
+@pytest.mark.parametrize("n,R,block", [(256, 32, 64), (300, 16, 128), (1000, 32, 256),
+                                       (700, 48, 512), (129, 16, 64)])
+def test_blocked_matches_oracle(n, R, block):
+    J = sg_inputs.sk_couplings(n, 40 + n)
+    temps = [0.4] * (R // 2) + [0.6] * (R // 2)
+    tw, tm = sg_inputs.log_schedule([0, 3, 8], 24)
+    got = run_sk(J, temps, 5 + n, sg.SG_SK_BLOCKED, block, 24, tw, tm)
+    check(J, temps, 5 + n, 24, tw, tm, got)
+
+
+@pytest.mark.parametrize("n,R", [(200, 8), (333, 5), (64, 2)])
+def test_plain_matches_oracle(n, R):
+    J = sg_inputs.sk_couplings(n, 60 + n)
+    temps = [0.4 + 0.1 * r for r in range(R)]
+    tw, tm = sg_inputs.log_schedule([0, 3], 16)
+    got = run_sk(J, temps, 9, sg.SG_SK_PLAIN, 0, 16, tw, tm)
+    check(J, temps, 9, 16, tw, tm, got)
+
+
+def test_block_size_does_not_change_results():
+    n, R = 640, 32
+    J = sg_inputs.sk_couplings(n, 3)
+    temps = [0.5] * R
+    tw, tm = sg_inputs.log_schedule([0, 2], 12)
+    outs = [run_sk(J, temps, 2, sg.SG_SK_BLOCKED, b, 12, tw, tm) for b in (64, 128, 256, 512)]
+    outs.append(run_sk(J, temps, 2, sg.SG_SK_PLAIN, 0, 12, tw, tm))
+    for o in outs[1:]:
+        for x, y in zip(outs[0], o):
+            assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("T", [0.0, math.inf])
+def test_zero_and_infinite_temperature(T):
+    n, R = 384, 16
+    J = sg_inputs.sk_couplings(n, 12)
+    temps = [T] * R
+    tw, tm = sg_inputs.log_schedule([0, 1], 10)
+    got = run_sk(J, temps, 3, sg.SG_SK_BLOCKED, 128, 10, tw, tm)
+    check(J, temps, 3, 10, tw, tm, got)
+
+
+def test_thresholds_exported_match_oracle():
+    n = 512
+    J = sg_inputs.sk_couplings(n, 1)
+    temps = [0.4] * 8 + [0.6] * 8
+    run = sg.SKRun(J, temps, 1, kernel=sg.SG_SK_BLOCKED, block=128)
+    thr = run.thresholds()
+    assert np.array_equal(thr[0], oracle.sk_thresholds(0.4, n))
+    assert np.array_equal(thr[15], oracle.sk_thresholds(0.6, n))
+    run.close()
+
+
+def test_checkpoint_resume_is_bit_exact():
+    n, R = 512, 16
+    J = sg_inputs.sk_couplings(n, 21)
+    temps = [0.4] * R
+    tw, tm = sg_inputs.log_schedule([0, 4], 30)
+    straight = run_sk(J, temps, 4, sg.SG_SK_BLOCKED, 128, 30, tw, tm)
+    run = sg.SKRun(J, temps, 4, kernel=sg.SG_SK_BLOCKED, block=128, tw=tw, tm=tm)
+    run.sweep(11)
+    blob = run.save_state()
+    run.close()
+    run2 = sg.SKRun(J, temps, 4, kernel=sg.SG_SK_BLOCKED, block=128, tw=tw, tm=tm)
+    run2.load_state(blob)
+    run2.sweep(19)
+    C, q, E = run2.results()
+    assert np.array_equal(run2.spins(), straight[0])
+    assert np.array_equal(C[0, :, 0], straight[1]) and np.array_equal(E[0, :, 0], straight[3])
+    run2.close()
+
+
+# --------------------------------------------------------------------------------------------
+# full-size workload: N = 8192, 256 replicas sharing J, T = 0.4, B = 128
+# --------------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def sk_big():
+    return sg_inputs.sk_couplings(8192, 3)
+
+
+def test_full_size_matches_oracle_on_sampled_replicas(sk_big):
+    J = sk_big
+    R, sweeps = 256, 12
+    temps = [0.4] * R
+    tw, tm = sg_inputs.log_schedule([0, 3, 8], sweeps)
+    got = run_sk(J, temps, 1, sg.SG_SK_BLOCKED, 128, sweeps, tw, tm)
+    # replicas are independent chains: the oracle follows a few of them one by one
+    for r0 in (0, 2, 126, 254):
+        check(J, temps, 1, sweeps, tw, tm, got, r_first=r0, r_count=2)
+    spins, C, q, E = got
+    assert np.all(np.abs(C) <= 8192) and np.all((C - 8192) % 2 == 0)
