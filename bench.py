@@ -222,6 +222,55 @@ def run_profile_case(args):
     return 0
 
 
+SK_N, SK_R, SK_T, SK_B = 8192, 256, 0.4, 128
+
+
+def run_sk(args):
+    """SK workload (not the headline line): N = 8192, +-1 couplings, 256 replicas sharing J,
+    T = 0.4, block B = 128; one step = one sweep.  Prints one JSON line with the blocked
+    (tensor-core) and plain kernels' throughput."""
+    import torch
+
+    import paper_1906_11195_gb300 as sg
+    from paper_1906_11195_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    J = sg_inputs.sk_couplings(SK_N, 3)
+    stream = torch.cuda.current_stream()
+    out = {"metric": "spin updates/ns", "unit": "spin updates/ns",
+           "config": {"workload": f"sk_blocked_N{SK_N}_R{SK_R}_T{SK_T}_B{args.sk_block}"}}
+    run = sg.SKRun(J, [SK_T] * SK_R, 1, kernel=sg.SG_SK_BLOCKED, block=args.sk_block)
+    run.sweep(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = run.launches
+    e0.record(stream)
+    run.sweep(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    run.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = run.launches - l0
+    run.close()
+    flops = 2.0 * SK_N * SK_N * SK_R  # field update per sweep (all rows, all blocks)
+    out.update({"value": SK_N * SK_R / (ms * 1e6), "ms_per_step": ms, "steps": args.steps,
+                "warmup": args.warmup, "gpu_launches": launches,
+                "field_gemm_tflops_over_sweep": flops / (ms * 1e-3) / 1e12})
+    if not args.skip_plain:
+        pr = sg.SKRun(J, [SK_T] * SK_R, 1, kernel=sg.SG_SK_PLAIN)
+        pr.sweep(1)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        pr.sweep(2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / 2
+        pr.close()
+        out["plain_kernel"] = {"value": SK_N * SK_R / (pms * 1e6), "ms_per_sweep": pms}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_gpu(args):
     import torch
 
@@ -391,6 +440,9 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
                     help="run only the single-instance sweep case used for ncu captures")
+    ap.add_argument("--workload", default="vb", choices=["vb", "sk"],
+                    help="vb: the headline bit-packed Viana-Bray line; sk: the SK blocked line")
+    ap.add_argument("--sk-block", type=int, default=SK_B)
     args = ap.parse_args()
     if args.warmup < 3:
         log("warning: fewer than 3 warm-up steps")
@@ -398,6 +450,8 @@ def main():
         return run_reference(args)
     if args.profile_case:
         return run_profile_case(args)
+    if args.workload == "sk":
+        return run_sk(args)
     return run_gpu(args)
 
 

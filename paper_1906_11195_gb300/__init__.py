@@ -242,14 +242,20 @@ class _Run:
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libsg needs a CUDA device")
-        self.h = handle
+        self.h = None
         self.device = torch.device(device or "cuda")
-        nbytes = sg_workspace_bytes(handle)
-        # 256-byte alignment: PyTorch's caching allocator returns 512-byte aligned blocks
-        self.workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=self.device)
-        self.stream = stream or torch.cuda.current_stream(self.device)
-        with torch.cuda.device(self.device):
-            sg_attach(handle, self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+        try:
+            nbytes = sg_workspace_bytes(handle)
+            # 256-byte alignment: PyTorch's caching allocator returns 512-byte aligned blocks
+            self.workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=self.device)
+            self.stream = stream or torch.cuda.current_stream(self.device)
+            with torch.cuda.device(self.device):
+                sg_attach(handle, self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+        except Exception:
+            sg_destroy(handle)
+            self.workspace = None
+            raise
+        self.h = handle
 
     def sweep(self, n):
         sg_sweep(self.h, n)
@@ -297,12 +303,7 @@ class VBRun(_Run):
                  device=None, stream=None):
         self.sizes = [int(np.asarray(g["row_ptr"]).size - 1) for g in graphs]
         self.n_replicas = n_replicas
-        h = sg_create_vb(graphs, n_lanes, n_replicas, kernel, tw, tm)
-        try:
-            super().__init__(h, device, stream)
-        except Exception:
-            sg_destroy(h)
-            raise
+        super().__init__(sg_create_vb(graphs, n_lanes, n_replicas, kernel, tw, tm), device, stream)
 
     def spins(self):
         """uint64 spins per graph: list of [R][n] arrays in the caller's vertex order."""
@@ -326,12 +327,8 @@ class SKRun(_Run):
                  stream=None):
         self.n = int(np.asarray(J).shape[0])
         self.n_replicas = len(temps)
-        h = sg_create_sk(J, len(temps), temps, seed, kernel, block, tw, tm)
-        try:
-            super().__init__(h, device, stream)
-        except Exception:
-            sg_destroy(h)
-            raise
+        super().__init__(sg_create_sk(J, len(temps), temps, seed, kernel, block, tw, tm), device,
+                         stream)
 
     def spins(self):
         return sg_get_spins(self.h, self.n * self.n_replicas, np.int8).reshape(self.n_replicas, self.n)

@@ -30,6 +30,54 @@ __device__ __forceinline__ uint32_t uint4_word(const uint4& v, int w) {
     return w == 0 ? v.x : (w == 1 ? v.y : (w == 2 ? v.z : v.w));
 }
 
+// --------------------------------------------------------------------------------------------
+// shared-memory barriers (mbarrier) and bulk asynchronous copies (inline PTX)
+// --------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: false if the barrier phase did not complete within max_iter polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, uint32_t max_iter) {
+    for (uint32_t it = 0; it < max_iter; ++it)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+
+// 1-D bulk copy global -> shared (TMA engine), completion counted on an mbarrier in bytes.
+// Both addresses must be 16-byte aligned and bytes a multiple of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
+                                              uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
 constexpr int kVbThrStride = 64;      // thresholds per (graph, replica): m = 0..63
 constexpr uint32_t kInactive = 0xFFFFFFFFu;
 constexpr int kDegShift = 26;         // vinfo = orig | deg << 26
@@ -48,6 +96,8 @@ struct VbPackedDev {
     const uint64_t* jb;          // [n_entries] coupling word (0 for padding entries)
     const uint64_t* seeds;       // [n_graphs]
     const uint32_t* thr;         // [n_graphs][R][64]
+    const uint4* groups;         // [n_groups] {first slice, slices, first entry, entries}
+    int* err;                    // device status word (bounded waits)
     uint64_t* S;                 // [n_slots][R]
     uint64_t* snap;              // [n_tw][n_slots][R]
     int64_t n_slots;
@@ -84,7 +134,7 @@ struct VbCountJob {
 int vb_packed_init(const VbPackedDev& d, cudaStream_t st);
 // sweep index t = *clock + t_off (the clock lives in device memory so that captured CUDA graphs
 // can be replayed at any time)
-int vb_packed_colour(const VbPackedDev& d, uint32_t slice_begin, uint32_t slice_end,
+int vb_packed_colour(const VbPackedDev& d, uint32_t group_begin, uint32_t group_end,
                      const uint32_t* clock, uint32_t t_off, cudaStream_t st);
 int vb_packed_snapshot(const VbPackedDev& d, int w, cudaStream_t st);
 int vb_packed_count(const VbPackedDev& d, const VbCountJob& job, cudaStream_t st);

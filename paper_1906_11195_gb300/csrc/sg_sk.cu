@@ -77,7 +77,7 @@ public:
             Np_ = (n + unit - 1) / unit * unit;
         } else {
             Np_ = (n + 127) / 128 * 128;
-            if (sk_plain_smem_bytes(Np_) > 227 * 1024) fail(SG_EINVAL, "n too large for the plain SK kernel");
+            if (sk_plain_smem_bytes(Np_) > 200 * 1024) fail(SG_EINVAL, "n too large for the plain SK kernel");
         }
         // couplings
         const int words = Np_ / 32;
@@ -144,14 +144,14 @@ public:
         check_cuda(cudaMemsetAsync(dE_, 0, nE() * 8, st), "memset");
         launches += sk_init(d_, st);
         if (kernel_ == SG_SK_BLOCKED) {
-            if (sk_field_prepare() != 0) fail(SG_ECUDA, "cannot raise the field kernel's shared memory limit");
+            if (sk_field_prepare(B_, kw_, NT_) != 0) fail(SG_ECUDA, "cannot raise the field kernel's shared memory limit");
             make_map_2d(&mapJ_, d_.J8, Np_, Np_, Np_, kw_, 128);
             make_map_2d(&mapD_, d_.D, Np_, R, Np_, kw_, NT_);
             // initial fields h = J s, one block of columns at a time (D holds s)
             for (int b0 = 0; b0 < Np_; b0 += B_)
                 launches += sk_field_update(d_, mapJ_, mapD_, b0, B_, kw_, NT_, 1, st);
         } else {
-            if (sk_plain_prepare() != 0) fail(SG_ECUDA, "cannot raise the plain kernel's shared memory limit");
+            if (sk_plain_prepare(Np_) != 0) fail(SG_ECUDA, "cannot raise the plain kernel's shared memory limit");
             // the plain path computes its initial fields with the same GEMM-free rule: h = J s
             fields_direct(st);
         }

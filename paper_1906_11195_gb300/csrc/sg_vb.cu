@@ -164,6 +164,8 @@ public:
             up((void*)pk_.slice_base, h_slice_base_.data(), h_slice_base_.size() * 4);
             up((void*)pk_.slice_graph, h_slice_graph_.data(), h_slice_graph_.size() * 4);
             up((void*)pk_.col, h_col_.data(), h_col_.size() * 4);
+            up((void*)pk_.groups, h_groups_.data(), h_groups_.size() * sizeof(uint4));
+            check_cuda(cudaMemsetAsync(pk_.err, 0, 4, st), "memset");
             up((void*)pk_.jb, h_jb_.data(), h_jb_.size() * 8);
             std::vector<uint64_t> seeds(n_inst);
             for (int b = 0; b < n_inst; ++b) seeds[b] = graphs_[b].seed;
@@ -185,8 +187,8 @@ public:
 
     void sweep(uint32_t t_off, cudaStream_t st) override {
         if (kernel_ == SG_VB_PACKED) {
-            for (size_t c = 0; c + 1 < colour_slice_.size(); ++c)
-                launches += vb_packed_colour(pk_, colour_slice_[c], colour_slice_[c + 1], clock_dev,
+            for (size_t c = 0; c + 1 < colour_group_.size(); ++c)
+                launches += vb_packed_colour(pk_, colour_group_[c], colour_group_[c + 1], clock_dev,
                                              t_off, st);
         } else {
             for (size_t c = 0; c + 1 < colour_begin_.size(); ++c)
@@ -327,6 +329,15 @@ public:
 
     std::vector<uint32_t> thresholds() const override { return thr_; }
 
+    int device_status(cudaStream_t st) override {
+        int v = 0;
+        if (kernel_ == SG_VB_PACKED && pk_.err) {
+            check_cuda(cudaMemcpyAsync(&v, pk_.err, 4, cudaMemcpyDeviceToHost, st), "status copy");
+            check_cuda(cudaStreamSynchronize(st), "status");
+        }
+        return v;
+    }
+
     std::vector<std::pair<void*, size_t>> state_regions() override {
         std::vector<std::pair<void*, size_t>> v;
         if (kernel_ == SG_VB_PACKED) {
@@ -368,6 +379,8 @@ private:
             pk_.slice_base = c.take<uint32_t>(h_slice_base_.size());
             pk_.slice_graph = c.take<uint32_t>(h_slice_graph_.size());
             pk_.col = c.take<uint32_t>(h_col_.size());
+            pk_.groups = c.take<uint4>(h_groups_.size());
+            pk_.err = c.take<int>(1);
             pk_.jb = c.take<uint64_t>(h_jb_.size());
             pk_.seeds = c.take<uint64_t>(n_inst);
             pk_.S = c.take<uint64_t>((size_t)n_slots_ * R);
@@ -516,6 +529,25 @@ private:
                 }
             }
         }
+        // staging groups: consecutive slices of one colour, <= 8 slices and <= 2048 entries
+        colour_group_.assign(cmax + 1, 0);
+        for (int c = 0; c < cmax; ++c) {
+            colour_group_[c] = (uint32_t)h_groups_.size();
+            int64_t s = colour_slice_[c];
+            while (s < (int64_t)colour_slice_[c + 1]) {
+                const int64_t first = s;
+                while (s < (int64_t)colour_slice_[c + 1] && s - first < 8 &&
+                       (int64_t)h_slice_base_[s + 1] - (int64_t)h_slice_base_[first] <= 2048)
+                    ++s;
+                uint4 gi;
+                gi.x = (uint32_t)first;
+                gi.y = (uint32_t)(s - first);
+                gi.z = h_slice_base_[first];
+                gi.w = h_slice_base_[s] - h_slice_base_[first];
+                h_groups_.push_back(gi);
+            }
+        }
+        colour_group_[cmax] = (uint32_t)h_groups_.size();
     }
 
     int kernel_ = SG_VB_PACKED;
@@ -523,7 +555,8 @@ private:
     std::vector<Graph> graphs_;
     std::vector<uint32_t> thr_;
     // packed host layout
-    std::vector<uint32_t> colour_slice_;
+    std::vector<uint32_t> colour_slice_, colour_group_;
+    std::vector<uint4> h_groups_;
     std::vector<std::vector<int64_t>> slot_of_;
     int64_t n_slots_ = 0;
     std::vector<uint32_t> h_vinfo_, h_slice_base_, h_slice_graph_, h_col_;

@@ -27,11 +27,11 @@ int sk_init(const SkDev& d, cudaStream_t st);
 int sk_inblock(const SkDev& d, int b0, int B, const uint32_t* clock, uint32_t t_off,
                cudaStream_t st);
 size_t sk_field_smem_bytes(int B, int kw, int NT);
-int sk_field_prepare();
+int sk_field_prepare(int B, int kw, int NT);
 int sk_field_update(const SkDev& d, const CUtensorMap& mapJ, const CUtensorMap& mapD, int b0,
                     int B, int kw, int NT, int scale, cudaStream_t st);
 size_t sk_plain_smem_bytes(int Np);
-int sk_plain_prepare();
+int sk_plain_prepare(int Np);
 int sk_plain_sweep(const SkDev& d, const uint32_t* clock, uint32_t t_off, cudaStream_t st);
 int sk_measure(const SkDev& d, int n_active, int64_t* cdst, int64_t c_stride_r,
                int64_t c_stride_w, int64_t* qdst, int64_t q_stride_p, int64_t* edst,

@@ -157,42 +157,8 @@ int sk_inblock(const SkDev& d, int b0, int B, const uint32_t* clock, uint32_t t_
 }
 
 // --------------------------------------------------------------------------------------------
-// tcgen05 / TMA / mbarrier helpers (inline PTX)
+// TMA tile load and tcgen05 descriptors (inline PTX); mbarrier helpers are in sg_internal.cuh
 // --------------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(phase)
-        : "memory");
-    return ok != 0;
-}
-
-// bounded wait: false if the barrier phase did not complete within max_iter polls
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, uint32_t max_iter) {
-    for (uint32_t it = 0; it < max_iter; ++it)
-        if (mbar_try_wait(bar, phase)) return true;
-    return false;
-}
-
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
                                             uint64_t* bar) {
     asm volatile(
@@ -344,10 +310,10 @@ int sk_field_update(const SkDev& d, const CUtensorMap& mapJ, const CUtensorMap& 
     return 1;
 }
 
-int sk_field_prepare() {
+int sk_field_prepare(int B, int kw, int NT) {
     const cudaError_t e = cudaFuncSetAttribute(k_sk_field_mma,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               200 * 1024);
+                                               (int)sk_field_smem_bytes(B, kw, NT));
     return e == cudaSuccess ? 0 : -1;
 }
 
@@ -400,10 +366,10 @@ __global__ void __launch_bounds__(256) k_sk_plain_sweep(SkDev d, const uint32_t*
 
 size_t sk_plain_smem_bytes(int Np) { return (size_t)Np * 8 + (size_t)Np / 8; }
 
-int sk_plain_prepare() {
+int sk_plain_prepare(int Np) {
     const cudaError_t e = cudaFuncSetAttribute(k_sk_plain_sweep,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               227 * 1024);
+                                               (int)sk_plain_smem_bytes(Np));
     return e == cudaSuccess ? 0 : -1;
 }
 

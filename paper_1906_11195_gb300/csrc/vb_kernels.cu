@@ -97,6 +97,8 @@ __device__ __forceinline__ void store_words(uint64_t* p, const SpinWords<R>& s) 
 }
 
 constexpr int kPlanes = 6;  // bit-sliced unsatisfied-edge counter, counts up to 63
+constexpr int kGroupSlices = 8;       // slices (warps) per staged group
+constexpr int kGroupEntries = 2048;   // staged sliced-ELL entries per group (>= 32 * 63)
 
 __device__ __forceinline__ void bitslice_add(uint64_t (&p)[kPlanes], uint64_t x) {
 #pragma unroll
@@ -119,75 +121,150 @@ __device__ __forceinline__ uint64_t bitslice_ge(const uint64_t (&p)[kPlanes], in
     return gt | eq;
 }
 
+// Staged colour-class kernel.  The slices of a colour class are cut into groups of at most
+// kGroupSlices slices (one warp each) and kGroupEntries sliced-ELL entries.  A persistent CTA
+// walks its groups; one thread stages the next groups' vinfo, own spin words, neighbour slots
+// and coupling words into shared memory with bulk asynchronous copies (double buffered, one
+// mbarrier per stage), so the only global-memory latency left on a thread's path is the gather
+// of its neighbours' spin words.
 template <int R>
-__global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_t slice_begin,
-                                                          uint32_t slice_end,
+struct VbStage {
+    uint64_t J[kGroupEntries];
+    uint32_t col[kGroupEntries];
+    uint64_t S[kGroupSlices * 32 * R];
+    uint32_t vinfo[kGroupSlices * 32];
+};
+
+constexpr uint32_t kStagePolls = 1u << 24;
+
+template <int R>
+__global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_t g_begin,
+                                                          uint32_t g_end,
                                                           const uint32_t* __restrict__ clock,
                                                           uint32_t t_off) {
-    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t slice = slice_begin + warp;
-    if (slice >= slice_end) return;
-    const int64_t slot = (int64_t)slice * 32 + lane;
-    const uint32_t vi = d.vinfo[slot];
-    if (vi == kInactive) return;
-    const uint32_t* __restrict__ col = d.col;
-    const uint64_t* __restrict__ jb = d.jb;
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    VbStage<R>* stage = reinterpret_cast<VbStage<R>*>(smem_raw);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stage + 2);
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
+    const uint32_t t = __ldg(clock) + t_off;
     const uint64_t* __restrict__ S = d.S;
 
-    const uint32_t g = d.slice_graph[slice];
-    const uint32_t base = d.slice_base[slice];
-    const uint32_t width = (d.slice_base[slice + 1] - base) >> 5;
-    const int deg = (int)(vi >> kDegShift);
-    const uint32_t orig = vi & kOrigMask;
-    const uint64_t seed = d.seeds[g];
-    const uint32_t t = __ldg(clock) + t_off;
-
-    SpinWords<R> si = load_words<R>(S + slot * R);
-
-    // random numbers: one Philox block per (vertex, sweep) serves replicas 0..3
-    const uint4 rnd = philox4x32_10(make_uint4(orig, t, 0u, 0u), (uint32_t)seed,
-                                    (uint32_t)(seed >> 32));
-    const uint32_t* thr = d.thr + (size_t)g * R * kVbThrStride;
-    int kmin[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint32_t r32 = uint4_word(rnd, r);
-        int ms = 0;
-        while (ms < deg && r32 < __ldg(thr + r * kVbThrStride + ms + 1)) ++ms;
-        kmin[r] = (deg - ms + 1) >> 1;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    __syncthreads();
 
-    uint64_t planes[R][kPlanes];
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-#pragma unroll
-        for (int b = 0; b < kPlanes; ++b) planes[r][b] = 0ull;
+    auto issue = [&](uint32_t g, int s) {
+        const uint4 gi = d.groups[g];  // first slice, slices, first entry, entries
+        const uint32_t nslot = gi.y * 32u;
+        const uint32_t bytes = nslot * 4u + nslot * R * 8u + gi.w * 12u;
+        mbar_expect_tx(&bars[s], bytes);
+        bulk_copy_g2s(stage[s].vinfo, d.vinfo + (int64_t)gi.x * 32, nslot * 4u, &bars[s]);
+        bulk_copy_g2s(stage[s].S, S + (int64_t)gi.x * 32 * R, nslot * R * 8u, &bars[s]);
+        if (gi.w) {
+            bulk_copy_g2s(stage[s].col, d.col + gi.z, gi.w * 4u, &bars[s]);
+            bulk_copy_g2s(stage[s].J, d.jb + gi.z, gi.w * 8u, &bars[s]);
+        }
+    };
 
-    uint32_t idx = base + lane;
+    uint32_t g = g_begin + blockIdx.x;
+    if (tid == 0) {
+        if (g < g_end) issue(g, 0);
+        if (g + gridDim.x < g_end) issue(g + gridDim.x, 1);
+    }
+    for (uint32_t it = 0; g < g_end; ++it, g += gridDim.x) {
+        const int s = (int)(it & 1u);
+        const uint4 gi = __ldg(&d.groups[g]);
+        if (!mbar_wait(&bars[s], (it >> 1) & 1u, kStagePolls)) {
+            if (lane == 0) atomicOr(d.err, 4);
+            break;  // every thread of the CTA times out on the same stage
+        }
+        if (warp < gi.y) {
+            const uint32_t slice = gi.x + warp;
+            const uint32_t base = __ldg(d.slice_base + slice);
+            const uint32_t width = (__ldg(d.slice_base + slice + 1) - base) >> 5;
+            const uint32_t vi = stage[s].vinfo[warp * 32 + lane];
+            if (vi != kInactive) {
+                const uint32_t gr = __ldg(d.slice_graph + slice);
+                const int deg = (int)(vi >> kDegShift);
+                const uint32_t orig = vi & kOrigMask;
+                const uint64_t seed = __ldg(d.seeds + gr);
+                SpinWords<R> si;
+#pragma unroll
+                for (int r = 0; r < R; ++r) si.v[r] = stage[s].S[(warp * 32 + lane) * R + r];
+                // one Philox block per (vertex, sweep) serves replicas 0..3
+                const uint4 rnd = philox4x32_10(make_uint4(orig, t, 0u, 0u), (uint32_t)seed,
+                                                (uint32_t)(seed >> 32));
+                const uint32_t* thr = d.thr + (size_t)gr * R * kVbThrStride;
+                int kmin[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t r32 = uint4_word(rnd, r);
+                    int ms = 0;
+                    while (ms < deg && r32 < __ldg(thr + r * kVbThrStride + ms + 1)) ++ms;
+                    kmin[r] = (deg - ms + 1) >> 1;
+                }
+                uint64_t planes[R][kPlanes];
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+#pragma unroll
+                    for (int b = 0; b < kPlanes; ++b) planes[r][b] = 0ull;
+                uint32_t loc = base - gi.z + lane;
 #pragma unroll 4
-    for (uint32_t e = 0; e < width; ++e, idx += 32) {
-        const uint32_t j = __ldcs(col + idx);
-        const uint64_t J = __ldcs(jb + idx);
-        const SpinWords<R> sj = gather_words<R>(S + (int64_t)j * R);
+                for (uint32_t e = 0; e < width; ++e, loc += 32) {
+                    const uint32_t j = stage[s].col[loc];
+                    const uint64_t J = stage[s].J[loc];
+                    const SpinWords<R> sj = gather_words<R>(S + (int64_t)j * R);
 #pragma unroll
-        for (int r = 0; r < R; ++r) bitslice_add(planes[r], si.v[r] ^ sj.v[r] ^ J);
+                    for (int r = 0; r < R; ++r) bitslice_add(planes[r], si.v[r] ^ sj.v[r] ^ J);
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) si.v[r] ^= bitslice_ge(planes[r], kmin[r]);
+                store_words<R>(d.S + ((int64_t)slice * 32 + lane) * R, si);
+            }
+        }
+        __syncthreads();  // stage s is free again
+        if (tid == 0 && g + 2 * gridDim.x < g_end) issue(g + 2 * gridDim.x, s);
     }
-#pragma unroll
-    for (int r = 0; r < R; ++r) si.v[r] ^= bitslice_ge(planes[r], kmin[r]);
-    store_words<R>(d.S + slot * R, si);
 }
 
-int vb_packed_colour(const VbPackedDev& d, uint32_t slice_begin, uint32_t slice_end,
+template <int R>
+static size_t colour_smem() {
+    return 2 * sizeof(VbStage<R>) + 2 * sizeof(uint64_t);
+}
+
+static int g_num_sms = 0;
+
+template <int R>
+static void colour_launch(const VbPackedDev& d, uint32_t g_begin, uint32_t g_end,
+                          const uint32_t* clock, uint32_t t_off, cudaStream_t st) {
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_vb_packed_colour<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)colour_smem<R>());
+        configured = true;
+    }
+    if (!g_num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 148;
+    }
+    const uint32_t ng = g_end - g_begin;
+    const uint32_t cap = (uint32_t)g_num_sms * 3u;
+    const uint32_t grid = ng < cap ? ng : cap;
+    k_vb_packed_colour<R><<<grid, 256, colour_smem<R>(), st>>>(d, g_begin, g_end, clock, t_off);
+}
+
+int vb_packed_colour(const VbPackedDev& d, uint32_t g_begin, uint32_t g_end,
                      const uint32_t* clock, uint32_t t_off, cudaStream_t st) {
-    if (slice_end <= slice_begin) return 0;
-    const uint32_t n = slice_end - slice_begin;
-    const int bs = 256;
-    const unsigned nb = (n + (bs / 32) - 1) / (bs / 32);
+    if (g_end <= g_begin) return 0;
     switch (d.R) {
-        case 1: k_vb_packed_colour<1><<<nb, bs, 0, st>>>(d, slice_begin, slice_end, clock, t_off); break;
-        case 2: k_vb_packed_colour<2><<<nb, bs, 0, st>>>(d, slice_begin, slice_end, clock, t_off); break;
-        case 4: k_vb_packed_colour<4><<<nb, bs, 0, st>>>(d, slice_begin, slice_end, clock, t_off); break;
+        case 1: colour_launch<1>(d, g_begin, g_end, clock, t_off, st); break;
+        case 2: colour_launch<2>(d, g_begin, g_end, clock, t_off, st); break;
+        case 4: colour_launch<4>(d, g_begin, g_end, clock, t_off, st); break;
         default: return -1;
     }
     return 1;
@@ -222,11 +299,14 @@ int vb_packed_snapshot(const VbPackedDev& d, int w, cudaStream_t st) {
 // accumulates bit-sliced per-lane counters (16 planes) and flushes them to global memory when
 // the graph changes and at the end of its run.
 // ---------------------------------------------------------------------------------------------
-constexpr int kCountPlanes = 16;
-constexpr int kCountSlicesPerWarp = 64;
+// A lane adds at most one word per slot (C, q) or one per entry (E: 16 slices x width <= 63 =
+// 1008 words), so 10 planes (up to 1023) cannot overflow before the flush at the end of a run.
+constexpr int kCountPlanes = 10;
+constexpr int kCountWide = kCountPlanes + 5;     // after the 32-lane butterfly
+constexpr int kCountSlicesPerWarp = 16;
 
 template <int NQ>
-__device__ __forceinline__ void count_add(uint64_t (&p)[NQ][kCountPlanes], int q, uint64_t x) {
+__device__ __forceinline__ void count_add(uint64_t (&p)[NQ][kCountWide], int q, uint64_t x) {
 #pragma unroll
     for (int b = 0; b < kCountPlanes; ++b) {
         const uint64_t c = p[q][b] & x;
@@ -235,27 +315,43 @@ __device__ __forceinline__ void count_add(uint64_t (&p)[NQ][kCountPlanes], int q
     }
 }
 
+// Sum the bit-sliced counters of the 32 lanes with a butterfly of bit-sliced additions, then
+// lane l writes the totals of spin lanes l and l + 32.
 template <int NQ>
-__device__ __forceinline__ void count_flush(uint64_t (&p)[NQ][kCountPlanes], const VbCountJob& job,
+__device__ __forceinline__ void count_flush(uint64_t (&p)[NQ][kCountWide], const VbCountJob& job,
                                             uint32_t g, int nq, uint32_t lane) {
-    for (int q = 0; q < nq; ++q) {
-        for (int k = 0; k < 64; ++k) {
-            uint32_t c = 0;
 #pragma unroll
-            for (int b = 0; b < kCountPlanes; ++b) c |= (uint32_t)((p[q][b] >> k) & 1ull) << b;
-            const uint32_t tot = __reduce_add_sync(0xFFFFFFFFu, c);
-            if (lane == 0 && tot)
-                atomicAdd((unsigned long long*)(job.dst + g * job.stride_g + q * job.stride_r +
-                                                k * job.stride_k),
-                          (unsigned long long)tot);
+    for (int q = 0; q < NQ; ++q) {
+        if (q >= nq) break;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            uint64_t carry = 0ull;
+#pragma unroll
+            for (int b = 0; b < kCountWide; ++b) {
+                const uint64_t o = __shfl_xor_sync(0xFFFFFFFFu, p[q][b], off);
+                const uint64_t x = p[q][b] ^ o;
+                const uint64_t sum = x ^ carry;
+                carry = (p[q][b] & o) | (carry & x);
+                p[q][b] = sum;
+            }
         }
+        uint32_t c0 = 0, c1 = 0;
 #pragma unroll
-        for (int b = 0; b < kCountPlanes; ++b) p[q][b] = 0ull;
+        for (int b = 0; b < kCountWide; ++b) {
+            c0 |= (uint32_t)((p[q][b] >> lane) & 1ull) << b;
+            c1 |= (uint32_t)((p[q][b] >> (lane + 32)) & 1ull) << b;
+        }
+        int64_t* base = job.dst + g * job.stride_g + q * job.stride_r;
+        if (c0) atomicAdd((unsigned long long*)(base + lane * job.stride_k), (unsigned long long)c0);
+        if (c1)
+            atomicAdd((unsigned long long*)(base + (lane + 32) * job.stride_k), (unsigned long long)c1);
+#pragma unroll
+        for (int b = 0; b < kCountWide; ++b) p[q][b] = 0ull;
     }
 }
 
 template <int R>
-__global__ void __launch_bounds__(256) k_vb_packed_count(VbPackedDev d, VbCountJob job) {
+__global__ void __launch_bounds__(256, R <= 2 ? 2 : 1) k_vb_packed_count(VbPackedDev d, VbCountJob job) {
     constexpr int NQ = R;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -263,22 +359,22 @@ __global__ void __launch_bounds__(256) k_vb_packed_count(VbPackedDev d, VbCountJ
     int64_t s_hi = s_lo + kCountSlicesPerWarp;
     if (s_hi > d.n_slices) s_hi = d.n_slices;
     const int nq = job.kind == 1 ? R / 2 : R;
-    uint64_t p[NQ][kCountPlanes];
+    uint64_t p[NQ][kCountWide];
 #pragma unroll
     for (int q = 0; q < NQ; ++q)
 #pragma unroll
-        for (int b = 0; b < kCountPlanes; ++b) p[q][b] = 0ull;
+        for (int b = 0; b < kCountWide; ++b) p[q][b] = 0ull;
     const int64_t words = d.n_slots * R;
     const uint64_t* snap = d.snap + (int64_t)(job.kind == 0 ? job.w : 0) * words;
     int64_t cur_g = -1;
     for (int64_t s = s_lo; s < s_hi; ++s) {
-        const uint32_t g = d.slice_graph[s];  // warp-uniform
+        const uint32_t g = __ldg(d.slice_graph + s);  // warp-uniform
         if ((int64_t)g != cur_g) {
             if (cur_g >= 0) count_flush<NQ>(p, job, (uint32_t)cur_g, nq, lane);
             cur_g = g;
         }
         const int64_t slot = s * 32 + lane;
-        if (d.vinfo[slot] == kInactive) continue;
+        if (__ldg(d.vinfo + slot) == kInactive) continue;
         const SpinWords<R> si = load_words<R>(d.S + slot * R);
         if (job.kind == 0) {
             const SpinWords<R> sw = load_words<R>(snap + slot * R);
@@ -288,13 +384,14 @@ __global__ void __launch_bounds__(256) k_vb_packed_count(VbPackedDev d, VbCountJ
 #pragma unroll
             for (int q = 0; q < R / 2; ++q) count_add<NQ>(p, q, si.v[2 * q] ^ si.v[2 * q + 1]);
         } else {
-            const uint32_t base = d.slice_base[s];
-            const uint32_t width = (d.slice_base[s + 1] - base) >> 5;
+            const uint32_t base = __ldg(d.slice_base + s);
+            const uint32_t width = (__ldg(d.slice_base + s + 1) - base) >> 5;
             uint32_t idx = base + lane;
+#pragma unroll 4
             for (uint32_t e = 0; e < width; ++e, idx += 32) {
-                const uint32_t j = d.col[idx];
-                const uint64_t J = d.jb[idx];
-                const SpinWords<R> sj = load_words<R>(d.S + (int64_t)j * R);
+                const uint32_t j = __ldg(d.col + idx);
+                const uint64_t J = __ldg(d.jb + idx);
+                const SpinWords<R> sj = gather_words<R>(d.S + (int64_t)j * R);
 #pragma unroll
                 for (int r = 0; r < R; ++r) count_add<NQ>(p, r, si.v[r] ^ sj.v[r] ^ J);
             }
