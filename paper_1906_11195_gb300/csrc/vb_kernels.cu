@@ -177,9 +177,10 @@ __global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_
     for (uint32_t it = 0; g < g_end; ++it, g += gridDim.x) {
         const int s = (int)(it & 1u);
         const uint4 gi = __ldg(&d.groups[g]);
-        if (!mbar_wait(&bars[s], (it >> 1) & 1u, kStagePolls)) {
-            if (lane == 0) atomicOr(d.err, 4);
-            break;  // every thread of the CTA times out on the same stage
+        // the decision to give up is made by the whole CTA, so no thread is left at a barrier
+        if (!__syncthreads_and(mbar_wait(&bars[s], (it >> 1) & 1u, kStagePolls))) {
+            if (tid == 0) atomicOr(d.err, 4);
+            break;
         }
         if (warp < gi.y) {
             const uint32_t slice = gi.x + warp;
