@@ -78,6 +78,28 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
         : "memory");
 }
 
+// Same, with an L2 cache-policy operand (createpolicy) attached to the copy.
+__device__ __forceinline__ void bulk_copy_g2s_hint(void* dst, const void* src, uint32_t bytes,
+                                                   uint64_t* bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+        : "memory");
+}
+
+// L2 eviction-priority policies: streamed data goes first, the spin array stays
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
 constexpr int kVbThrStride = 64;      // thresholds per (graph, replica): m = 0..63
 constexpr uint32_t kInactive = 0xFFFFFFFFu;
 constexpr int kDegShift = 26;         // vinfo = orig | deg << 26
@@ -85,7 +107,7 @@ constexpr uint32_t kOrigMask = (1u << kDegShift) - 1u;
 
 // ---------------------------------------------------------------------------------------------
 // Viana-Bray packed layout (sliced ELL over colour-major slots).
-// Slots are ordered by (colour, graph, degree, original label); every (colour, graph) group is
+// Slots are ordered by (colour, graph, degree descending, original label); every (colour, graph) group is
 // padded to a multiple of 32 slots, so a warp-sized slice has one colour and one graph.
 // ---------------------------------------------------------------------------------------------
 struct VbPackedDev {

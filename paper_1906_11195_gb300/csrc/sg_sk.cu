@@ -165,8 +165,9 @@ public:
             launches += sk_plain_sweep(d_, clock_dev, t_off, st);
             return;
         }
+        launches += sk_kstar_sweep(d_, clock_dev, t_off, st);
         for (int b0 = 0; b0 < n_; b0 += B_) {
-            if (sk_inblock(d_, b0, B_, clock_dev, t_off, st) < 0) fail(SG_EINVAL, "unsupported block size");
+            if (sk_inblock(d_, b0, B_, st) < 0) fail(SG_EINVAL, "unsupported block size");
             ++launches;
             launches += sk_field_update(d_, mapJ_, mapD_, b0, B_, kw_, NT_, 2, st);
         }
@@ -285,6 +286,7 @@ private:
         d_.S = c.take<uint32_t>((size_t)R * words);
         d_.D = c.take<uint8_t>((size_t)R * Np_);
         d_.H = c.take<int32_t>((size_t)R * Np_);
+        d_.kst = c.take<int32_t>(kernel_ == SG_SK_BLOCKED ? (size_t)R * Np_ : 0);
         d_.snap = c.take<uint32_t>((size_t)R * words * tw.size());
         d_.err = c.take<int>(1);
         d_.seed = seed_;

@@ -443,7 +443,7 @@ private:
         }
     }
 
-    // sliced-ELL over slots ordered by (colour, graph, degree, original label)
+    // sliced-ELL over slots ordered by (colour, graph, degree descending, original label)
     void build_packed() {
         int cmax = 0;
         for (const Graph& g : graphs_) cmax = std::max(cmax, g.n_colours);
@@ -469,7 +469,8 @@ private:
                 const Graph& g = graphs_[b];
                 if (c >= g.n_colours) continue;
                 const int64_t start = cursor;
-                for (int d = 0; d <= SG_VB_MAX_DEGREE; ++d)
+                // highest degree first: the longest slices start early instead of forming the tail
+                for (int d = SG_VB_MAX_DEGREE; d >= 0; --d)
                     for (int32_t i : bucket[b][(size_t)c * (SG_VB_MAX_DEGREE + 1) + d]) {
                         slot_of_[b][i] = cursor++;
                         slot_graph_vertex.push_back(i);

@@ -17,6 +17,7 @@ struct SkDev {
     uint32_t* S;              // [R][Np/32] spins, bit = 1 means s = -1
     uint8_t* D;               // [R][Np] e4m3 spin changes (s' - s)/2 of the current block
     int32_t* H;               // [R][Np] local fields sum_j J_ij s_j
+    int32_t* kst;             // [R][Np] K* of the current sweep (largest accepted k)
     uint32_t* snap;           // [n_tw][R][Np/32]
     int* err;                 // device status word
     uint64_t seed;
@@ -24,8 +25,8 @@ struct SkDev {
 };
 
 int sk_init(const SkDev& d, cudaStream_t st);
-int sk_inblock(const SkDev& d, int b0, int B, const uint32_t* clock, uint32_t t_off,
-               cudaStream_t st);
+int sk_kstar_sweep(const SkDev& d, const uint32_t* clock, uint32_t t_off, cudaStream_t st);
+int sk_inblock(const SkDev& d, int b0, int B, cudaStream_t st);
 size_t sk_field_smem_bytes(int B, int kw, int NT);
 int sk_field_prepare(int B, int kw, int NT);
 int sk_field_update(const SkDev& d, const CUtensorMap& mapJ, const CUtensorMap& mapD, int b0,

@@ -75,20 +75,48 @@ int sk_init(const SkDev& d, cudaStream_t st) {
 }
 
 // --------------------------------------------------------------------------------------------
-// in-block sequential update, one warp per replica
+// K* of every (replica, spin) for one sweep: depends only on the random numbers and the tables,
+// so it is computed for the whole sweep at once, off the sequential chain.
+// --------------------------------------------------------------------------------------------
+__global__ void k_sk_kstar(SkDev d, const uint32_t* __restrict__ clock, uint32_t t_off) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over R * Np
+    if (idx >= (int64_t)d.R * d.Np) return;
+    const int r = (int)(idx / d.Np);
+    const int i = (int)(idx % d.Np);
+    int k = -0x7FFFFFFF;  // padding never flips
+    if (i < d.N) {
+        const uint32_t t = __ldg(clock) + t_off;
+        const uint4 rnd = philox4x32_10(make_uint4((uint32_t)i, t, (uint32_t)(r >> 2), 0u),
+                                        (uint32_t)d.seed, (uint32_t)(d.seed >> 32));
+        k = sk_kstar(uint4_word(rnd, r & 3), d.thr + (int64_t)d.temp_index[r] * d.N, d.N,
+                     d.coef[r]);
+    }
+    d.kst[idx] = k;
+}
+
+int sk_kstar_sweep(const SkDev& d, const uint32_t* clock, uint32_t t_off, cudaStream_t st) {
+    const int64_t total = (int64_t)d.R * d.Np;
+    k_sk_kstar<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(d, clock, t_off);
+    return 1;
+}
+
+// --------------------------------------------------------------------------------------------
+// in-block sequential update, one warp per replica; the block's couplings (B rows x B/32 words)
+// are staged once per CTA in shared memory and shared by its 8 replicas
 // --------------------------------------------------------------------------------------------
 template <int NC>
-__global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0,
-                                                    const uint32_t* __restrict__ clock,
-                                                    uint32_t t_off) {
+__global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0) {
+    extern __shared__ uint32_t jblk[];  // [32 * NC rows][NC words]
     const int lane = threadIdx.x & 31;
-    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (r >= d.R) return;
-    const uint32_t t = __ldg(clock) + t_off;
     const int words = d.Np / 32;
     const int wb = b0 / 32;
-    const uint32_t* thr = d.thr + (int64_t)d.temp_index[r] * d.N;
-    const float coef = d.coef[r];
+    for (int k = threadIdx.x; k < 32 * NC * NC; k += blockDim.x) {
+        const int row = k / NC, w = k % NC;
+        jblk[k] = d.Jbits[(int64_t)(b0 + row) * words + wb + w];
+    }
+    __syncthreads();
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= d.R) return;
     int h[NC];
     int kst[NC];
     uint32_t sw[NC];
@@ -96,22 +124,15 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0,
     for (int c = 0; c < NC; ++c) {
         const int i = b0 + 32 * c + lane;
         h[c] = d.H[(int64_t)r * d.Np + i];
+        kst[c] = d.kst[(int64_t)r * d.Np + i];
         sw[c] = d.S[(int64_t)r * words + wb + c];
-        if (i < d.N) {
-            const uint4 rnd = philox4x32_10(make_uint4((uint32_t)i, t, (uint32_t)(r >> 2), 0u),
-                                            (uint32_t)d.seed, (uint32_t)(d.seed >> 32));
-            kst[c] = sk_kstar(uint4_word(rnd, r & 3), thr, d.N, coef);
-        } else {
-            kst[c] = -0x7FFFFFFF;  // padding never flips
-        }
     }
-    const uint32_t* Jb = d.Jbits;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         const int i = b0 + 32 * c + lane;
         const uint32_t sbit = (sw[c] >> lane) & 1u;
         const int x = sbit ? -h[c] : h[c];
-        const uint32_t neg = Jb[(int64_t)i * words + wb + c] ^ sw[c] ^ (sbit ? 0xFFFFFFFFu : 0u);
+        const uint32_t neg = jblk[(32 * c + lane) * NC + c] ^ sw[c] ^ (sbit ? 0xFFFFFFFFu : 0u);
         uint32_t F = 0;
         int resolved = 0;
         while (resolved < 32) {
@@ -133,8 +154,7 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0,
             const int pf = __popc(F);
 #pragma unroll
             for (int c2 = c + 1; c2 < NC; ++c2) {
-                const int i2 = b0 + 32 * c2 + lane;
-                const uint32_t m = Jb[(int64_t)i2 * words + wb + c] ^ nsw;
+                const uint32_t m = jblk[(32 * c2 + lane) * NC + c] ^ nsw;
                 h[c2] += 2 * (pf - 2 * __popc(F & m));
             }
         }
@@ -142,15 +162,16 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0,
     }
 }
 
-int sk_inblock(const SkDev& d, int b0, int B, const uint32_t* clock, uint32_t t_off,
-               cudaStream_t st) {
+int sk_inblock(const SkDev& d, int b0, int B, cudaStream_t st) {
     const unsigned nb = (unsigned)((d.R + 7) / 8);
-    switch (B / 32) {
-        case 1: k_sk_inblock<1><<<nb, 256, 0, st>>>(d, b0, clock, t_off); break;
-        case 2: k_sk_inblock<2><<<nb, 256, 0, st>>>(d, b0, clock, t_off); break;
-        case 4: k_sk_inblock<4><<<nb, 256, 0, st>>>(d, b0, clock, t_off); break;
-        case 8: k_sk_inblock<8><<<nb, 256, 0, st>>>(d, b0, clock, t_off); break;
-        case 16: k_sk_inblock<16><<<nb, 256, 0, st>>>(d, b0, clock, t_off); break;
+    const int nc = B / 32;
+    const size_t smem = (size_t)32 * nc * nc * 4;
+    switch (nc) {
+        case 1: k_sk_inblock<1><<<nb, 256, smem, st>>>(d, b0); break;
+        case 2: k_sk_inblock<2><<<nb, 256, smem, st>>>(d, b0); break;
+        case 4: k_sk_inblock<4><<<nb, 256, smem, st>>>(d, b0); break;
+        case 8: k_sk_inblock<8><<<nb, 256, smem, st>>>(d, b0); break;
+        case 16: k_sk_inblock<16><<<nb, 256, smem, st>>>(d, b0); break;
         default: return -1;
     }
     return 1;
@@ -278,13 +299,15 @@ __global__ void __launch_bounds__(128) k_sk_field_mma(const __grid_constant__ CU
                 : "r"(ta));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             const int ncol = NT - c0 < 32 ? NT - c0 : 32;
+            // all loads of the chunk first (independent), then the adds and stores
+            int hv[32];
+            int* hbase = d.H + (int64_t)(n0 + c0) * d.Np + row;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                if (j < ncol) {
-                    int* hp = d.H + (int64_t)(n0 + c0 + j) * d.Np + row;
-                    *hp += scale * __float2int_rn(__uint_as_float(v[j]));
-                }
-            }
+            for (int j = 0; j < 32; ++j)
+                if (j < ncol) hv[j] = __ldcg(hbase + (int64_t)j * d.Np);
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (j < ncol) hbase[(int64_t)j * d.Np] = hv[j] + scale * __float2int_rn(__uint_as_float(v[j]));
         }
     } else if (tid == 0) {
         // give any copies still in flight a bounded chance to land before the CTA exits

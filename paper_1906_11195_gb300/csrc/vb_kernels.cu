@@ -84,6 +84,37 @@ __device__ __forceinline__ SpinWords<R> gather_words(const uint64_t* p) {
     return s;
 }
 
+// gather of a neighbour's words through the read-only path with an L2 evict-last policy
+template <int R>
+__device__ __forceinline__ SpinWords<R> gather_words_keep(const uint64_t* p, uint64_t pol) {
+    SpinWords<R> s;
+    if constexpr (R == 1) {
+        asm volatile("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;"
+                     : "=l"(s.v[0]) : "l"(p), "l"(pol));
+    } else {
+#pragma unroll
+        for (int h = 0; h < R / 2; ++h)
+            asm volatile("ld.global.nc.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
+                         : "=l"(s.v[2 * h]), "=l"(s.v[2 * h + 1])
+                         : "l"(p + 2 * h), "l"(pol));
+    }
+    return s;
+}
+
+template <int R>
+__device__ __forceinline__ void store_words_keep(uint64_t* p, const SpinWords<R>& s, uint64_t pol) {
+    if constexpr (R == 1) {
+        asm volatile("st.global.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(p), "l"(s.v[0]), "l"(pol)
+                     : "memory");
+    } else {
+#pragma unroll
+        for (int h = 0; h < R / 2; ++h)
+            asm volatile("st.global.L2::cache_hint.v2.u64 [%0], {%1, %2}, %3;" ::"l"(p + 2 * h),
+                         "l"(s.v[2 * h]), "l"(s.v[2 * h + 1]), "l"(pol)
+                         : "memory");
+    }
+}
+
 template <int R>
 __device__ __forceinline__ void store_words(uint64_t* p, const SpinWords<R>& s) {
     if constexpr (R == 1) {
@@ -156,16 +187,19 @@ __global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_
     }
     __syncthreads();
 
+    const uint64_t pol_stream = l2_evict_first(), pol_keep = l2_evict_last();
     auto issue = [&](uint32_t g, int s) {
         const uint4 gi = d.groups[g];  // first slice, slices, first entry, entries
         const uint32_t nslot = gi.y * 32u;
         const uint32_t bytes = nslot * 4u + nslot * R * 8u + gi.w * 12u;
         mbar_expect_tx(&bars[s], bytes);
-        bulk_copy_g2s(stage[s].vinfo, d.vinfo + (int64_t)gi.x * 32, nslot * 4u, &bars[s]);
-        bulk_copy_g2s(stage[s].S, S + (int64_t)gi.x * 32 * R, nslot * R * 8u, &bars[s]);
+        bulk_copy_g2s_hint(stage[s].vinfo, d.vinfo + (int64_t)gi.x * 32, nslot * 4u, &bars[s],
+                           pol_stream);
+        bulk_copy_g2s_hint(stage[s].S, S + (int64_t)gi.x * 32 * R, nslot * R * 8u, &bars[s],
+                           pol_keep);
         if (gi.w) {
-            bulk_copy_g2s(stage[s].col, d.col + gi.z, gi.w * 4u, &bars[s]);
-            bulk_copy_g2s(stage[s].J, d.jb + gi.z, gi.w * 8u, &bars[s]);
+            bulk_copy_g2s_hint(stage[s].col, d.col + gi.z, gi.w * 4u, &bars[s], pol_stream);
+            bulk_copy_g2s_hint(stage[s].J, d.jb + gi.z, gi.w * 8u, &bars[s], pol_stream);
         }
     };
 
@@ -217,13 +251,13 @@ __global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_
                 for (uint32_t e = 0; e < width; ++e, loc += 32) {
                     const uint32_t j = stage[s].col[loc];
                     const uint64_t J = stage[s].J[loc];
-                    const SpinWords<R> sj = gather_words<R>(S + (int64_t)j * R);
+                    const SpinWords<R> sj = gather_words_keep<R>(S + (int64_t)j * R, pol_keep);
 #pragma unroll
                     for (int r = 0; r < R; ++r) bitslice_add(planes[r], si.v[r] ^ sj.v[r] ^ J);
                 }
 #pragma unroll
                 for (int r = 0; r < R; ++r) si.v[r] ^= bitslice_ge(planes[r], kmin[r]);
-                store_words<R>(d.S + ((int64_t)slice * 32 + lane) * R, si);
+                store_words_keep<R>(d.S + ((int64_t)slice * 32 + lane) * R, si, pol_keep);
             }
         }
         __syncthreads();  // stage s is free again
