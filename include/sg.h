@@ -175,6 +175,25 @@ int sg_destroy(sg_handle h);
 /* Number of kernel launches the handle has queued since creation (for launch accounting). */
 int sg_launch_count(sg_handle h, int64_t *count);
 
+/* SK local fields h[r][i] = sum_j J_ij s[r][j] computed on the tensor cores without allocating
+ * any device memory.  The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory where they need the fields -- a host application that fixes the
+ * library's memory budget, a plugin whose process owns every device allocation, or code running
+ * inside a stream capture, where allocation is not allowed.
+ *   J  device int8[n*n], row-major, +-1 off the diagonal, 0 on it, symmetric (not checked here)
+ *   s  device int8[n_replicas*n], spins +-1, replica-major
+ *   h  device int32[n_replicas*n], output, replica-major
+ *   n  2..2048;  n_replicas a multiple of 16 in 16..128;  cuda_stream a cudaStream_t (or NULL)
+ * The tensor-core operand images live in one static device array of about 5.3 MiB inside the
+ * library (held by every GPU that loads it until the process exits); larger sizes return
+ * SG_EINVAL.  The first call on a device looks up that array's device address (make that first
+ * call before any stream capture).  Every call reuses the array and clears what must start at
+ * zero, so calls that overlap on the GPU (different streams or host threads) race with each
+ * other: serialise them.  The call is queued on cuda_stream and returns after it completed;
+ * errors are reported like every other call (status code, sg_last_error). */
+int sg_sk_fields_noalloc(const int8_t *J, const int8_t *s, int32_t n, int32_t n_replicas,
+                         int32_t *h, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,7 +35,7 @@ EXPORTED = [
     "sg_last_error", "sg_create_vb", "sg_create_sk", "sg_workspace_bytes", "sg_attach",
     "sg_sweep", "sg_time", "sg_synchronize", "sg_result_shape", "sg_read_results", "sg_measure",
     "sg_get_spins", "sg_get_thresholds", "sg_state_bytes", "sg_save_state", "sg_load_state",
-    "sg_destroy", "sg_launch_count",
+    "sg_destroy", "sg_launch_count", "sg_sk_fields_noalloc",
 ]
 
 
@@ -88,6 +88,7 @@ def _load():
                 "sg_load_state": (ctypes.c_int, [H, P, sz]),
                 "sg_destroy": (ctypes.c_int, [H]),
                 "sg_launch_count": (ctypes.c_int, [H, P]),
+                "sg_sk_fields_noalloc": (ctypes.c_int, [P, P, i32, i32, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -232,6 +233,15 @@ def sg_launch_count(h) -> int:
     v = ctypes.c_int64()
     _check(_load().sg_launch_count(h, ctypes.byref(v)))
     return int(v.value)
+
+
+def sg_sk_fields_noalloc(J_dev: int, s_dev: int, n: int, n_replicas: int, h_dev: int,
+                         stream_handle: int):
+    """Local fields h = J s for callers that cannot allocate device memory (device pointers in
+    and out; the library's fixed static scratch holds the tensor-core operand images)."""
+    _check(_load().sg_sk_fields_noalloc(ctypes.c_void_p(J_dev), ctypes.c_void_p(s_dev), int(n),
+                                        int(n_replicas), ctypes.c_void_p(h_dev),
+                                        ctypes.c_void_p(stream_handle)))
 
 
 # ----------------------------------------------------------------------------------------------

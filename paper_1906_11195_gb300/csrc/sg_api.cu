@@ -60,6 +60,8 @@ struct sg_ctx {
 
 static thread_local std::string g_last_error;
 
+void sg::record_error(const std::string& msg) { g_last_error = msg; }
+
 static int set_error(int code, const std::string& msg) {
     g_last_error = msg;
     return code;

@@ -18,6 +18,8 @@ struct Error {
 };
 
 [[noreturn]] void fail(int code, const std::string& msg);
+// set the message returned by sg_last_error() on this thread
+void record_error(const std::string& msg);
 void check_cuda(cudaError_t e, const char* what);
 
 // 256-byte aligned carving of one caller-provided workspace (a null base only measures).
