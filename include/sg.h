@@ -110,12 +110,31 @@ int sg_create_vb(const sg_vb_graph *graphs, int32_t n_graphs, int32_t n_lanes,
  *   temps      double[R] replica temperatures (host)
  *   seed       Philox key
  *   kernel     SG_SK_PLAIN or SG_SK_BLOCKED
- *   block      spins per block B for SG_SK_BLOCKED (multiple of 32, divides the padded size);
- *              ignored by SG_SK_PLAIN
+ *   block      spins per block B for SG_SK_BLOCKED: 64, 128, 256 or 512, or 0 to let the
+ *              autotuner choose among 64, 128 and 256 at attach; ignored by SG_SK_PLAIN
  *   tw, tm     schedule, as for sg_create_vb */
 int sg_create_sk(int32_t n, const int8_t *J, int32_t n_replicas, const double *temps,
                  uint64_t seed, int32_t kernel, int32_t block, const int64_t *tw, int32_t n_tw,
                  const int64_t *tm, int32_t n_tm, sg_handle *out);
+
+/* One SK sample of a batch: n spins, couplings J (int8[n*n], host, as for sg_create_sk), its own
+ * Philox key and the temperatures of its n_replicas replicas (double[n_replicas], host). */
+typedef struct {
+    int32_t n;
+    const int8_t *J;
+    uint64_t seed;
+    const double *temps;
+} sg_sk_sample;
+
+/* Create a batch of independent SK samples of uneven size (the uneven-N runs used for the
+ * extrapolation in N of SI section 1) that advance in lock-step; each sweep is one CUDA graph
+ * whose branches, one per sample, run concurrently.  Arguments as for sg_create_sk; every sample
+ * has n_replicas replicas.  block = 0 lets an autotuner pick B in {64, 128, 256} per sample by
+ * timing trial sweeps at attach (the trajectory does not depend on B).  Results are laid out
+ * with n_inst = n_samples; spins concatenate int8[R][n_s] over the samples. */
+int sg_create_sk_batch(const sg_sk_sample *samples, int32_t n_samples, int32_t n_replicas,
+                       int32_t kernel, int32_t block, const int64_t *tw, int32_t n_tw,
+                       const int64_t *tm, int32_t n_tm, sg_handle *out);
 
 /* Device workspace size the handle needs (bytes). */
 int sg_workspace_bytes(sg_handle h, size_t *bytes);

@@ -32,7 +32,8 @@ _ERRNAMES = {SG_EINVAL: "SG_EINVAL", SG_ENOMEM: "SG_ENOMEM", SG_ECUDA: "SG_ECUDA
              SG_ETIMEOUT: "SG_ETIMEOUT", SG_ESTATE: "SG_ESTATE"}
 
 EXPORTED = [
-    "sg_last_error", "sg_create_vb", "sg_create_sk", "sg_workspace_bytes", "sg_attach",
+    "sg_last_error", "sg_create_vb", "sg_create_sk", "sg_create_sk_batch", "sg_workspace_bytes",
+    "sg_attach",
     "sg_sweep", "sg_time", "sg_synchronize", "sg_result_shape", "sg_read_results", "sg_measure",
     "sg_get_spins", "sg_get_thresholds", "sg_state_bytes", "sg_save_state", "sg_load_state",
     "sg_destroy", "sg_launch_count", "sg_sk_fields_noalloc",
@@ -48,6 +49,11 @@ class SGError(RuntimeError):
 class sg_vb_graph(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
                 ("jbits", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("temps", ctypes.c_void_p)]
+
+
+class sg_sk_sample(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("J", ctypes.c_void_p), ("seed", ctypes.c_uint64),
+                ("temps", ctypes.c_void_p)]
 
 
 _lib = None
@@ -73,6 +79,7 @@ def _load():
                 "sg_last_error": (ctypes.c_char_p, []),
                 "sg_create_vb": (ctypes.c_int, [P, i32, i32, i32, i32, P, i32, P, i32, P]),
                 "sg_create_sk": (ctypes.c_int, [i32, P, i32, P, u64, i32, i32, P, i32, P, i32, P]),
+                "sg_create_sk_batch": (ctypes.c_int, [P, i32, i32, i32, i32, P, i32, P, i32, P]),
                 "sg_workspace_bytes": (ctypes.c_int, [H, P]),
                 "sg_attach": (ctypes.c_int, [H, P, sz, P]),
                 "sg_sweep": (ctypes.c_int, [H, i64]),
@@ -149,6 +156,24 @@ def sg_create_sk(J, n_replicas, temps, seed, kernel, block, tw, tm):
     _check(lib.sg_create_sk(int(Jc.shape[0]), _p(Jc), int(n_replicas), _p(T),
                             int(seed) & (2**64 - 1), int(kernel), int(block), _p(tw_a), tw_a.size,
                             _p(tm_a), tm_a.size, ctypes.byref(h)))
+    return h
+
+
+def sg_create_sk_batch(samples, n_replicas, kernel, block, tw, tm):
+    """samples: list of dicts with J (int8 n x n), seed, temps (n_replicas temperatures)."""
+    lib = _load()
+    keep = []
+    arr = (sg_sk_sample * len(samples))()
+    for b, x in enumerate(samples):
+        Jc = np.ascontiguousarray(x["J"], dtype=np.int8)
+        T = np.ascontiguousarray(x["temps"], dtype=np.float64)
+        keep += [Jc, T]
+        arr[b] = sg_sk_sample(int(Jc.shape[0]), _p(Jc), int(x["seed"]) & (2**64 - 1), _p(T))
+    tw_a, tm_a = _i64(tw), _i64(tm)
+    h = ctypes.c_void_p()
+    _check(lib.sg_create_sk_batch(ctypes.cast(arr, ctypes.c_void_p), len(samples), int(n_replicas),
+                                  int(kernel), int(block), _p(tw_a), tw_a.size, _p(tm_a),
+                                  tm_a.size, ctypes.byref(h)))
     return h
 
 
@@ -328,6 +353,25 @@ class VBRun(_Run):
     def thresholds(self):
         return sg_get_thresholds(self.h, len(self.sizes) * self.n_replicas * 64).reshape(
             len(self.sizes), self.n_replicas, 64)
+
+
+class SKBatchRun(_Run):
+    """Independent SK samples of uneven size advancing in lock-step (one graph per sweep)."""
+
+    def __init__(self, samples, n_replicas, kernel=SG_SK_BLOCKED, block=0, tw=(), tm=(),
+                 device=None, stream=None):
+        self.sizes = [int(np.asarray(x["J"]).shape[0]) for x in samples]
+        self.n_replicas = n_replicas
+        super().__init__(sg_create_sk_batch(samples, n_replicas, kernel, block, tw, tm), device,
+                         stream)
+
+    def spins(self):
+        flat = sg_get_spins(self.h, sum(self.sizes) * self.n_replicas, np.int8)
+        out, off = [], 0
+        for n in self.sizes:
+            out.append(flat[off:off + n * self.n_replicas].reshape(self.n_replicas, n))
+            off += n * self.n_replicas
+        return out
 
 
 class SKRun(_Run):

@@ -201,6 +201,21 @@ int sg_create_sk(int32_t n, const int8_t* J, int32_t n_replicas, const double* t
     });
 }
 
+int sg_create_sk_batch(const sg_sk_sample* samples, int32_t n_samples, int32_t n_replicas,
+                       int32_t kernel, int32_t block, const int64_t* tw, int32_t n_tw,
+                       const int64_t* tm, int32_t n_tm, sg_handle* out) {
+    return guarded([&] {
+        if (!out) sg::fail(SG_EINVAL, "out is null");
+        *out = nullptr;
+        std::unique_ptr<sg_ctx> h(new sg_ctx());
+        h->tw = read_schedule(tw, n_tw, "tw");
+        h->tm = read_schedule(tm, n_tm, "tm");
+        h->model.reset(sg::make_sk_batch_model(samples, n_samples, n_replicas, kernel, block, h->tw,
+                                               h->tm));
+        *out = h.release();
+    });
+}
+
 int sg_workspace_bytes(sg_handle h, size_t* bytes) {
     return guarded([&] {
         if (!h || !bytes) sg::fail(SG_EINVAL, "null argument");

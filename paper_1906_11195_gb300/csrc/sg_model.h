@@ -70,6 +70,9 @@ public:
 
 Model* make_vb_model(const void* graphs, int n_graphs, int n_lanes, int n_replicas, int kernel,
                      const std::vector<int64_t>& tw, const std::vector<int64_t>& tm);
+Model* make_sk_batch_model(const void* samples, int n_samples, int n_replicas, int kernel,
+                           int block, const std::vector<int64_t>& tw,
+                           const std::vector<int64_t>& tm);
 Model* make_sk_model(int n, const int8_t* J, int n_replicas, const double* temps, uint64_t seed,
                      int kernel, int block, const std::vector<int64_t>& tw,
                      const std::vector<int64_t>& tm);

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -66,14 +67,16 @@ public:
         tm = tm_;
         seed_ = seed;
         if (kernel == SG_SK_BLOCKED) {
-            if (!(block == 64 || block == 128 || block == 256 || block == 512))
-                fail(SG_EINVAL, "block must be 64, 128, 256 or 512");
+            if (!(block == 0 || block == 64 || block == 128 || block == 256 || block == 512))
+                fail(SG_EINVAL, "block must be 0 (autotune), 64, 128, 256 or 512");
             if (R % 16) fail(SG_EINVAL, "blocked SK needs a multiple of 16 replicas");
             if (R > 128 && R % 128) fail(SG_EINVAL, "more than 128 replicas must be a multiple of 128");
-            B_ = block;
-            kw_ = block >= 128 ? 128 : 64;
+            autotune_ = block == 0;
+            B_ = autotune_ ? 128 : block;
+            kw_ = B_ >= 128 ? 128 : 64;
             NT_ = R <= 128 ? R : 128;
-            const int unit = std::max(128, B_);
+            // autotuning picks among 64, 128 and 256, which all divide a multiple of 256
+            const int unit = autotune_ ? 256 : std::max(128, B_);
             Np_ = (n + unit - 1) / unit * unit;
         } else {
             Np_ = (n + 127) / 128 * 128;
@@ -137,28 +140,19 @@ public:
         up((void*)d_.thr, h_thr_.data(), h_thr_.size() * 4);
         up((void*)d_.temp_index, h_tidx_.data(), h_tidx_.size() * 4);
         up((void*)d_.coef, h_coef_.data(), h_coef_.size() * 4);
-        check_cuda(cudaMemsetAsync(d_.H, 0, (size_t)R * Np_ * 4, st), "memset");
-        check_cuda(cudaMemsetAsync(d_.err, 0, 4, st), "memset");
-        check_cuda(cudaMemsetAsync(dC_, 0, nC() * 8, st), "memset");
-        check_cuda(cudaMemsetAsync(dQ_, 0, nQ() * 8, st), "memset");
-        check_cuda(cudaMemsetAsync(dE_, 0, nE() * 8, st), "memset");
-        launches += sk_init(d_, st);
         if (kernel_ == SG_SK_BLOCKED) {
-            if (sk_field_prepare(B_, kw_, NT_) != 0) fail(SG_ECUDA, "cannot raise the field kernel's shared memory limit");
-            make_map_2d(&mapJ_, d_.J8, Np_, Np_, Np_, kw_, 128);
-            make_map_2d(&mapD_, d_.D, Np_, R, Np_, kw_, NT_);
-            // initial fields h = J s, one block of columns at a time (D holds s)
-            for (int b0 = 0; b0 < Np_; b0 += B_)
-                launches += sk_field_update(d_, mapJ_, mapD_, b0, B_, kw_, NT_, 1, st);
+            if (autotune_) tune_block(st);
+            set_block(B_);
         } else {
             if (sk_plain_prepare(Np_) != 0) fail(SG_ECUDA, "cannot raise the plain kernel's shared memory limit");
-            // the plain path computes its initial fields with the same GEMM-free rule: h = J s
-            fields_direct(st);
         }
+        init_state(st);
         check_cuda(cudaGetLastError(), "init launch");
         check_cuda(cudaStreamSynchronize(st), "attach");
         if (device_status(st)) fail(SG_ETIMEOUT, "device wait expired during initialisation");
     }
+
+    int block() const { return B_; }
 
     void sweep(uint32_t t_off, cudaStream_t st) override {
         if (kernel_ == SG_SK_PLAIN) {
@@ -275,6 +269,64 @@ private:
 
     void fields_direct(cudaStream_t st);
 
+    void set_block(int B) {
+        B_ = B;
+        kw_ = B >= 128 ? 128 : 64;
+        if (sk_field_prepare(B_, kw_, NT_) != 0)
+            fail(SG_ECUDA, "cannot raise the field kernel's shared memory limit");
+        make_map_2d(&mapJ_, d_.J8, Np_, Np_, Np_, kw_, 128);
+        make_map_2d(&mapD_, d_.D, Np_, R, Np_, kw_, NT_);
+    }
+
+    // tau = 0 state: initial spins, exact fields, zero counters
+    void init_state(cudaStream_t st) {
+        check_cuda(cudaMemsetAsync(d_.H, 0, (size_t)R * Np_ * 4, st), "memset");
+        check_cuda(cudaMemsetAsync(d_.err, 0, 4, st), "memset");
+        check_cuda(cudaMemsetAsync(dC_, 0, nC() * 8, st), "memset");
+        check_cuda(cudaMemsetAsync(dQ_, 0, nQ() * 8, st), "memset");
+        check_cuda(cudaMemsetAsync(dE_, 0, nE() * 8, st), "memset");
+        launches += sk_init(d_, st);
+        if (kernel_ == SG_SK_BLOCKED) {
+            // initial fields h = J s, one block of columns at a time (D holds s)
+            for (int b0 = 0; b0 < Np_; b0 += B_)
+                launches += sk_field_update(d_, mapJ_, mapD_, b0, B_, kw_, NT_, 1, st);
+        } else {
+            fields_direct(st);  // h = J s on CUDA cores
+        }
+    }
+
+    // Autotuner: time two sweeps with each block size that divides Np and keep the fastest.
+    // The trial sweeps run from a fresh state which init_state() then rebuilds, so the choice
+    // never changes the trajectory (every block size gives the same integers).
+    void tune_block(cudaStream_t st) {
+        cudaEvent_t e0, e1;
+        check_cuda(cudaEventCreate(&e0), "cudaEventCreate");
+        check_cuda(cudaEventCreate(&e1), "cudaEventCreate");
+        float best_ms = 0.f;
+        int best = 128;
+        for (int B : {64, 128, 256}) {
+            if (Np_ % B) continue;
+            set_block(B);
+            init_state(st);
+            check_cuda(cudaMemsetAsync(clock_dev, 0, 4, st), "memset");
+            sweep(0, st);  // warm-up
+            check_cuda(cudaEventRecord(e0, st), "cudaEventRecord");
+            sweep(1, st);
+            sweep(2, st);
+            check_cuda(cudaEventRecord(e1, st), "cudaEventRecord");
+            check_cuda(cudaEventSynchronize(e1), "cudaEventSynchronize");
+            float ms = 0.f;
+            check_cuda(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+            if (best_ms == 0.f || ms < best_ms) {
+                best_ms = ms;
+                best = B;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        B_ = best;
+    }
+
     void carve(Carver& c) {
         const int words = Np_ / 32;
         clock_dev = c.take<uint32_t>(1);
@@ -302,6 +354,7 @@ private:
     }
 
     int kernel_ = SG_SK_BLOCKED;
+    bool autotune_ = false;
     int n_ = 0, Np_ = 0, B_ = 128, kw_ = 128, NT_ = 128;
     uint64_t seed_ = 0;
     std::vector<uint8_t> h_J8_;
@@ -338,7 +391,163 @@ void SkModel::fields_direct(cudaStream_t st) {
     ++launches;
 }
 
+// A batch of independent SK samples (uneven N) advancing in lock-step.  Each sweep forks one
+// branch per sample onto its own stream and joins them, so that under stream capture a sweep
+// becomes one CUDA graph whose branches run concurrently.
+class SkBatchModel : public Model {
+public:
+    SkBatchModel(const sg_sk_sample* samples, int n_samples, int n_replicas, int kernel, int block,
+                 const std::vector<int64_t>& tw_, const std::vector<int64_t>& tm_) {
+        if (!samples || n_samples < 1) fail(SG_EINVAL, "need at least one sample");
+        n_inst = n_samples;
+        R = n_replicas;
+        L = 1;
+        tw = tw_;
+        tm = tm_;
+        for (int b = 0; b < n_samples; ++b) {
+            const sg_sk_sample& x = samples[b];
+            try {
+                subs_.emplace_back(new SkModel(x.n, x.J, n_replicas, x.temps, x.seed, kernel, block, tw, tm));
+            } catch (const Error& e) {
+                fail(e.code, "sample " + std::to_string(b) + ": " + e.msg);
+            }
+        }
+    }
+
+    ~SkBatchModel() override {
+        for (auto& e : events_) cudaEventDestroy(e);
+        if (fork_) cudaEventDestroy(fork_);
+        for (auto& st : streams_) cudaStreamDestroy(st);
+    }
+
+    size_t workspace_bytes() const override {
+        size_t off = 256;  // batch clock
+        for (auto& m : subs_) off = ((off + 255) & ~size_t(255)) + m->workspace_bytes();
+        return off;
+    }
+
+    void attach(char* ws, cudaStream_t st) override {
+        clock_dev = reinterpret_cast<uint32_t*>(ws);
+        size_t off = 256;
+        for (auto& m : subs_) {
+            off = (off + 255) & ~size_t(255);
+            m->attach(ws + off, st);
+            off += m->workspace_bytes();
+            launches += m->launches;
+            m->launches = 0;
+            m->clock_dev = clock_dev;  // every sample reads the batch clock
+        }
+        check_cuda(cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming), "cudaEventCreate");
+        for (size_t b = 0; b < subs_.size(); ++b) {
+            cudaStream_t s2;
+            cudaEvent_t e;
+            check_cuda(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking), "cudaStreamCreate");
+            streams_.push_back(s2);
+            check_cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+            events_.push_back(e);
+        }
+    }
+
+    void sweep(uint32_t t_off, cudaStream_t st) override {
+        check_cuda(cudaEventRecord(fork_, st), "cudaEventRecord");
+        for (size_t b = 0; b < subs_.size(); ++b) {
+            check_cuda(cudaStreamWaitEvent(streams_[b], fork_, 0), "cudaStreamWaitEvent");
+            subs_[b]->sweep(t_off, streams_[b]);
+            check_cuda(cudaEventRecord(events_[b], streams_[b]), "cudaEventRecord");
+        }
+        for (size_t b = 0; b < subs_.size(); ++b)
+            check_cuda(cudaStreamWaitEvent(st, events_[b], 0), "cudaStreamWaitEvent");
+        collect();
+    }
+
+    void snapshot(int w, cudaStream_t st) override {
+        for (auto& m : subs_) m->snapshot(w, st);
+        collect();
+    }
+
+    void measure_scheduled(int u, int64_t tau, cudaStream_t st) override {
+        for (auto& m : subs_) m->measure_scheduled(u, tau, st);
+        collect();
+    }
+
+    void measure_now(int64_t tau, cudaStream_t st) override {
+        for (auto& m : subs_) m->measure_now(tau, st);
+        collect();
+    }
+
+    void read_scheduled(int64_t tau, int64_t* C, int64_t* q, int64_t* E, cudaStream_t st) override {
+        const size_t nc = (size_t)R * tw.size() * tm.size(), nq = (size_t)(R / 2) * tm.size(),
+                     ne = (size_t)R * tm.size();
+        for (size_t b = 0; b < subs_.size(); ++b)
+            subs_[b]->read_scheduled(tau, C + b * nc, q + b * nq, E + b * ne, st);
+    }
+
+    void read_now(int64_t tau, int64_t* C, int64_t* q, int64_t* E, cudaStream_t st) override {
+        const size_t nc = (size_t)R * tw.size(), nq = (size_t)(R / 2), ne = (size_t)R;
+        for (size_t b = 0; b < subs_.size(); ++b)
+            subs_[b]->read_now(tau, C + b * nc, q + b * nq, E + b * ne, st);
+    }
+
+    size_t spins_bytes() const override {
+        size_t t = 0;
+        for (auto& m : subs_) t += m->spins_bytes();
+        return t;
+    }
+
+    void get_spins(void* dst, cudaStream_t st) override {
+        char* p = static_cast<char*>(dst);
+        for (auto& m : subs_) {
+            m->get_spins(p, st);
+            p += m->spins_bytes();
+        }
+    }
+
+    std::vector<uint32_t> thresholds() const override {
+        std::vector<uint32_t> t;
+        for (auto& m : subs_) {
+            auto x = m->thresholds();
+            t.insert(t.end(), x.begin(), x.end());
+        }
+        return t;
+    }
+
+    std::vector<std::pair<void*, size_t>> state_regions() override {
+        std::vector<std::pair<void*, size_t>> v;
+        for (auto& m : subs_) {
+            auto x = m->state_regions();
+            v.insert(v.end(), x.begin(), x.end());
+        }
+        return v;
+    }
+
+    int device_status(cudaStream_t st) override {
+        int v = 0;
+        for (auto& m : subs_) v |= m->device_status(st);
+        return v;
+    }
+
+private:
+    void collect() {
+        for (auto& m : subs_) {
+            launches += m->launches;
+            m->launches = 0;
+        }
+    }
+
+    std::vector<std::unique_ptr<SkModel>> subs_;
+    std::vector<cudaStream_t> streams_;
+    std::vector<cudaEvent_t> events_;
+    cudaEvent_t fork_ = nullptr;
+};
+
 }  // namespace
+
+Model* make_sk_batch_model(const void* samples, int n_samples, int n_replicas, int kernel,
+                           int block, const std::vector<int64_t>& tw,
+                           const std::vector<int64_t>& tm) {
+    return new SkBatchModel(static_cast<const sg_sk_sample*>(samples), n_samples, n_replicas,
+                            kernel, block, tw, tm);
+}
 
 Model* make_sk_model(int n, const int8_t* J, int n_replicas, const double* temps, uint64_t seed,
                      int kernel, int block, const std::vector<int64_t>& tw,

@@ -530,7 +530,8 @@ private:
                 }
             }
         }
-        // staging groups: consecutive slices of one colour, <= 8 slices and <= 2048 entries
+        // staging groups: consecutive slices of one colour, <= 8 slices and <= 1024 entries;
+        // a single slice wider than that (degree > 32) forms a group flagged "wide"
         colour_group_.assign(cmax + 1, 0);
         for (int c = 0; c < cmax; ++c) {
             colour_group_[c] = (uint32_t)h_groups_.size();
@@ -538,11 +539,16 @@ private:
             while (s < (int64_t)colour_slice_[c + 1]) {
                 const int64_t first = s;
                 while (s < (int64_t)colour_slice_[c + 1] && s - first < 8 &&
-                       (int64_t)h_slice_base_[s + 1] - (int64_t)h_slice_base_[first] <= 2048)
+                       (int64_t)h_slice_base_[s + 1] - (int64_t)h_slice_base_[first] <= 1024)
                     ++s;
+                bool wide = false;
+                if (s == first) {  // one slice alone exceeds the stage
+                    ++s;
+                    wide = true;
+                }
                 uint4 gi;
                 gi.x = (uint32_t)first;
-                gi.y = (uint32_t)(s - first);
+                gi.y = (uint32_t)(s - first) | (wide ? 0x80000000u : 0u);
                 gi.z = h_slice_base_[first];
                 gi.w = h_slice_base_[s] - h_slice_base_[first];
                 h_groups_.push_back(gi);

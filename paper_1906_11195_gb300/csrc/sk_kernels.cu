@@ -333,11 +333,17 @@ int sk_field_update(const SkDev& d, const CUtensorMap& mapJ, const CUtensorMap& 
     return 1;
 }
 
+// The limit is a property of the kernel, shared by every handle: it only ever grows.
+static int g_field_smem_limit = 0;
+
 int sk_field_prepare(int B, int kw, int NT) {
+    const int need = (int)sk_field_smem_bytes(B, kw, NT);
+    if (need <= g_field_smem_limit) return 0;
     const cudaError_t e = cudaFuncSetAttribute(k_sk_field_mma,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)sk_field_smem_bytes(B, kw, NT));
-    return e == cudaSuccess ? 0 : -1;
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+    if (e != cudaSuccess) return -1;
+    g_field_smem_limit = need;
+    return 0;
 }
 
 // --------------------------------------------------------------------------------------------
@@ -389,11 +395,16 @@ __global__ void __launch_bounds__(256) k_sk_plain_sweep(SkDev d, const uint32_t*
 
 size_t sk_plain_smem_bytes(int Np) { return (size_t)Np * 8 + (size_t)Np / 8; }
 
+static int g_plain_smem_limit = 0;
+
 int sk_plain_prepare(int Np) {
+    const int need = (int)sk_plain_smem_bytes(Np);
+    if (need <= g_plain_smem_limit) return 0;
     const cudaError_t e = cudaFuncSetAttribute(k_sk_plain_sweep,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)sk_plain_smem_bytes(Np));
-    return e == cudaSuccess ? 0 : -1;
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+    if (e != cudaSuccess) return -1;
+    g_plain_smem_limit = need;
+    return 0;
 }
 
 int sk_plain_sweep(const SkDev& d, const uint32_t* clock, uint32_t t_off, cudaStream_t st) {

@@ -129,7 +129,7 @@ __device__ __forceinline__ void store_words(uint64_t* p, const SpinWords<R>& s) 
 
 constexpr int kPlanes = 6;  // bit-sliced unsatisfied-edge counter, counts up to 63
 constexpr int kGroupSlices = 8;       // slices (warps) per staged group
-constexpr int kGroupEntries = 2048;   // staged sliced-ELL entries per group (>= 32 * 63)
+constexpr int kGroupEntries = 1024;   // staged sliced-ELL entries per group
 
 __device__ __forceinline__ void bitslice_add(uint64_t (&p)[kPlanes], uint64_t x) {
 #pragma unroll
@@ -152,14 +152,22 @@ __device__ __forceinline__ uint64_t bitslice_ge(const uint64_t (&p)[kPlanes], in
     return gt | eq;
 }
 
-// Staged colour-class kernel.  The slices of a colour class are cut into groups of at most
+// Pipelined colour-class kernel.  The slices of a colour class are cut into groups of at most
 // kGroupSlices slices (one warp each) and kGroupEntries sliced-ELL entries.  A persistent CTA
-// walks its groups; one thread stages the next groups' vinfo, own spin words, neighbour slots
-// and coupling words into shared memory with bulk asynchronous copies (double buffered, one
-// mbarrier per stage), so the only global-memory latency left on a thread's path is the gather
-// of its neighbours' spin words.
+// walks its groups through a two-stage shared-memory pipeline:
+//   * one thread stages a group's vinfo, own spin words, neighbour slots and coupling words with
+//     bulk asynchronous copies (completion on the stage's mbarrier), two groups ahead;
+//   * as soon as a group is staged, every thread starts asynchronous 16-byte copies (cp.async)
+//     of its neighbours' spin words into the stage, one group ahead of the computation;
+//   * the computation of a group reads everything from shared memory.
+// So the random gathers of the next group are in flight while the current group is computed,
+// and no global-memory latency is left on the dependent path.  A group holding one slice wider
+// than the stage (degree > 32, flagged by the host) is computed straight from global memory.
+constexpr uint32_t kWideGroup = 0x80000000u;
+
 template <int R>
 struct VbStage {
+    uint64_t gath[kGroupEntries * R];
     uint64_t J[kGroupEntries];
     uint32_t col[kGroupEntries];
     uint64_t S[kGroupSlices * 32 * R];
@@ -167,6 +175,21 @@ struct VbStage {
 };
 
 constexpr uint32_t kStagePolls = 1u << 24;
+
+template <int R>
+__device__ __forceinline__ void gather_async(uint64_t* dst, const uint64_t* src, uint64_t pol) {
+    if constexpr (R == 1) {
+        asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;" ::"r"(
+                         smem_addr(dst)), "l"(src), "l"(pol)
+                     : "memory");
+    } else {
+#pragma unroll
+        for (int h = 0; h < R / 2; ++h)
+            asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(
+                             smem_addr(dst + 2 * h)), "l"(src + 2 * h), "l"(pol)
+                         : "memory");
+    }
+}
 
 template <int R>
 __global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_t g_begin,
@@ -179,6 +202,7 @@ __global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
     const uint32_t t = __ldg(clock) + t_off;
     const uint64_t* __restrict__ S = d.S;
+    const uint64_t pol_stream = l2_evict_first(), pol_keep = l2_evict_last();
 
     if (tid == 0) {
         mbar_init(&bars[0], 1);
@@ -187,41 +211,71 @@ __global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_
     }
     __syncthreads();
 
-    const uint64_t pol_stream = l2_evict_first(), pol_keep = l2_evict_last();
-    auto issue = [&](uint32_t g, int s) {
-        const uint4 gi = d.groups[g];  // first slice, slices, first entry, entries
-        const uint32_t nslot = gi.y * 32u;
-        const uint32_t bytes = nslot * 4u + nslot * R * 8u + gi.w * 12u;
+    auto issue_stage = [&](uint32_t g, int s) {  // one thread
+        const uint4 gi = d.groups[g];  // first slice, slices (| wide), first entry, entries
+        const uint32_t nsl = gi.y & ~kWideGroup;
+        const bool wide = (gi.y & kWideGroup) != 0u;
+        const uint32_t nslot = nsl * 32u;
+        const uint32_t bytes = nslot * 4u + nslot * R * 8u + (wide ? 0u : gi.w * 12u);
         mbar_expect_tx(&bars[s], bytes);
         bulk_copy_g2s_hint(stage[s].vinfo, d.vinfo + (int64_t)gi.x * 32, nslot * 4u, &bars[s],
                            pol_stream);
         bulk_copy_g2s_hint(stage[s].S, S + (int64_t)gi.x * 32 * R, nslot * R * 8u, &bars[s],
                            pol_keep);
-        if (gi.w) {
+        if (gi.w && !wide) {
             bulk_copy_g2s_hint(stage[s].col, d.col + gi.z, gi.w * 4u, &bars[s], pol_stream);
             bulk_copy_g2s_hint(stage[s].J, d.jb + gi.z, gi.w * 8u, &bars[s], pol_stream);
         }
     };
-
-    uint32_t g = g_begin + blockIdx.x;
-    if (tid == 0) {
-        if (g < g_end) issue(g, 0);
-        if (g + gridDim.x < g_end) issue(g + gridDim.x, 1);
-    }
-    for (uint32_t it = 0; g < g_end; ++it, g += gridDim.x) {
-        const int s = (int)(it & 1u);
+    // every thread: start the copies of its neighbours' words for the staged group
+    auto issue_gathers = [&](uint32_t g, int s) {
         const uint4 gi = __ldg(&d.groups[g]);
-        // the decision to give up is made by the whole CTA, so no thread is left at a barrier
-        if (!__syncthreads_and(mbar_wait(&bars[s], (it >> 1) & 1u, kStagePolls))) {
-            if (tid == 0) atomicOr(d.err, 4);
-            break;
-        }
-        if (warp < gi.y) {
+        const uint32_t nsl = gi.y & ~kWideGroup;
+        if (warp < nsl && !(gi.y & kWideGroup)) {
             const uint32_t slice = gi.x + warp;
-            const uint32_t base = __ldg(d.slice_base + slice);
-            const uint32_t width = (__ldg(d.slice_base + slice + 1) - base) >> 5;
+            if (stage[s].vinfo[warp * 32 + lane] != kInactive) {
+                const uint32_t base = __ldg(d.slice_base + slice);
+                const uint32_t width = (__ldg(d.slice_base + slice + 1) - base) >> 5;
+                uint32_t loc = base - gi.z + lane;
+                for (uint32_t e = 0; e < width; ++e, loc += 32)
+                    gather_async<R>(&stage[s].gath[loc * R], S + (int64_t)stage[s].col[loc] * R,
+                                    pol_keep);
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+
+    const uint32_t g0 = g_begin + blockIdx.x, stride = gridDim.x;
+    if (tid == 0) {
+        if (g0 < g_end) issue_stage(g0, 0);
+        if (g0 + stride < g_end) issue_stage(g0 + stride, 1);
+    }
+    bool ok = true;
+    if (g0 < g_end) {
+        ok = __syncthreads_and(mbar_wait(&bars[0], 0, kStagePolls));
+        if (ok) issue_gathers(g0, 0);
+    }
+    uint32_t it = 0;
+    for (uint32_t g = g0; ok && g < g_end; g += stride, ++it) {
+        const int s = (int)(it & 1u);
+        const uint32_t gn = g + stride;
+        if (gn < g_end) {
+            ok = __syncthreads_and(mbar_wait(&bars[s ^ 1], ((it + 1) >> 1) & 1u, kStagePolls));
+            if (!ok) break;
+            issue_gathers(gn, s ^ 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        const uint4 gi = __ldg(&d.groups[g]);
+        const uint32_t nsl = gi.y & ~kWideGroup;
+        const bool wide = (gi.y & kWideGroup) != 0u;
+        if (warp < nsl) {
+            const uint32_t slice = gi.x + warp;
             const uint32_t vi = stage[s].vinfo[warp * 32 + lane];
             if (vi != kInactive) {
+                const uint32_t base = __ldg(d.slice_base + slice);
+                const uint32_t width = (__ldg(d.slice_base + slice + 1) - base) >> 5;
                 const uint32_t gr = __ldg(d.slice_graph + slice);
                 const int deg = (int)(vi >> kDegShift);
                 const uint32_t orig = vi & kOrigMask;
@@ -229,40 +283,48 @@ __global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_
                 SpinWords<R> si;
 #pragma unroll
                 for (int r = 0; r < R; ++r) si.v[r] = stage[s].S[(warp * 32 + lane) * R + r];
-                // one Philox block per (vertex, sweep) serves replicas 0..3
-                const uint4 rnd = philox4x32_10(make_uint4(orig, t, 0u, 0u), (uint32_t)seed,
-                                                (uint32_t)(seed >> 32));
-                const uint32_t* thr = d.thr + (size_t)gr * R * kVbThrStride;
-                int kmin[R];
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const uint32_t r32 = uint4_word(rnd, r);
-                    int ms = 0;
-                    while (ms < deg && r32 < __ldg(thr + r * kVbThrStride + ms + 1)) ++ms;
-                    kmin[r] = (deg - ms + 1) >> 1;
-                }
                 uint64_t planes[R][kPlanes];
 #pragma unroll
                 for (int r = 0; r < R; ++r)
 #pragma unroll
                     for (int b = 0; b < kPlanes; ++b) planes[r][b] = 0ull;
-                uint32_t loc = base - gi.z + lane;
-#pragma unroll 4
-                for (uint32_t e = 0; e < width; ++e, loc += 32) {
-                    const uint32_t j = stage[s].col[loc];
-                    const uint64_t J = stage[s].J[loc];
-                    const SpinWords<R> sj = gather_words_keep<R>(S + (int64_t)j * R, pol_keep);
+                if (!wide) {
+                    uint32_t loc = base - gi.z + lane;
+                    for (uint32_t e = 0; e < width; ++e, loc += 32) {
+                        const uint64_t J = stage[s].J[loc];
 #pragma unroll
-                    for (int r = 0; r < R; ++r) bitslice_add(planes[r], si.v[r] ^ sj.v[r] ^ J);
+                        for (int r = 0; r < R; ++r)
+                            bitslice_add(planes[r], si.v[r] ^ stage[s].gath[loc * R + r] ^ J);
+                    }
+                } else {
+                    uint32_t idx = base + lane;
+                    for (uint32_t e = 0; e < width; ++e, idx += 32) {
+                        const uint32_t j = __ldg(d.col + idx);
+                        const uint64_t J = __ldg(d.jb + idx);
+                        const SpinWords<R> sj = gather_words<R>(S + (int64_t)j * R);
+#pragma unroll
+                        for (int r = 0; r < R; ++r) bitslice_add(planes[r], si.v[r] ^ sj.v[r] ^ J);
+                    }
                 }
+                // one Philox block per (vertex, sweep) serves replicas 0..3
+                const uint4 rnd = philox4x32_10(make_uint4(orig, t, 0u, 0u), (uint32_t)seed,
+                                                (uint32_t)(seed >> 32));
+                const uint32_t* thr = d.thr + (size_t)gr * R * kVbThrStride;
 #pragma unroll
-                for (int r = 0; r < R; ++r) si.v[r] ^= bitslice_ge(planes[r], kmin[r]);
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t r32 = uint4_word(rnd, r);
+                    int ms = 0;
+                    while (ms < deg && r32 < __ldg(thr + r * kVbThrStride + ms + 1)) ++ms;
+                    si.v[r] ^= bitslice_ge(planes[r], (deg - ms + 1) >> 1);
+                }
                 store_words_keep<R>(d.S + ((int64_t)slice * 32 + lane) * R, si, pol_keep);
             }
         }
         __syncthreads();  // stage s is free again
-        if (tid == 0 && g + 2 * gridDim.x < g_end) issue(g + 2 * gridDim.x, s);
+        if (tid == 0 && g + 2 * stride < g_end) issue_stage(g + 2 * stride, s);
     }
+    if (!ok && tid == 0) atomicOr(d.err, 4);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 template <int R>
@@ -288,7 +350,7 @@ static void colour_launch(const VbPackedDev& d, uint32_t g_begin, uint32_t g_end
         if (g_num_sms <= 0) g_num_sms = 148;
     }
     const uint32_t ng = g_end - g_begin;
-    const uint32_t cap = (uint32_t)g_num_sms * 3u;
+    const uint32_t cap = (uint32_t)g_num_sms * (R == 4 ? 2u : 3u);
     const uint32_t grid = ng < cap ? ng : cap;
     k_vb_packed_colour<R><<<grid, 256, colour_smem<R>(), st>>>(d, g_begin, g_end, clock, t_off);
 }

@@ -142,3 +142,26 @@ def test_full_size_matches_oracle_on_sampled_replicas(sk_big):
         check(J, temps, 1, sweeps, tw, tm, got, r_first=r0, r_count=2)
     spins, C, q, E = got
     assert np.all(np.abs(C) <= 8192) and np.all((C - 8192) % 2 == 0)
+
+
+def test_batched_uneven_samples_with_autotuned_blocks():
+    """Uneven SK samples in one handle (one graph branch per sample), block chosen by the
+    autotuner (block = 0), T = 0.4 and 0.6 replicas; every sample equals its own oracle run."""
+    sizes = [int(x) for x in sg_inputs.log_uniform_sizes(5, 7, 10.5, 9)]
+    R = 32
+    samples = []
+    for k, n in enumerate(sizes):
+        samples.append(dict(J=sg_inputs.sk_couplings(n, 900 + k), seed=50 + k,
+                            temps=[0.4] * (R // 2) + [0.6] * (R // 2)))
+    tw, tm = sg_inputs.log_schedule([0, 3], 20)
+    run = sg.SKBatchRun(samples, R, kernel=sg.SG_SK_BLOCKED, block=0, tw=tw, tm=tm)
+    run.sweep(20)
+    run.synchronize()
+    C, q, E = run.results()
+    spins = run.spins()
+    run.close()
+    for b, x in enumerate(samples):
+        ref = oracle.sk_run(x["J"], x["temps"], x["seed"], 20, tw, tm)
+        assert np.array_equal(spins[b], ref["spins"]), b
+        assert np.array_equal(C[b, :, 0], ref["C"]) and np.array_equal(E[b, :, 0], ref["E"])
+        assert np.array_equal(q[b, :, 0], ref["q"])
