@@ -225,6 +225,55 @@ def run_profile_case(args):
 SK_N, SK_R, SK_T, SK_B = 8192, 256, 0.4, 128
 
 
+def run_vb_batch(args):
+    """Batched uneven VB workload (not the headline line): args.batch graphs (512 in the full
+    workload) of Poissonian c = 4 graphs with N = round(2^U), U ~ Uniform[10, 20], 64 lanes,
+    R = 2, T = 1.0, all advancing in lock-step (one launch per colour index per sweep, replayed
+    from CUDA graphs).  One step = one sweep of the whole batch."""
+    import torch
+
+    import paper_1906_11195_gb300 as sg
+    from paper_1906_11195_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    sizes = sg_inputs.log_uniform_sizes(args.batch, 10, 20, 4)
+    graphs = []
+    t0 = time.perf_counter()
+    for k, n in enumerate(sizes):
+        rp, col, eid = sg_inputs.poisson_graph(int(n), MEAN_DEGREE, (4 << 20) + k)
+        jb = sg_inputs.vb_lane_couplings(eid, eid.max() + 1, (4 << 20) + k)
+        graphs.append(dict(row_ptr=rp, col=col, jbits=jb, seed=(4 << 20) + k, temps=[1.0] * REPLICAS))
+    log(f"generated {len(graphs)} graphs, sum N = {int(sizes.sum())} in {time.perf_counter() - t0:.1f} s")
+    t0 = time.perf_counter()
+    run = sg.VBRun(graphs, n_lanes=LANES, n_replicas=REPLICAS, kernel=sg.SG_VB_PACKED)
+    log(f"created and attached in {time.perf_counter() - t0:.1f} s")
+    stream = torch.cuda.current_stream()
+    run.sweep(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = run.launches
+    e0.record(stream)
+    run.sweep(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    run.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    updates = int(sizes.sum()) * LANES * REPLICAS
+    n_entries = sum(int(g["row_ptr"][-1]) for g in graphs)
+    bytes_sweep = algorithmic_bytes_per_sweep(int(sizes.sum()), n_entries, REPLICAS)
+    peak, _ = peaks()
+    out = {"metric": "spin updates/ns", "unit": "spin updates/ns",
+           "value": updates / (ms * 1e6), "ms_per_step": ms, "steps": args.steps,
+           "warmup": args.warmup, "gpu_launches": run.launches - l0,
+           "config": {"workload": f"vb_batch_{args.batch}_graphs_N2^10..2^20_c4_lanes64_R2_T1.0",
+                      "sum_N": int(sizes.sum())},
+           "roofline": {"bound": "hbm", "achieved": bytes_sweep / (ms * 1e-3) / 1e9, "peak": peak,
+                        "unit": "GB/s", "frac": bytes_sweep / (ms * 1e-3) / 1e9 / peak}}
+    run.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_sk(args):
     """SK workload (not the headline line): N = 8192, +-1 couplings, 256 replicas sharing J,
     T = 0.4, block B = 128; one step = one sweep.  Prints one JSON line with the blocked
@@ -440,8 +489,10 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
                     help="run only the single-instance sweep case used for ncu captures")
-    ap.add_argument("--workload", default="vb", choices=["vb", "sk"],
-                    help="vb: the headline bit-packed Viana-Bray line; sk: the SK blocked line")
+    ap.add_argument("--workload", default="vb", choices=["vb", "sk", "vb_batch"],
+                    help="vb: the headline bit-packed Viana-Bray line; sk: the SK blocked line; "
+                         "vb_batch: the uneven batch of Viana-Bray graphs")
+    ap.add_argument("--batch", type=int, default=512, help="graphs in the vb_batch workload")
     ap.add_argument("--sk-block", type=int, default=SK_B)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -452,6 +503,8 @@ def main():
         return run_profile_case(args)
     if args.workload == "sk":
         return run_sk(args)
+    if args.workload == "vb_batch":
+        return run_vb_batch(args)
     return run_gpu(args)
 
 

@@ -120,13 +120,13 @@ public:
             h_tidx_.push_back(it->second);
             h_coef_.push_back((float)(sqrt((double)n) * T / 2.0));
         }
+        Carver c;
+        carve(c);
+        ws_bytes_ = c.off;
     }
 
-    size_t workspace_bytes() const override {
-        Carver c;
-        const_cast<SkModel*>(this)->carve(c);
-        return c.off;
-    }
+    // computed once at construction: carving with a null base would reset the device views
+    size_t workspace_bytes() const override { return ws_bytes_; }
 
     void attach(char* ws, cudaStream_t st) override {
         Carver c;
@@ -355,6 +355,7 @@ private:
 
     int kernel_ = SG_SK_BLOCKED;
     bool autotune_ = false;
+    size_t ws_bytes_ = 0;
     int n_ = 0, Np_ = 0, B_ = 128, kw_ = 128, NT_ = 128;
     uint64_t seed_ = 0;
     std::vector<uint8_t> h_J8_;

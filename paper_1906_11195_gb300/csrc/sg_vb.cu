@@ -143,13 +143,13 @@ public:
             }
         if (kernel == SG_VB_PACKED) build_packed();
         else build_plain();
+        Carver c;
+        carve(c);
+        ws_bytes_ = c.off;
     }
 
-    size_t workspace_bytes() const override {
-        Carver c;
-        const_cast<VbModel*>(this)->carve(c);
-        return c.off;
-    }
+    // computed once at construction: carving with a null base would reset the device views
+    size_t workspace_bytes() const override { return ws_bytes_; }
 
     void attach(char* ws, cudaStream_t st) override {
         Carver c;
@@ -559,6 +559,7 @@ private:
 
     int kernel_ = SG_VB_PACKED;
     int Lc_ = 64;
+    size_t ws_bytes_ = 0;
     std::vector<Graph> graphs_;
     std::vector<uint32_t> thr_;
     // packed host layout

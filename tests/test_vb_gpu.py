@@ -146,7 +146,9 @@ def test_sweep_chunking_and_measure_now():
     for x, y in zip(a[:4], b[:4]):
         assert np.array_equal(np.asarray(x), np.asarray(y))
     run = sg.VBRun([g], n_lanes=64, n_replicas=2, kernel=sg.SG_VB_PACKED, tw=tw, tm=tm)
-    run.sweep(21)
+    run.sweep(10)
+    assert sg.sg_workspace_bytes(run.h) == run.workspace.numel()  # querying must not disturb it
+    run.sweep(11)
     C, q, E = run.measure()
     ref = oracle.vb_run(g["row_ptr"], g["col"], g["jbits"], 64, g["temps"], g["seed"], 21, tw, [21])
     assert np.array_equal(C[0], ref["C"][..., 0])
