@@ -119,6 +119,7 @@ struct VbPackedDev {
     const uint64_t* seeds;       // [n_graphs]
     const uint32_t* thr;         // [n_graphs][R][64]
     const uint4* groups;         // [n_groups] {first slice, slices, first entry, entries}
+    const uint4* slice_meta;     // [n_slices] {first entry, width, graph, 0}
     int* err;                    // device status word (bounded waits)
     uint64_t* S;                 // [n_slots][R]
     uint64_t* snap;              // [n_tw][n_slots][R]

@@ -141,6 +141,13 @@ public:
         up((void*)d_.temp_index, h_tidx_.data(), h_tidx_.size() * 4);
         up((void*)d_.coef, h_coef_.data(), h_coef_.size() * 4);
         if (kernel_ == SG_SK_BLOCKED) {
+            if (!side_) {
+                check_cuda(cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking), "cudaStreamCreate");
+                for (int k = 0; k < 2; ++k) {
+                    check_cuda(cudaEventCreateWithFlags(&side_done_[k], cudaEventDisableTiming), "cudaEventCreate");
+                    check_cuda(cudaEventCreateWithFlags(&inblock_done_[k], cudaEventDisableTiming), "cudaEventCreate");
+                }
+            }
             if (autotune_) tune_block(st);
             set_block(B_);
         } else {
@@ -154,17 +161,51 @@ public:
 
     int block() const { return B_; }
 
+    ~SkModel() override {
+        for (int k = 0; k < 2; ++k) {
+            if (side_done_[k]) cudaEventDestroy(side_done_[k]);
+            if (inblock_done_[k]) cudaEventDestroy(inblock_done_[k]);
+        }
+        if (side_) cudaStreamDestroy(side_);
+    }
+
     void sweep(uint32_t t_off, cudaStream_t st) override {
         if (kernel_ == SG_SK_PLAIN) {
             launches += sk_plain_sweep(d_, clock_dev, t_off, st);
             return;
         }
+        // Critical path: in-block(b) -> field update of the rows of block b+1 -> in-block(b+1).
+        // The update of all other rows by block b runs on a side stream (a parallel graph
+        // branch) and is joined before in-block(b+2); rows updated from both branches use
+        // atomic adds, which commute, so the integers are the same as in sequential order.
         launches += sk_kstar_sweep(d_, clock_dev, t_off, st);
-        for (int b0 = 0; b0 < n_; b0 += B_) {
+        const int ntiles = Np_ / 128;
+        const int nblocks = (n_ + B_ - 1) / B_;
+        bool pending[2] = {false, false};
+        for (int b = 0; b < nblocks; ++b) {
+            const int b0 = b * B_;
+            if (pending[b & 1]) {  // the side-stream update of block b-2
+                check_cuda(cudaStreamWaitEvent(st, side_done_[b & 1], 0), "cudaStreamWaitEvent");
+                pending[b & 1] = false;
+            }
             if (sk_inblock(d_, b0, B_, st) < 0) fail(SG_EINVAL, "unsupported block size");
             ++launches;
-            launches += sk_field_update(d_, mapJ_, mapD_, b0, B_, kw_, NT_, 2, st);
+            // row tiles holding block b+1 (a whole tile may cover more than one block)
+            int nt0 = ntiles, nt1 = ntiles;
+            if (b + 1 < nblocks) {
+                nt0 = (b0 + B_) / 128;
+                nt1 = std::min(ntiles, (b0 + 2 * B_ + 127) / 128);
+            }
+            check_cuda(cudaEventRecord(inblock_done_[b & 1], st), "cudaEventRecord");
+            check_cuda(cudaStreamWaitEvent(side_, inblock_done_[b & 1], 0), "cudaStreamWaitEvent");
+            launches += sk_field_update_rows(d_, mapJ_, mapD_, b0, B_, kw_, NT_, 2, 0, nt0, 1, side_);
+            launches += sk_field_update_rows(d_, mapJ_, mapD_, b0, B_, kw_, NT_, 2, nt1, ntiles, 1, side_);
+            check_cuda(cudaEventRecord(side_done_[b & 1], side_), "cudaEventRecord");
+            pending[b & 1] = true;
+            launches += sk_field_update_rows(d_, mapJ_, mapD_, b0, B_, kw_, NT_, 2, nt0, nt1, 1, st);
         }
+        for (int k = 0; k < 2; ++k)
+            if (pending[k]) check_cuda(cudaStreamWaitEvent(st, side_done_[k], 0), "cudaStreamWaitEvent");
     }
 
     void snapshot(int w, cudaStream_t st) override { launches += sk_snapshot(d_, w, st); }
@@ -356,6 +397,8 @@ private:
     int kernel_ = SG_SK_BLOCKED;
     bool autotune_ = false;
     size_t ws_bytes_ = 0;
+    cudaStream_t side_ = nullptr;                      // branch for the off-critical-path update
+    cudaEvent_t side_done_[2] = {}, inblock_done_[2] = {};
     int n_ = 0, Np_ = 0, B_ = 128, kw_ = 128, NT_ = 128;
     uint64_t seed_ = 0;
     std::vector<uint8_t> h_J8_;

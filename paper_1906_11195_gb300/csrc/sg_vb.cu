@@ -165,6 +165,7 @@ public:
             up((void*)pk_.slice_graph, h_slice_graph_.data(), h_slice_graph_.size() * 4);
             up((void*)pk_.col, h_col_.data(), h_col_.size() * 4);
             up((void*)pk_.groups, h_groups_.data(), h_groups_.size() * sizeof(uint4));
+            up((void*)pk_.slice_meta, h_slice_meta_.data(), h_slice_meta_.size() * sizeof(uint4));
             check_cuda(cudaMemsetAsync(pk_.err, 0, 4, st), "memset");
             up((void*)pk_.jb, h_jb_.data(), h_jb_.size() * 8);
             std::vector<uint64_t> seeds(n_inst);
@@ -380,6 +381,7 @@ private:
             pk_.slice_graph = c.take<uint32_t>(h_slice_graph_.size());
             pk_.col = c.take<uint32_t>(h_col_.size());
             pk_.groups = c.take<uint4>(h_groups_.size());
+            pk_.slice_meta = c.take<uint4>(h_slice_meta_.size());
             pk_.err = c.take<int>(1);
             pk_.jb = c.take<uint64_t>(h_jb_.size());
             pk_.seeds = c.take<uint64_t>(n_inst);
@@ -530,6 +532,15 @@ private:
                 }
             }
         }
+        h_slice_meta_.resize(n_slices);
+        for (int64_t s = 0; s < n_slices; ++s) {
+            uint4 m;
+            m.x = h_slice_base_[s];
+            m.y = (h_slice_base_[s + 1] - h_slice_base_[s]) / 32;
+            m.z = h_slice_graph_[s];
+            m.w = 0;
+            h_slice_meta_[s] = m;
+        }
         // staging groups: consecutive slices of one colour, <= 8 slices and <= 1024 entries;
         // a single slice wider than that (degree > 32) forms a group flagged "wide"
         colour_group_.assign(cmax + 1, 0);
@@ -564,7 +575,7 @@ private:
     std::vector<uint32_t> thr_;
     // packed host layout
     std::vector<uint32_t> colour_slice_, colour_group_;
-    std::vector<uint4> h_groups_;
+    std::vector<uint4> h_groups_, h_slice_meta_;
     std::vector<std::vector<int64_t>> slot_of_;
     int64_t n_slots_ = 0;
     std::vector<uint32_t> h_vinfo_, h_slice_base_, h_slice_graph_, h_col_;

@@ -207,7 +207,7 @@ constexpr uint32_t kWaitPolls = 1u << 24;
 __global__ void __launch_bounds__(128) k_sk_field_mma(const __grid_constant__ CUtensorMap mapJ,
                                                       const __grid_constant__ CUtensorMap mapD,
                                                       SkDev d, int b0, int B, int kw, int NT,
-                                                      int scale) {
+                                                      int scale, int mt0, int atomic_add) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte aligned operand area
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(128) k_sk_field_mma(const __grid_constant__ CU
     uint32_t* tslot = (uint32_t*)(bars + 2);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.x * 128;
+    const int m0 = (mt0 + (int)blockIdx.x) * 128;
     const int n0 = blockIdx.y * NT;
     const uint32_t ncols = NT <= 32 ? 32u : (NT <= 64 ? 64u : (NT <= 128 ? 128u : 256u));
 
@@ -299,15 +299,26 @@ __global__ void __launch_bounds__(128) k_sk_field_mma(const __grid_constant__ CU
                 : "r"(ta));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             const int ncol = NT - c0 < 32 ? NT - c0 : 32;
-            // all loads of the chunk first (independent), then the adds and stores
-            int hv[32];
             int* hbase = d.H + (int64_t)(n0 + c0) * d.Np + row;
+            if (atomic_add) {
+                // concurrent updates of the same rows (row tiles split across streams) commute
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if (j < ncol) hv[j] = __ldcg(hbase + (int64_t)j * d.Np);
+                for (int j = 0; j < 32; ++j)
+                    if (j < ncol) {
+                        const int dv = __float2int_rn(__uint_as_float(v[j]));
+                        if (dv) atomicAdd(hbase + (int64_t)j * d.Np, scale * dv);
+                    }
+            } else {
+                // all loads of the chunk first (independent), then the adds and stores
+                int hv[32];
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if (j < ncol) hbase[(int64_t)j * d.Np] = hv[j] + scale * __float2int_rn(__uint_as_float(v[j]));
+                for (int j = 0; j < 32; ++j)
+                    if (j < ncol) hv[j] = __ldcg(hbase + (int64_t)j * d.Np);
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (j < ncol)
+                        hbase[(int64_t)j * d.Np] = hv[j] + scale * __float2int_rn(__uint_as_float(v[j]));
+            }
         }
     } else if (tid == 0) {
         // give any copies still in flight a bounded chance to land before the CTA exits
@@ -325,12 +336,20 @@ size_t sk_field_smem_bytes(int B, int kw, int NT) {
     return 1024 + (size_t)nchunks * (128 + NT) * kw + 64;
 }
 
+int sk_field_update_rows(const SkDev& d, const CUtensorMap& mapJ, const CUtensorMap& mapD, int b0,
+                         int B, int kw, int NT, int scale, int mt_begin, int mt_end,
+                         int atomic_add, cudaStream_t st) {
+    if (mt_end <= mt_begin) return 0;
+    const size_t smem = sk_field_smem_bytes(B, kw, NT);
+    dim3 grid((unsigned)(mt_end - mt_begin), (unsigned)(d.R / NT));
+    k_sk_field_mma<<<grid, 128, smem, st>>>(mapJ, mapD, d, b0, B, kw, NT, scale, mt_begin,
+                                            atomic_add);
+    return 1;
+}
+
 int sk_field_update(const SkDev& d, const CUtensorMap& mapJ, const CUtensorMap& mapD, int b0,
                     int B, int kw, int NT, int scale, cudaStream_t st) {
-    const size_t smem = sk_field_smem_bytes(B, kw, NT);
-    dim3 grid((unsigned)(d.Np / 128), (unsigned)(d.R / NT));
-    k_sk_field_mma<<<grid, 128, smem, st>>>(mapJ, mapD, d, b0, B, kw, NT, scale);
-    return 1;
+    return sk_field_update_rows(d, mapJ, mapD, b0, B, kw, NT, scale, 0, d.Np / 128, 0, st);
 }
 
 // The limit is a property of the kernel, shared by every handle: it only ever grows.

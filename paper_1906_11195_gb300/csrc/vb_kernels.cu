@@ -131,20 +131,23 @@ constexpr int kPlanes = 6;  // bit-sliced unsatisfied-edge counter, counts up to
 constexpr int kGroupSlices = 8;       // slices (warps) per staged group
 constexpr int kGroupEntries = 1024;   // staged sliced-ELL entries per group
 
-__device__ __forceinline__ void bitslice_add(uint64_t (&p)[kPlanes], uint64_t x) {
+// add one 64-lane word into a P-plane bit-sliced counter (the count never exceeds 2^P - 1)
+template <int P>
+__device__ __forceinline__ void bitslice_add(uint64_t (&p)[P], uint64_t x) {
 #pragma unroll
-    for (int b = 0; b < kPlanes; ++b) {
+    for (int b = 0; b < P; ++b) {
         const uint64_t c = p[b] & x;
         p[b] ^= x;
         x = c;
     }
 }
 
-// lanes whose counter value is >= k (k a per-thread scalar, 0 <= k <= 63)
-__device__ __forceinline__ uint64_t bitslice_ge(const uint64_t (&p)[kPlanes], int k) {
+// lanes whose counter value is >= k (k a per-thread scalar, 0 <= k <= 2^P - 1)
+template <int P>
+__device__ __forceinline__ uint64_t bitslice_ge(const uint64_t (&p)[P], int k) {
     uint64_t gt = 0ull, eq = ~0ull;
 #pragma unroll
-    for (int b = kPlanes - 1; b >= 0; --b) {
+    for (int b = P - 1; b >= 0; --b) {
         const uint64_t kb = ((k >> b) & 1) ? ~0ull : 0ull;
         gt |= eq & p[b] & ~kb;
         eq &= ~(p[b] ^ kb);
@@ -172,7 +175,40 @@ struct VbStage {
     uint32_t col[kGroupEntries];
     uint64_t S[kGroupSlices * 32 * R];
     uint32_t vinfo[kGroupSlices * 32];
+    uint4 meta[kGroupSlices];  // per slice: first entry, width, graph, 0
 };
+
+// Count the unsatisfied edges of one vertex (all lanes, all replicas) with a P-plane counter
+// and flip the lanes whose count reaches kmin.  Neighbour words come from the stage, or straight
+// from global memory for a wide slice (stage == nullptr).
+template <int R, int P>
+__device__ __forceinline__ void count_and_flip(SpinWords<R>& si, const VbStage<R>* stage,
+                                               uint32_t loc, uint32_t width, const VbPackedDev& d,
+                                               uint32_t idx, const int (&kmin)[R]) {
+    uint64_t planes[R][P];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int b = 0; b < P; ++b) planes[r][b] = 0ull;
+    if (stage) {
+        for (uint32_t e = 0; e < width; ++e, loc += 32) {
+            const uint64_t J = stage->J[loc];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                bitslice_add<P>(planes[r], si.v[r] ^ stage->gath[loc * R + r] ^ J);
+        }
+    } else {
+        for (uint32_t e = 0; e < width; ++e, idx += 32) {
+            const uint32_t j = __ldg(d.col + idx);
+            const uint64_t J = __ldg(d.jb + idx);
+            const SpinWords<R> sj = gather_words<R>(d.S + (int64_t)j * R);
+#pragma unroll
+            for (int r = 0; r < R; ++r) bitslice_add<P>(planes[r], si.v[r] ^ sj.v[r] ^ J);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) si.v[r] ^= bitslice_ge<P>(planes[r], kmin[r]);
+}
 
 constexpr uint32_t kStagePolls = 1u << 24;
 
@@ -216,8 +252,9 @@ __global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_
         const uint32_t nsl = gi.y & ~kWideGroup;
         const bool wide = (gi.y & kWideGroup) != 0u;
         const uint32_t nslot = nsl * 32u;
-        const uint32_t bytes = nslot * 4u + nslot * R * 8u + (wide ? 0u : gi.w * 12u);
+        const uint32_t bytes = nslot * 4u + nslot * R * 8u + nsl * 16u + (wide ? 0u : gi.w * 12u);
         mbar_expect_tx(&bars[s], bytes);
+        bulk_copy_g2s_hint(stage[s].meta, d.slice_meta + gi.x, nsl * 16u, &bars[s], pol_stream);
         bulk_copy_g2s_hint(stage[s].vinfo, d.vinfo + (int64_t)gi.x * 32, nslot * 4u, &bars[s],
                            pol_stream);
         bulk_copy_g2s_hint(stage[s].S, S + (int64_t)gi.x * 32 * R, nslot * R * 8u, &bars[s],
@@ -232,11 +269,10 @@ __global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_
         const uint4 gi = __ldg(&d.groups[g]);
         const uint32_t nsl = gi.y & ~kWideGroup;
         if (warp < nsl && !(gi.y & kWideGroup)) {
-            const uint32_t slice = gi.x + warp;
             if (stage[s].vinfo[warp * 32 + lane] != kInactive) {
-                const uint32_t base = __ldg(d.slice_base + slice);
-                const uint32_t width = (__ldg(d.slice_base + slice + 1) - base) >> 5;
-                uint32_t loc = base - gi.z + lane;
+                const uint4 m = stage[s].meta[warp];
+                const uint32_t width = m.y;
+                uint32_t loc = m.x - gi.z + lane;
                 for (uint32_t e = 0; e < width; ++e, loc += 32)
                     gather_async<R>(&stage[s].gath[loc * R], S + (int64_t)stage[s].col[loc] * R,
                                     pol_keep);
@@ -274,49 +310,36 @@ __global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_
             const uint32_t slice = gi.x + warp;
             const uint32_t vi = stage[s].vinfo[warp * 32 + lane];
             if (vi != kInactive) {
-                const uint32_t base = __ldg(d.slice_base + slice);
-                const uint32_t width = (__ldg(d.slice_base + slice + 1) - base) >> 5;
-                const uint32_t gr = __ldg(d.slice_graph + slice);
+                const uint4 m = stage[s].meta[warp];  // first entry, width, graph
+                const uint32_t width = m.y, gr = m.z;
                 const int deg = (int)(vi >> kDegShift);
                 const uint32_t orig = vi & kOrigMask;
                 const uint64_t seed = __ldg(d.seeds + gr);
                 SpinWords<R> si;
 #pragma unroll
                 for (int r = 0; r < R; ++r) si.v[r] = stage[s].S[(warp * 32 + lane) * R + r];
-                uint64_t planes[R][kPlanes];
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-#pragma unroll
-                    for (int b = 0; b < kPlanes; ++b) planes[r][b] = 0ull;
-                if (!wide) {
-                    uint32_t loc = base - gi.z + lane;
-                    for (uint32_t e = 0; e < width; ++e, loc += 32) {
-                        const uint64_t J = stage[s].J[loc];
-#pragma unroll
-                        for (int r = 0; r < R; ++r)
-                            bitslice_add(planes[r], si.v[r] ^ stage[s].gath[loc * R + r] ^ J);
-                    }
-                } else {
-                    uint32_t idx = base + lane;
-                    for (uint32_t e = 0; e < width; ++e, idx += 32) {
-                        const uint32_t j = __ldg(d.col + idx);
-                        const uint64_t J = __ldg(d.jb + idx);
-                        const SpinWords<R> sj = gather_words<R>(S + (int64_t)j * R);
-#pragma unroll
-                        for (int r = 0; r < R; ++r) bitslice_add(planes[r], si.v[r] ^ sj.v[r] ^ J);
-                    }
-                }
-                // one Philox block per (vertex, sweep) serves replicas 0..3
+                // one Philox block per (vertex, sweep) serves replicas 0..3; the accepted
+                // m form a prefix 1..m*, so a lane flips iff u >= ceil((d - m*) / 2)
                 const uint4 rnd = philox4x32_10(make_uint4(orig, t, 0u, 0u), (uint32_t)seed,
                                                 (uint32_t)(seed >> 32));
                 const uint32_t* thr = d.thr + (size_t)gr * R * kVbThrStride;
+                int kmin[R];
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const uint32_t r32 = uint4_word(rnd, r);
                     int ms = 0;
                     while (ms < deg && r32 < __ldg(thr + r * kVbThrStride + ms + 1)) ++ms;
-                    si.v[r] ^= bitslice_ge(planes[r], (deg - ms + 1) >> 1);
+                    kmin[r] = (deg - ms + 1) >> 1;
                 }
+                const VbStage<R>* sp = wide ? nullptr : &stage[s];
+                const uint32_t loc = m.x - gi.z + lane, idx = m.x + lane;
+                // the slice's width (warp-uniform) sets the counter size
+                if (width <= 1) count_and_flip<R, 1>(si, sp, loc, width, d, idx, kmin);
+                else if (width <= 3) count_and_flip<R, 2>(si, sp, loc, width, d, idx, kmin);
+                else if (width <= 7) count_and_flip<R, 3>(si, sp, loc, width, d, idx, kmin);
+                else if (width <= 15) count_and_flip<R, 4>(si, sp, loc, width, d, idx, kmin);
+                else if (width <= 31) count_and_flip<R, 5>(si, sp, loc, width, d, idx, kmin);
+                else count_and_flip<R, 6>(si, sp, loc, width, d, idx, kmin);
                 store_words_keep<R>(d.S + ((int64_t)slice * 32 + lane) * R, si, pol_keep);
             }
         }
