@@ -120,6 +120,8 @@ struct VbPackedDev {
     const uint32_t* thr;         // [n_graphs][R][64]
     const uint4* groups;         // [n_groups] {first slice, slices, first entry, entries}
     const uint4* slice_meta;     // [n_slices] {first entry, width, graph, 0}
+    const uint32_t* group_graph; // [n_groups] graph of each group (groups never mix graphs)
+    const uint8_t* gtab;         // [n_graphs] {uint32 thr[R][64]; uint64 seed; uint64 pad}
     int* err;                    // device status word (bounded waits)
     uint64_t* S;                 // [n_slots][R]
     uint64_t* snap;              // [n_tw][n_slots][R]

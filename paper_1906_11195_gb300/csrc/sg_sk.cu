@@ -148,6 +148,7 @@ public:
                     check_cuda(cudaEventCreateWithFlags(&inblock_done_[k], cudaEventDisableTiming), "cudaEventCreate");
                 }
             }
+            if (sk_inblock_prepare() != 0) fail(SG_ECUDA, "cannot raise the in-block kernel's shared memory limit");
             if (autotune_) tune_block(st);
             set_block(B_);
         } else {
@@ -174,27 +175,37 @@ public:
             launches += sk_plain_sweep(d_, clock_dev, t_off, st);
             return;
         }
-        // Critical path: in-block(b) -> field update of the rows of block b+1 -> in-block(b+1).
-        // The update of all other rows by block b runs on a side stream (a parallel graph
-        // branch) and is joined before in-block(b+2); rows updated from both branches use
-        // atomic adds, which commute, so the integers are the same as in sequential order.
         launches += sk_kstar_sweep(d_, clock_dev, t_off, st);
         const int ntiles = Np_ / 128;
         const int nblocks = (n_ + B_ - 1) / B_;
+        if (B_ < 128) {
+            // a row tile spans two blocks: plain sequence in-block(b) -> full field update
+            for (int b = 0; b < nblocks; ++b) {
+                if (sk_inblock(d_, b * B_, -1, B_, st) < 0) fail(SG_EINVAL, "unsupported block size");
+                ++launches;
+                launches += sk_field_update(d_, mapJ_, mapD_, b * B_, B_, kw_, NT_, 2, st);
+            }
+            return;
+        }
+        // Critical path: in-block(b) only.  It folds the previous block's flips into its own
+        // rows; the tensor-core update of all other rows by block b runs on a side stream (a
+        // parallel graph branch) and is joined before in-block(b+2), the first to need it.
+        // Both branches add into disjoint rows or with atomics, so the integers are exact.
         bool pending[2] = {false, false};
         for (int b = 0; b < nblocks; ++b) {
             const int b0 = b * B_;
-            if (pending[b & 1]) {  // the side-stream update of block b-2
+            if (pending[b & 1]) {
                 check_cuda(cudaStreamWaitEvent(st, side_done_[b & 1], 0), "cudaStreamWaitEvent");
                 pending[b & 1] = false;
             }
-            if (sk_inblock(d_, b0, B_, st) < 0) fail(SG_EINVAL, "unsupported block size");
+            if (sk_inblock(d_, b0, b > 0 ? b0 - B_ : -1, B_, st) < 0)
+                fail(SG_EINVAL, "unsupported block size");
             ++launches;
-            // row tiles holding block b+1 (a whole tile may cover more than one block)
+            // rows of block b+1 are left to in-block(b+1); the last block updates every row
             int nt0 = ntiles, nt1 = ntiles;
             if (b + 1 < nblocks) {
                 nt0 = (b0 + B_) / 128;
-                nt1 = std::min(ntiles, (b0 + 2 * B_ + 127) / 128);
+                nt1 = (b0 + 2 * B_) / 128;
             }
             check_cuda(cudaEventRecord(inblock_done_[b & 1], st), "cudaEventRecord");
             check_cuda(cudaStreamWaitEvent(side_, inblock_done_[b & 1], 0), "cudaStreamWaitEvent");
@@ -202,7 +213,6 @@ public:
             launches += sk_field_update_rows(d_, mapJ_, mapD_, b0, B_, kw_, NT_, 2, nt1, ntiles, 1, side_);
             check_cuda(cudaEventRecord(side_done_[b & 1], side_), "cudaEventRecord");
             pending[b & 1] = true;
-            launches += sk_field_update_rows(d_, mapJ_, mapD_, b0, B_, kw_, NT_, 2, nt0, nt1, 1, st);
         }
         for (int k = 0; k < 2; ++k)
             if (pending[k]) check_cuda(cudaStreamWaitEvent(st, side_done_[k], 0), "cudaStreamWaitEvent");
@@ -380,6 +390,7 @@ private:
         d_.D = c.take<uint8_t>((size_t)R * Np_);
         d_.H = c.take<int32_t>((size_t)R * Np_);
         d_.kst = c.take<int32_t>(kernel_ == SG_SK_BLOCKED ? (size_t)R * Np_ : 0);
+        d_.flips = c.take<uint32_t>(kernel_ == SG_SK_BLOCKED ? (size_t)R * words : 0);
         d_.snap = c.take<uint32_t>((size_t)R * words * tw.size());
         d_.err = c.take<int>(1);
         d_.seed = seed_;

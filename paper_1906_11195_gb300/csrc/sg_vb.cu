@@ -166,6 +166,8 @@ public:
             up((void*)pk_.col, h_col_.data(), h_col_.size() * 4);
             up((void*)pk_.groups, h_groups_.data(), h_groups_.size() * sizeof(uint4));
             up((void*)pk_.slice_meta, h_slice_meta_.data(), h_slice_meta_.size() * sizeof(uint4));
+            up((void*)pk_.group_graph, h_group_graph_.data(), h_group_graph_.size() * 4);
+            up((void*)pk_.gtab, h_gtab_.data(), h_gtab_.size());
             check_cuda(cudaMemsetAsync(pk_.err, 0, 4, st), "memset");
             up((void*)pk_.jb, h_jb_.data(), h_jb_.size() * 8);
             std::vector<uint64_t> seeds(n_inst);
@@ -382,6 +384,8 @@ private:
             pk_.col = c.take<uint32_t>(h_col_.size());
             pk_.groups = c.take<uint4>(h_groups_.size());
             pk_.slice_meta = c.take<uint4>(h_slice_meta_.size());
+            pk_.group_graph = c.take<uint32_t>(h_group_graph_.size());
+            pk_.gtab = c.take<uint8_t>(h_gtab_.size());
             pk_.err = c.take<int>(1);
             pk_.jb = c.take<uint64_t>(h_jb_.size());
             pk_.seeds = c.take<uint64_t>(n_inst);
@@ -550,6 +554,7 @@ private:
             while (s < (int64_t)colour_slice_[c + 1]) {
                 const int64_t first = s;
                 while (s < (int64_t)colour_slice_[c + 1] && s - first < 8 &&
+                       h_slice_graph_[s] == h_slice_graph_[first] &&
                        (int64_t)h_slice_base_[s + 1] - (int64_t)h_slice_base_[first] <= 1024)
                     ++s;
                 bool wide = false;
@@ -563,7 +568,16 @@ private:
                 gi.z = h_slice_base_[first];
                 gi.w = h_slice_base_[s] - h_slice_base_[first];
                 h_groups_.push_back(gi);
+                h_group_graph_.push_back(h_slice_graph_[first]);
             }
+        }
+        // per-graph table staged with each group: thresholds of the R replicas, then the key
+        const size_t gtab_bytes = (size_t)R * kVbThrStride * 4 + 16;
+        h_gtab_.assign(gtab_bytes * n_inst, 0);
+        for (int b = 0; b < n_inst; ++b) {
+            memcpy(&h_gtab_[b * gtab_bytes], &thr_[(size_t)b * R * kVbThrStride],
+                   (size_t)R * kVbThrStride * 4);
+            memcpy(&h_gtab_[b * gtab_bytes + (size_t)R * kVbThrStride * 4], &graphs_[b].seed, 8);
         }
         colour_group_[cmax] = (uint32_t)h_groups_.size();
     }
@@ -576,6 +590,8 @@ private:
     // packed host layout
     std::vector<uint32_t> colour_slice_, colour_group_;
     std::vector<uint4> h_groups_, h_slice_meta_;
+    std::vector<uint32_t> h_group_graph_;
+    std::vector<uint8_t> h_gtab_;
     std::vector<std::vector<int64_t>> slot_of_;
     int64_t n_slots_ = 0;
     std::vector<uint32_t> h_vinfo_, h_slice_base_, h_slice_graph_, h_col_;

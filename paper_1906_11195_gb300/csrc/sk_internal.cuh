@@ -18,6 +18,7 @@ struct SkDev {
     uint8_t* D;               // [R][Np] e4m3 spin changes (s' - s)/2 of the current block
     int32_t* H;               // [R][Np] local fields sum_j J_ij s_j
     int32_t* kst;             // [R][Np] K* of the current sweep (largest accepted k)
+    uint32_t* flips;          // [R][Np/32] flip masks written by the latest in-block update
     uint32_t* snap;           // [n_tw][R][Np/32]
     int* err;                 // device status word
     uint64_t seed;
@@ -26,7 +27,9 @@ struct SkDev {
 
 int sk_init(const SkDev& d, cudaStream_t st);
 int sk_kstar_sweep(const SkDev& d, const uint32_t* clock, uint32_t t_off, cudaStream_t st);
-int sk_inblock(const SkDev& d, int b0, int B, cudaStream_t st);
+// prev_b0 < 0: no previous-block update folded in (the caller's field GEMM covered those rows)
+int sk_inblock(const SkDev& d, int b0, int prev_b0, int B, cudaStream_t st);
+int sk_inblock_prepare();
 size_t sk_field_smem_bytes(int B, int kw, int NT);
 int sk_field_prepare(int B, int kw, int NT);
 int sk_field_update(const SkDev& d, const CUtensorMap& mapJ, const CUtensorMap& mapD, int b0,

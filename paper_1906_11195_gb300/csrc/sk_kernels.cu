@@ -101,18 +101,26 @@ int sk_kstar_sweep(const SkDev& d, const uint32_t* clock, uint32_t t_off, cudaSt
 }
 
 // --------------------------------------------------------------------------------------------
-// in-block sequential update, one warp per replica; the block's couplings (B rows x B/32 words)
-// are staged once per CTA in shared memory and shared by its 8 replicas
+// in-block sequential update, one warp per replica.  The CTA stages the couplings of the
+// block's rows with the block's own columns (and, when prev_b0 >= 0, with the previous block's
+// columns) in shared memory; its 8 replicas share them.
+// When prev_b0 >= 0 the kernel first adds the previous block's flips to the fields of its own
+// rows (popcounts over bit-packed couplings, written back to H): that update is on the
+// sequential critical path, while the tensor-core update of every other row runs elsewhere.
 // --------------------------------------------------------------------------------------------
 template <int NC>
-__global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0) {
-    extern __shared__ uint32_t jblk[];  // [32 * NC rows][NC words]
+__global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0, int prev_b0) {
+    extern __shared__ uint32_t jblk[];  // [32 * NC rows][2 * NC words]: own cols, previous cols
+    constexpr int W = 2 * NC;
     const int lane = threadIdx.x & 31;
     const int words = d.Np / 32;
     const int wb = b0 / 32;
-    for (int k = threadIdx.x; k < 32 * NC * NC; k += blockDim.x) {
-        const int row = k / NC, w = k % NC;
-        jblk[k] = d.Jbits[(int64_t)(b0 + row) * words + wb + w];
+    const int pwb = prev_b0 >= 0 ? prev_b0 / 32 : 0;
+    const int nw = prev_b0 >= 0 ? W : NC;
+    for (int k = threadIdx.x; k < 32 * NC * nw; k += blockDim.x) {
+        const int row = k / nw, w = k % nw;
+        const int col_word = w < NC ? wb + w : pwb + (w - NC);
+        jblk[row * W + w] = d.Jbits[(int64_t)(b0 + row) * words + col_word];
     }
     __syncthreads();
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -127,12 +135,33 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0) {
         kst[c] = d.kst[(int64_t)r * d.Np + i];
         sw[c] = d.S[(int64_t)r * words + wb + c];
     }
+    if (prev_b0 >= 0) {
+        // fields += 2 sum_{j flipped in the previous block} J_ij s_j'
+        int dh[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) dh[c] = 0;
+#pragma unroll
+        for (int cp = 0; cp < NC; ++cp) {
+            const uint32_t F = d.flips[(int64_t)r * words + pwb + cp];
+            if (!F) continue;
+            const uint32_t sn = d.S[(int64_t)r * words + pwb + cp];
+            const int pf = __popc(F);
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                dh[c] += 2 * (pf - 2 * __popc(F & (jblk[(32 * c + lane) * W + NC + cp] ^ sn)));
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            if (dh[c]) d.H[(int64_t)r * d.Np + b0 + 32 * c + lane] = h[c] + dh[c];
+            h[c] += dh[c];
+        }
+    }
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         const int i = b0 + 32 * c + lane;
         const uint32_t sbit = (sw[c] >> lane) & 1u;
         const int x = sbit ? -h[c] : h[c];
-        const uint32_t neg = jblk[(32 * c + lane) * NC + c] ^ sw[c] ^ (sbit ? 0xFFFFFFFFu : 0u);
+        const uint32_t neg = jblk[(32 * c + lane) * W + c] ^ sw[c] ^ (sbit ? 0xFFFFFFFFu : 0u);
         uint32_t F = 0;
         int resolved = 0;
         while (resolved < 32) {
@@ -148,13 +177,16 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0) {
         // changes D_i = (s' - s)/2 for the field GEMM: -s_old where flipped
         const int dval = ((F >> lane) & 1u) ? (sbit ? 1 : -1) : 0;
         d.D[(int64_t)r * d.Np + i] = e4m3_of_sign(dval);
-        if (lane == 0) d.S[(int64_t)r * words + wb + c] = nsw;
+        if (lane == 0) {
+            d.S[(int64_t)r * words + wb + c] = nsw;
+            d.flips[(int64_t)r * words + wb + c] = F;
+        }
         // fields of the later rows of this block: h += 2 sum_{j in F} J_ij s_j'
         if (F) {
             const int pf = __popc(F);
 #pragma unroll
             for (int c2 = c + 1; c2 < NC; ++c2) {
-                const uint32_t m = jblk[(32 * c2 + lane) * NC + c] ^ nsw;
+                const uint32_t m = jblk[(32 * c2 + lane) * W + c] ^ nsw;
                 h[c2] += 2 * (pf - 2 * __popc(F & m));
             }
         }
@@ -162,19 +194,25 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0) {
     }
 }
 
-int sk_inblock(const SkDev& d, int b0, int B, cudaStream_t st) {
+int sk_inblock(const SkDev& d, int b0, int prev_b0, int B, cudaStream_t st) {
     const unsigned nb = (unsigned)((d.R + 7) / 8);
     const int nc = B / 32;
-    const size_t smem = (size_t)32 * nc * nc * 4;
+    const size_t smem = (size_t)32 * nc * 2 * nc * 4;
     switch (nc) {
-        case 1: k_sk_inblock<1><<<nb, 256, smem, st>>>(d, b0); break;
-        case 2: k_sk_inblock<2><<<nb, 256, smem, st>>>(d, b0); break;
-        case 4: k_sk_inblock<4><<<nb, 256, smem, st>>>(d, b0); break;
-        case 8: k_sk_inblock<8><<<nb, 256, smem, st>>>(d, b0); break;
-        case 16: k_sk_inblock<16><<<nb, 256, smem, st>>>(d, b0); break;
+        case 2: k_sk_inblock<2><<<nb, 256, smem, st>>>(d, b0, prev_b0); break;
+        case 4: k_sk_inblock<4><<<nb, 256, smem, st>>>(d, b0, prev_b0); break;
+        case 8: k_sk_inblock<8><<<nb, 256, smem, st>>>(d, b0, prev_b0); break;
+        case 16: k_sk_inblock<16><<<nb, 256, smem, st>>>(d, b0, prev_b0); break;
         default: return -1;
     }
     return 1;
+}
+
+int sk_inblock_prepare() {
+    const cudaError_t e = cudaFuncSetAttribute(k_sk_inblock<16>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               32 * 16 * 32 * 4);
+    return e == cudaSuccess ? 0 : -1;
 }
 
 // --------------------------------------------------------------------------------------------

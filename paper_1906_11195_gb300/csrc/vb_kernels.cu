@@ -176,6 +176,8 @@ struct VbStage {
     uint64_t S[kGroupSlices * 32 * R];
     uint32_t vinfo[kGroupSlices * 32];
     uint4 meta[kGroupSlices];  // per slice: first entry, width, graph, 0
+    uint32_t thr[R * kVbThrStride];  // the group's graph: thresholds of its replicas ...
+    uint64_t seed[2];                // ... and its Philox key
 };
 
 // Count the unsatisfied edges of one vertex (all lanes, all replicas) with a P-plane counter
@@ -252,9 +254,13 @@ __global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_
         const uint32_t nsl = gi.y & ~kWideGroup;
         const bool wide = (gi.y & kWideGroup) != 0u;
         const uint32_t nslot = nsl * 32u;
-        const uint32_t bytes = nslot * 4u + nslot * R * 8u + nsl * 16u + (wide ? 0u : gi.w * 12u);
+        const uint32_t gtab_bytes = R * kVbThrStride * 4u + 16u;
+        const uint32_t bytes =
+            nslot * 4u + nslot * R * 8u + nsl * 16u + gtab_bytes + (wide ? 0u : gi.w * 12u);
         mbar_expect_tx(&bars[s], bytes);
         bulk_copy_g2s_hint(stage[s].meta, d.slice_meta + gi.x, nsl * 16u, &bars[s], pol_stream);
+        bulk_copy_g2s(stage[s].thr, d.gtab + (size_t)d.group_graph[g] * gtab_bytes, gtab_bytes,
+                      &bars[s]);
         bulk_copy_g2s_hint(stage[s].vinfo, d.vinfo + (int64_t)gi.x * 32, nslot * 4u, &bars[s],
                            pol_stream);
         bulk_copy_g2s_hint(stage[s].S, S + (int64_t)gi.x * 32 * R, nslot * R * 8u, &bars[s],
@@ -265,7 +271,7 @@ __global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_
         }
     };
     // every thread: start the copies of its neighbours' words for the staged group
-    auto issue_gathers = [&](uint32_t g, int s) {
+    auto issue_gathers = [&](uint32_t g, int s) -> uint4 {
         const uint4 gi = __ldg(&d.groups[g]);
         const uint32_t nsl = gi.y & ~kWideGroup;
         if (warp < nsl && !(gi.y & kWideGroup)) {
@@ -279,6 +285,7 @@ __global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_
             }
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
+        return gi;
     };
 
     const uint32_t g0 = g_begin + blockIdx.x, stride = gridDim.x;
@@ -287,34 +294,35 @@ __global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_
         if (g0 + stride < g_end) issue_stage(g0 + stride, 1);
     }
     bool ok = true;
+    uint4 gi_next = make_uint4(0u, 0u, 0u, 0u);
     if (g0 < g_end) {
         ok = __syncthreads_and(mbar_wait(&bars[0], 0, kStagePolls));
-        if (ok) issue_gathers(g0, 0);
+        if (ok) gi_next = issue_gathers(g0, 0);
     }
     uint32_t it = 0;
     for (uint32_t g = g0; ok && g < g_end; g += stride, ++it) {
         const int s = (int)(it & 1u);
         const uint32_t gn = g + stride;
+        const uint4 gi = gi_next;
         if (gn < g_end) {
             ok = __syncthreads_and(mbar_wait(&bars[s ^ 1], ((it + 1) >> 1) & 1u, kStagePolls));
             if (!ok) break;
-            issue_gathers(gn, s ^ 1);
+            gi_next = issue_gathers(gn, s ^ 1);
             asm volatile("cp.async.wait_group 1;" ::: "memory");
         } else {
             asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
-        const uint4 gi = __ldg(&d.groups[g]);
         const uint32_t nsl = gi.y & ~kWideGroup;
         const bool wide = (gi.y & kWideGroup) != 0u;
         if (warp < nsl) {
             const uint32_t slice = gi.x + warp;
             const uint32_t vi = stage[s].vinfo[warp * 32 + lane];
             if (vi != kInactive) {
-                const uint4 m = stage[s].meta[warp];  // first entry, width, graph
-                const uint32_t width = m.y, gr = m.z;
+                const uint4 m = stage[s].meta[warp];  // first entry, width
+                const uint32_t width = m.y;
                 const int deg = (int)(vi >> kDegShift);
                 const uint32_t orig = vi & kOrigMask;
-                const uint64_t seed = __ldg(d.seeds + gr);
+                const uint64_t seed = stage[s].seed[0];
                 SpinWords<R> si;
 #pragma unroll
                 for (int r = 0; r < R; ++r) si.v[r] = stage[s].S[(warp * 32 + lane) * R + r];
@@ -322,13 +330,13 @@ __global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_
                 // m form a prefix 1..m*, so a lane flips iff u >= ceil((d - m*) / 2)
                 const uint4 rnd = philox4x32_10(make_uint4(orig, t, 0u, 0u), (uint32_t)seed,
                                                 (uint32_t)(seed >> 32));
-                const uint32_t* thr = d.thr + (size_t)gr * R * kVbThrStride;
+                const uint32_t* thr = stage[s].thr;
                 int kmin[R];
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const uint32_t r32 = uint4_word(rnd, r);
                     int ms = 0;
-                    while (ms < deg && r32 < __ldg(thr + r * kVbThrStride + ms + 1)) ++ms;
+                    while (ms < deg && r32 < thr[r * kVbThrStride + ms + 1]) ++ms;
                     kmin[r] = (deg - ms + 1) >> 1;
                 }
                 const VbStage<R>* sp = wide ? nullptr : &stage[s];
