@@ -206,8 +206,10 @@ def run_profile_case(args):
     _build.build()
     torch.cuda.set_device(0)
     rp, col, jb = instance(0)
-    g = dict(row_ptr=rp, col=col, jbits=jb, seed=1, temps=[TEMPS[0]] * REPLICAS)
-    run = sg.VBRun([g], n_lanes=LANES, n_replicas=REPLICAS, kernel=sg.SG_VB_PACKED)
+    temps = [TEMPS[0]] * REPLICAS if args.profile_replicas == 2 else \
+        [T for T in TEMPS for _ in range(args.profile_replicas // len(TEMPS))]
+    g = dict(row_ptr=rp, col=col, jbits=jb, seed=1, temps=temps)
+    run = sg.VBRun([g], n_lanes=LANES, n_replicas=len(temps), kernel=sg.SG_VB_PACKED)
     run.sweep(args.warmup)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -489,6 +491,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
                     help="run only the single-instance sweep case used for ncu captures")
+    ap.add_argument("--profile-replicas", type=int, default=2, choices=[2, 4],
+                    help="replicas of the profile case (4: two per temperature)")
     ap.add_argument("--workload", default="vb", choices=["vb", "sk", "vb_batch"],
                     help="vb: the headline bit-packed Viana-Bray line; sk: the SK blocked line; "
                          "vb_batch: the uneven batch of Viana-Bray graphs")

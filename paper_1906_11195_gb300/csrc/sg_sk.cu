@@ -160,8 +160,6 @@ public:
         if (device_status(st)) fail(SG_ETIMEOUT, "device wait expired during initialisation");
     }
 
-    int block() const { return B_; }
-
     ~SkModel() override {
         for (int k = 0; k < 2; ++k) {
             if (side_done_[k]) cudaEventDestroy(side_done_[k]);
@@ -201,16 +199,18 @@ public:
             if (sk_inblock(d_, b0, b > 0 ? b0 - B_ : -1, B_, st) < 0)
                 fail(SG_EINVAL, "unsupported block size");
             ++launches;
-            // rows of block b+1 are left to in-block(b+1); the last block updates every row
-            int nt0 = ntiles, nt1 = ntiles;
+            // rows of block b+1 are left to in-block(b+1); the last block updates every row.
+            // The rows written here are disjoint from those in-block(b+1) writes concurrently,
+            // and the side stream runs its updates one after another: no atomics needed.
+            int skip0 = 0, skip1 = 0;
             if (b + 1 < nblocks) {
-                nt0 = (b0 + B_) / 128;
-                nt1 = (b0 + 2 * B_) / 128;
+                skip0 = (b0 + B_) / 128;
+                skip1 = std::min(ntiles, (b0 + 2 * B_) / 128);
             }
             check_cuda(cudaEventRecord(inblock_done_[b & 1], st), "cudaEventRecord");
             check_cuda(cudaStreamWaitEvent(side_, inblock_done_[b & 1], 0), "cudaStreamWaitEvent");
-            launches += sk_field_update_rows(d_, mapJ_, mapD_, b0, B_, kw_, NT_, 2, 0, nt0, 1, side_);
-            launches += sk_field_update_rows(d_, mapJ_, mapD_, b0, B_, kw_, NT_, 2, nt1, ntiles, 1, side_);
+            launches += sk_field_update_rows(d_, mapJ_, mapD_, b0, B_, kw_, NT_, 2, skip0, skip1, 0,
+                                             side_);
             check_cuda(cudaEventRecord(side_done_[b & 1], side_), "cudaEventRecord");
             pending[b & 1] = true;
         }

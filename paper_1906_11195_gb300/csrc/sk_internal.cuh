@@ -34,11 +34,11 @@ size_t sk_field_smem_bytes(int B, int kw, int NT);
 int sk_field_prepare(int B, int kw, int NT);
 int sk_field_update(const SkDev& d, const CUtensorMap& mapJ, const CUtensorMap& mapD, int b0,
                     int B, int kw, int NT, int scale, cudaStream_t st);
-// same on row tiles [mt_begin, mt_end) only; atomic_add = 1 when another launch may update
+// same on every row tile except [skip0, skip1); atomic_add = 1 when another launch may update
 // the same rows concurrently
 int sk_field_update_rows(const SkDev& d, const CUtensorMap& mapJ, const CUtensorMap& mapD, int b0,
-                         int B, int kw, int NT, int scale, int mt_begin, int mt_end,
-                         int atomic_add, cudaStream_t st);
+                         int B, int kw, int NT, int scale, int skip0, int skip1, int atomic_add,
+                         cudaStream_t st);
 size_t sk_plain_smem_bytes(int Np);
 int sk_plain_prepare(int Np);
 int sk_plain_sweep(const SkDev& d, const uint32_t* clock, uint32_t t_off, cudaStream_t st);

@@ -245,7 +245,8 @@ constexpr uint32_t kWaitPolls = 1u << 24;
 __global__ void __launch_bounds__(128) k_sk_field_mma(const __grid_constant__ CUtensorMap mapJ,
                                                       const __grid_constant__ CUtensorMap mapD,
                                                       SkDev d, int b0, int B, int kw, int NT,
-                                                      int scale, int mt0, int atomic_add) {
+                                                      int scale, int skip0, int skip1,
+                                                      int atomic_add) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte aligned operand area
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -256,7 +257,13 @@ __global__ void __launch_bounds__(128) k_sk_field_mma(const __grid_constant__ CU
     uint32_t* tslot = (uint32_t*)(bars + 2);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int m0 = (mt0 + (int)blockIdx.x) * 128;
+    // row tiles [0, ntiles) without [skip0, skip1)
+    const int tile = (int)blockIdx.x < skip0 ? (int)blockIdx.x : (int)blockIdx.x + (skip1 - skip0);
+    const int m0 = tile * 128;
+    if (threadIdx.x == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapJ)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapD)) : "memory");
+    }
     const int n0 = blockIdx.y * NT;
     const uint32_t ncols = NT <= 32 ? 32u : (NT <= 64 ? 64u : (NT <= 128 ? 128u : 256u));
 
@@ -375,19 +382,21 @@ size_t sk_field_smem_bytes(int B, int kw, int NT) {
 }
 
 int sk_field_update_rows(const SkDev& d, const CUtensorMap& mapJ, const CUtensorMap& mapD, int b0,
-                         int B, int kw, int NT, int scale, int mt_begin, int mt_end,
-                         int atomic_add, cudaStream_t st) {
-    if (mt_end <= mt_begin) return 0;
+                         int B, int kw, int NT, int scale, int skip0, int skip1, int atomic_add,
+                         cudaStream_t st) {
+    const int ntiles = d.Np / 128;
+    const int n = ntiles - (skip1 - skip0);
+    if (n <= 0) return 0;
     const size_t smem = sk_field_smem_bytes(B, kw, NT);
-    dim3 grid((unsigned)(mt_end - mt_begin), (unsigned)(d.R / NT));
-    k_sk_field_mma<<<grid, 128, smem, st>>>(mapJ, mapD, d, b0, B, kw, NT, scale, mt_begin,
+    dim3 grid((unsigned)n, (unsigned)(d.R / NT));
+    k_sk_field_mma<<<grid, 128, smem, st>>>(mapJ, mapD, d, b0, B, kw, NT, scale, skip0, skip1,
                                             atomic_add);
     return 1;
 }
 
 int sk_field_update(const SkDev& d, const CUtensorMap& mapJ, const CUtensorMap& mapD, int b0,
                     int B, int kw, int NT, int scale, cudaStream_t st) {
-    return sk_field_update_rows(d, mapJ, mapD, b0, B, kw, NT, scale, 0, d.Np / 128, 0, st);
+    return sk_field_update_rows(d, mapJ, mapD, b0, B, kw, NT, scale, 0, 0, 0, st);
 }
 
 // The limit is a property of the kernel, shared by every handle: it only ever grows.

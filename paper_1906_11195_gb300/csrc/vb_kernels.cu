@@ -127,7 +127,6 @@ __device__ __forceinline__ void store_words(uint64_t* p, const SpinWords<R>& s) 
     }
 }
 
-constexpr int kPlanes = 6;  // bit-sliced unsatisfied-edge counter, counts up to 63
 constexpr int kGroupSlices = 8;       // slices (warps) per staged group
 constexpr int kGroupEntries = 1024;   // staged sliced-ELL entries per group
 
