@@ -60,6 +60,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
     return ok != 0;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 // bounded wait: false if the barrier phase did not complete within max_iter polls
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, uint32_t max_iter) {
     for (uint32_t it = 0; it < max_iter; ++it)
@@ -159,8 +163,10 @@ struct VbCountJob {
 int vb_packed_init(const VbPackedDev& d, cudaStream_t st);
 // sweep index t = *clock + t_off (the clock lives in device memory so that captured CUDA graphs
 // can be replayed at any time)
+// variant selects the pipeline shape (0: 4 stages, 1 CTA/SM; 1: 3 stages, 2 CTAs/SM)
 int vb_packed_colour(const VbPackedDev& d, uint32_t group_begin, uint32_t group_end,
-                     const uint32_t* clock, uint32_t t_off, cudaStream_t st);
+                     const uint32_t* clock, uint32_t t_off, int variant, cudaStream_t st);
+constexpr int kVbColourVariants = 2;
 int vb_packed_snapshot(const VbPackedDev& d, int w, cudaStream_t st);
 int vb_packed_count(const VbPackedDev& d, const VbCountJob& job, cudaStream_t st);
 

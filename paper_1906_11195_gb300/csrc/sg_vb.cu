@@ -174,6 +174,7 @@ public:
             for (int b = 0; b < n_inst; ++b) seeds[b] = graphs_[b].seed;
             up((void*)pk_.seeds, seeds.data(), seeds.size() * 8);
             launches += vb_packed_init(pk_, st);
+            tune_variant(st);
         } else {
             up((void*)pl_.row_ptr, h_row_ptr_.data(), h_row_ptr_.size() * 4);
             up((void*)pl_.col, h_col_i_.data(), h_col_i_.size() * 4);
@@ -188,11 +189,42 @@ public:
         check_cuda(cudaStreamSynchronize(st), "attach");
     }
 
+    // Autotuner: time two sweeps with each pipeline shape of the colour kernel and keep the
+    // fastest, then redraw the initial spins (the trial sweeps leave no trace: the initial
+    // configuration is a pure function of the seed, and no measurement was taken).
+    void tune_variant(cudaStream_t st) {
+        cudaEvent_t e0, e1;
+        check_cuda(cudaEventCreate(&e0), "cudaEventCreate");
+        check_cuda(cudaEventCreate(&e1), "cudaEventCreate");
+        float best = 0.f;
+        int best_v = 0;
+        for (int v = 0; v < kVbColourVariants; ++v) {
+            variant_ = v;
+            check_cuda(cudaMemsetAsync(clock_dev, 0, 4, st), "memset");
+            sweep(0, st);  // warm-up
+            check_cuda(cudaEventRecord(e0, st), "cudaEventRecord");
+            sweep(1, st);
+            sweep(2, st);
+            check_cuda(cudaEventRecord(e1, st), "cudaEventRecord");
+            check_cuda(cudaEventSynchronize(e1), "cudaEventSynchronize");
+            float ms = 0.f;
+            check_cuda(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+            if (v == 0 || ms < best) {
+                best = ms;
+                best_v = v;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        variant_ = best_v;
+        launches += vb_packed_init(pk_, st);
+    }
+
     void sweep(uint32_t t_off, cudaStream_t st) override {
         if (kernel_ == SG_VB_PACKED) {
             for (size_t c = 0; c + 1 < colour_group_.size(); ++c)
                 launches += vb_packed_colour(pk_, colour_group_[c], colour_group_[c + 1], clock_dev,
-                                             t_off, st);
+                                             t_off, variant_, st);
         } else {
             for (size_t c = 0; c + 1 < colour_begin_.size(); ++c)
                 launches += vb_plain_colour(pl_, colour_begin_[c], colour_begin_[c + 1], clock_dev,
@@ -583,6 +615,7 @@ private:
     }
 
     int kernel_ = SG_VB_PACKED;
+    int variant_ = 0;  // colour-kernel pipeline shape chosen by the autotuner at attach
     int Lc_ = 64;
     size_t ws_bytes_ = 0;
     std::vector<Graph> graphs_;

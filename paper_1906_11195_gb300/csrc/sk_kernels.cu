@@ -117,24 +117,26 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0, int prev_b0
     const int wb = b0 / 32;
     const int pwb = prev_b0 >= 0 ? prev_b0 / 32 : 0;
     const int nw = prev_b0 >= 0 ? W : NC;
-    for (int k = threadIdx.x; k < 32 * NC * nw; k += blockDim.x) {
-        const int row = k / nw, w = k % nw;
-        const int col_word = w < NC ? wb + w : pwb + (w - NC);
-        jblk[row * W + w] = d.Jbits[(int64_t)(b0 + row) * words + col_word];
-    }
-    __syncthreads();
+    // this warp's replica state first (independent loads, in flight during the staging)
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (r >= d.R) return;
+    const bool active = r < d.R;
     int h[NC];
     int kst[NC];
     uint32_t sw[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         const int i = b0 + 32 * c + lane;
-        h[c] = d.H[(int64_t)r * d.Np + i];
-        kst[c] = d.kst[(int64_t)r * d.Np + i];
-        sw[c] = d.S[(int64_t)r * words + wb + c];
+        h[c] = active ? d.H[(int64_t)r * d.Np + i] : 0;
+        kst[c] = active ? d.kst[(int64_t)r * d.Np + i] : 0;
+        sw[c] = active ? d.S[(int64_t)r * words + wb + c] : 0u;
     }
+    for (int k = threadIdx.x; k < 32 * NC * nw; k += blockDim.x) {
+        const int row = k / nw, w = k % nw;
+        const int col_word = w < NC ? wb + w : pwb + (w - NC);
+        jblk[row * W + w] = d.Jbits[(int64_t)(b0 + row) * words + col_word];
+    }
+    __syncthreads();
+    if (!active) return;
     if (prev_b0 >= 0) {
         // fields += 2 sum_{j flipped in the previous block} J_ij s_j'
         int dh[NC];
@@ -219,11 +221,11 @@ int sk_inblock_prepare() {
 // TMA tile load and tcgen05 descriptors (inline PTX); mbarrier helpers are in sg_internal.cuh
 // --------------------------------------------------------------------------------------------
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                            uint64_t* bar) {
+                                            uint64_t* bar, uint64_t policy) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar)), "l"(policy)
         : "memory");
 }
 
@@ -242,7 +244,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, int kw) {
 // --------------------------------------------------------------------------------------------
 constexpr uint32_t kWaitPolls = 1u << 24;
 
-__global__ void __launch_bounds__(128) k_sk_field_mma(const __grid_constant__ CUtensorMap mapJ,
+__global__ void __launch_bounds__(128, 1) k_sk_field_mma(const __grid_constant__ CUtensorMap mapJ,
                                                       const __grid_constant__ CUtensorMap mapD,
                                                       SkDev d, int b0, int B, int kw, int NT,
                                                       int scale, int skip0, int skip1,
@@ -283,14 +285,28 @@ __global__ void __launch_bounds__(128) k_sk_field_mma(const __grid_constant__ CU
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
+    const uint64_t pol_keep = l2_evict_last();
+
+    // Prefetch this thread's fields (row m0 + 32 warp + lane, up to 128 replica columns) while
+    // the operands land and the MMAs run: no other launch writes these rows meanwhile.
+    const int row = m0 + 32 * warp + lane;
+    int hv[4][32];
+    if (!atomic_add) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (32 * c + j < NT) hv[c][j] = __ldcg(d.H + (int64_t)(n0 + 32 * c + j) * d.Np + row);
+    }
 
     bool ok = true;
     if (tid == 0) {
         const uint32_t bytes = (uint32_t)(nchunks * (128 + NT) * kw);
         mbar_expect_tx(&bars[0], bytes);
         for (int kc = 0; kc < nchunks; ++kc) {
-            tma_load_2d(sA + (size_t)kc * 128 * kw, &mapJ, b0 + kc * kw, m0, &bars[0]);
-            tma_load_2d(sB + (size_t)kc * NT * kw, &mapD, b0 + kc * kw, n0, &bars[0]);
+            // the couplings are read every sweep: keep them in L2
+            tma_load_2d(sA + (size_t)kc * 128 * kw, &mapJ, b0 + kc * kw, m0, &bars[0], pol_keep);
+            tma_load_2d(sB + (size_t)kc * NT * kw, &mapD, b0 + kc * kw, n0, &bars[0], pol_keep);
         }
         ok = mbar_wait(&bars[0], 0, kWaitPolls);
         if (ok) {
@@ -327,10 +343,11 @@ __global__ void __launch_bounds__(128) k_sk_field_mma(const __grid_constant__ CU
     ok = __syncthreads_and(ok);
     if (ok) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int row = m0 + 32 * warp + lane;
-        for (int c0 = 0; c0 < NT; c0 += 32) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (32 * c >= NT) break;
             uint32_t v[32];
-            const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+            const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * c);
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -343,26 +360,17 @@ __global__ void __launch_bounds__(128) k_sk_field_mma(const __grid_constant__ CU
                   "=r"(v[30]), "=r"(v[31])
                 : "r"(ta));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const int ncol = NT - c0 < 32 ? NT - c0 : 32;
-            int* hbase = d.H + (int64_t)(n0 + c0) * d.Np + row;
-            if (atomic_add) {
-                // concurrent updates of the same rows (row tiles split across streams) commute
+            int* hbase = d.H + (int64_t)(n0 + 32 * c) * d.Np + row;
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (j < ncol) {
-                        const int dv = __float2int_rn(__uint_as_float(v[j]));
-                        if (dv) atomicAdd(hbase + (int64_t)j * d.Np, scale * dv);
-                    }
-            } else {
-                // all loads of the chunk first (independent), then the adds and stores
-                int hv[32];
-#pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (j < ncol) hv[j] = __ldcg(hbase + (int64_t)j * d.Np);
-#pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (j < ncol)
-                        hbase[(int64_t)j * d.Np] = hv[j] + scale * __float2int_rn(__uint_as_float(v[j]));
+            for (int j = 0; j < 32; ++j) {
+                if (32 * c + j >= NT) break;
+                const int dv = __float2int_rn(__uint_as_float(v[j]));
+                if (atomic_add) {
+                    // concurrent updates of the same rows (split across streams) commute
+                    if (dv) atomicAdd(hbase + (int64_t)j * d.Np, scale * dv);
+                } else {
+                    hbase[(int64_t)j * d.Np] = hv[c][j] + scale * dv;
+                }
             }
         }
     } else if (tid == 0) {

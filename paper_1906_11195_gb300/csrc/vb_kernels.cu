@@ -228,149 +228,171 @@ __device__ __forceinline__ void gather_async(uint64_t* dst, const uint64_t* src,
     }
 }
 
+// One consumer warp's work on one slice of a staged group (neighbour words already gathered).
 template <int R>
-__global__ void __launch_bounds__(256) k_vb_packed_colour(VbPackedDev d, uint32_t g_begin,
-                                                          uint32_t g_end,
-                                                          const uint32_t* __restrict__ clock,
-                                                          uint32_t t_off) {
+__device__ __forceinline__ void update_slice(const VbPackedDev& d, const VbStage<R>& st,
+                                             const uint4& gi, uint32_t warp, uint32_t lane,
+                                             uint32_t t, uint64_t pol_keep) {
+    const bool wide = (gi.y & kWideGroup) != 0u;
+    const uint32_t slice = gi.x + warp;
+    const uint32_t vi = st.vinfo[warp * 32 + lane];
+    if (vi == kInactive) return;
+    const uint4 m = st.meta[warp];  // first entry, width
+    const uint32_t width = m.y;
+    const int deg = (int)(vi >> kDegShift);
+    const uint32_t orig = vi & kOrigMask;
+    const uint64_t seed = st.seed[0];
+    SpinWords<R> si;
+#pragma unroll
+    for (int r = 0; r < R; ++r) si.v[r] = st.S[(warp * 32 + lane) * R + r];
+    // one Philox block per (vertex, sweep) serves replicas 0..3; the accepted m form a prefix
+    // 1..m*, so a lane flips iff its unsatisfied count u >= ceil((d - m*) / 2)
+    const uint4 rnd =
+        philox4x32_10(make_uint4(orig, t, 0u, 0u), (uint32_t)seed, (uint32_t)(seed >> 32));
+    int kmin[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint32_t r32 = uint4_word(rnd, r);
+        int ms = 0;
+        while (ms < deg && r32 < st.thr[r * kVbThrStride + ms + 1]) ++ms;
+        kmin[r] = (deg - ms + 1) >> 1;
+    }
+    const VbStage<R>* sp = wide ? nullptr : &st;
+    const uint32_t loc = m.x - gi.z + lane, idx = m.x + lane;
+    // the slice's width (warp-uniform) sets the counter size
+    if (width <= 1) count_and_flip<R, 1>(si, sp, loc, width, d, idx, kmin);
+    else if (width <= 3) count_and_flip<R, 2>(si, sp, loc, width, d, idx, kmin);
+    else if (width <= 7) count_and_flip<R, 3>(si, sp, loc, width, d, idx, kmin);
+    else if (width <= 15) count_and_flip<R, 4>(si, sp, loc, width, d, idx, kmin);
+    else if (width <= 31) count_and_flip<R, 5>(si, sp, loc, width, d, idx, kmin);
+    else count_and_flip<R, 6>(si, sp, loc, width, d, idx, kmin);
+    store_words_keep<R>(d.S + ((int64_t)slice * 32 + lane) * R, si, pol_keep);
+}
+
+// Warp-specialised, persistent colour-class kernel.  Warp kGroupSlices (the producer) stages
+// the CTA's groups into a ring of NS shared-memory stages with bulk asynchronous copies; each
+// stage has a "full" mbarrier (bytes landed) and an "empty" one (released by the consumer
+// warps).  Consumer warp w owns slice w of every group: it starts the cp.async gathers of its
+// neighbours' words for the group L ahead, waits for the gathers of the current group, updates
+// its 32 vertices and releases the stage.  No CTA-wide barrier is on the path, so warps drift
+// independently, and NS stages keep copies in flight while others compute.
+template <int R, int NS, int L>
+__global__ void __launch_bounds__(32 * (kGroupSlices + 1))
+    k_vb_packed_colour(VbPackedDev d, uint32_t g_begin, uint32_t g_end,
+                       const uint32_t* __restrict__ clock, uint32_t t_off) {
+    static_assert(NS >= L + 1, "the producer must be able to run L groups ahead");
     extern __shared__ __align__(128) uint8_t smem_raw[];
     VbStage<R>* stage = reinterpret_cast<VbStage<R>*>(smem_raw);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(stage + 2);
+    uint64_t* full = reinterpret_cast<uint64_t*>(stage + NS);
+    uint64_t* empty = full + NS;
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
     const uint32_t t = __ldg(clock) + t_off;
     const uint64_t* __restrict__ S = d.S;
     const uint64_t pol_stream = l2_evict_first(), pol_keep = l2_evict_last();
+    const uint32_t g0 = g_begin + blockIdx.x, stride = gridDim.x;
+    const uint32_t n_mine = g0 < g_end ? (g_end - g0 + stride - 1) / stride : 0u;
 
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kGroupSlices);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
-    auto issue_stage = [&](uint32_t g, int s) {  // one thread
-        const uint4 gi = d.groups[g];  // first slice, slices (| wide), first entry, entries
-        const uint32_t nsl = gi.y & ~kWideGroup;
-        const bool wide = (gi.y & kWideGroup) != 0u;
-        const uint32_t nslot = nsl * 32u;
-        const uint32_t gtab_bytes = R * kVbThrStride * 4u + 16u;
-        const uint32_t bytes =
-            nslot * 4u + nslot * R * 8u + nsl * 16u + gtab_bytes + (wide ? 0u : gi.w * 12u);
-        mbar_expect_tx(&bars[s], bytes);
-        bulk_copy_g2s_hint(stage[s].meta, d.slice_meta + gi.x, nsl * 16u, &bars[s], pol_stream);
-        bulk_copy_g2s(stage[s].thr, d.gtab + (size_t)d.group_graph[g] * gtab_bytes, gtab_bytes,
-                      &bars[s]);
-        bulk_copy_g2s_hint(stage[s].vinfo, d.vinfo + (int64_t)gi.x * 32, nslot * 4u, &bars[s],
-                           pol_stream);
-        bulk_copy_g2s_hint(stage[s].S, S + (int64_t)gi.x * 32 * R, nslot * R * 8u, &bars[s],
-                           pol_keep);
-        if (gi.w && !wide) {
-            bulk_copy_g2s_hint(stage[s].col, d.col + gi.z, gi.w * 4u, &bars[s], pol_stream);
-            bulk_copy_g2s_hint(stage[s].J, d.jb + gi.z, gi.w * 8u, &bars[s], pol_stream);
+    if (warp == kGroupSlices) {
+        // ------------------------------------------------------------------ producer
+        if (lane == 0) {
+            for (uint32_t k = 0; k < n_mine; ++k) {
+                const int s = (int)(k % NS);
+                if (k >= (uint32_t)NS &&
+                    !mbar_wait(&empty[s], ((k / NS) - 1) & 1u, kStagePolls)) {
+                    atomicOr(d.err, 4);
+                    break;
+                }
+                const uint32_t g = g0 + k * stride;
+                const uint4 gi = d.groups[g];  // first slice, slices (| wide), entry, entries
+                const uint32_t nsl = gi.y & ~kWideGroup;
+                const bool wide = (gi.y & kWideGroup) != 0u;
+                const uint32_t nslot = nsl * 32u;
+                const uint32_t gtab_bytes = R * kVbThrStride * 4u + 16u;
+                const uint32_t bytes = nslot * 4u + nslot * R * 8u + nsl * 16u + gtab_bytes +
+                                       (wide ? 0u : gi.w * 12u);
+                mbar_expect_tx(&full[s], bytes);
+                bulk_copy_g2s_hint(stage[s].meta, d.slice_meta + gi.x, nsl * 16u, &full[s],
+                                   pol_stream);
+                bulk_copy_g2s(stage[s].thr, d.gtab + (size_t)d.group_graph[g] * gtab_bytes,
+                              gtab_bytes, &full[s]);
+                bulk_copy_g2s_hint(stage[s].vinfo, d.vinfo + (int64_t)gi.x * 32, nslot * 4u,
+                                   &full[s], pol_stream);
+                bulk_copy_g2s_hint(stage[s].S, S + (int64_t)gi.x * 32 * R, nslot * R * 8u,
+                                   &full[s], pol_keep);
+                if (gi.w && !wide) {
+                    bulk_copy_g2s_hint(stage[s].col, d.col + gi.z, gi.w * 4u, &full[s],
+                                       pol_stream);
+                    bulk_copy_g2s_hint(stage[s].J, d.jb + gi.z, gi.w * 8u, &full[s], pol_stream);
+                }
+            }
         }
-    };
-    // every thread: start the copies of its neighbours' words for the staged group
-    auto issue_gathers = [&](uint32_t g, int s) -> uint4 {
-        const uint4 gi = __ldg(&d.groups[g]);
-        const uint32_t nsl = gi.y & ~kWideGroup;
-        if (warp < nsl && !(gi.y & kWideGroup)) {
-            if (stage[s].vinfo[warp * 32 + lane] != kInactive) {
+        return;
+    }
+
+    // ---------------------------------------------------------------------- consumers
+    // start the gathers of this warp's slice of group k (its stage has landed)
+    auto gathers = [&](uint32_t k) -> bool {
+        if (k < n_mine) {
+            const int s = (int)(k % NS);
+            if (!mbar_wait(&full[s], (k / NS) & 1u, kStagePolls)) return false;
+            const uint4 gi = __ldg(&d.groups[g0 + k * stride]);
+            const uint32_t nsl = gi.y & ~kWideGroup;
+            if (warp < nsl && !(gi.y & kWideGroup) &&
+                stage[s].vinfo[warp * 32 + lane] != kInactive) {
                 const uint4 m = stage[s].meta[warp];
-                const uint32_t width = m.y;
                 uint32_t loc = m.x - gi.z + lane;
-                for (uint32_t e = 0; e < width; ++e, loc += 32)
+                for (uint32_t e = 0; e < m.y; ++e, loc += 32)
                     gather_async<R>(&stage[s].gath[loc * R], S + (int64_t)stage[s].col[loc] * R,
                                     pol_keep);
             }
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
-        return gi;
+        return true;
     };
-
-    const uint32_t g0 = g_begin + blockIdx.x, stride = gridDim.x;
-    if (tid == 0) {
-        if (g0 < g_end) issue_stage(g0, 0);
-        if (g0 + stride < g_end) issue_stage(g0 + stride, 1);
-    }
     bool ok = true;
-    uint4 gi_next = make_uint4(0u, 0u, 0u, 0u);
-    if (g0 < g_end) {
-        ok = __syncthreads_and(mbar_wait(&bars[0], 0, kStagePolls));
-        if (ok) gi_next = issue_gathers(g0, 0);
-    }
-    uint32_t it = 0;
-    for (uint32_t g = g0; ok && g < g_end; g += stride, ++it) {
-        const int s = (int)(it & 1u);
-        const uint32_t gn = g + stride;
-        const uint4 gi = gi_next;
-        if (gn < g_end) {
-            ok = __syncthreads_and(mbar_wait(&bars[s ^ 1], ((it + 1) >> 1) & 1u, kStagePolls));
-            if (!ok) break;
-            gi_next = issue_gathers(gn, s ^ 1);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
+    for (uint32_t k = 0; k < (uint32_t)L; ++k) ok = ok && gathers(k);
+    for (uint32_t k = 0; ok && k < n_mine; ++k) {
+        if (!gathers(k + L)) {
+            ok = false;
+            break;
         }
-        const uint32_t nsl = gi.y & ~kWideGroup;
-        const bool wide = (gi.y & kWideGroup) != 0u;
-        if (warp < nsl) {
-            const uint32_t slice = gi.x + warp;
-            const uint32_t vi = stage[s].vinfo[warp * 32 + lane];
-            if (vi != kInactive) {
-                const uint4 m = stage[s].meta[warp];  // first entry, width
-                const uint32_t width = m.y;
-                const int deg = (int)(vi >> kDegShift);
-                const uint32_t orig = vi & kOrigMask;
-                const uint64_t seed = stage[s].seed[0];
-                SpinWords<R> si;
-#pragma unroll
-                for (int r = 0; r < R; ++r) si.v[r] = stage[s].S[(warp * 32 + lane) * R + r];
-                // one Philox block per (vertex, sweep) serves replicas 0..3; the accepted
-                // m form a prefix 1..m*, so a lane flips iff u >= ceil((d - m*) / 2)
-                const uint4 rnd = philox4x32_10(make_uint4(orig, t, 0u, 0u), (uint32_t)seed,
-                                                (uint32_t)(seed >> 32));
-                const uint32_t* thr = stage[s].thr;
-                int kmin[R];
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const uint32_t r32 = uint4_word(rnd, r);
-                    int ms = 0;
-                    while (ms < deg && r32 < thr[r * kVbThrStride + ms + 1]) ++ms;
-                    kmin[r] = (deg - ms + 1) >> 1;
-                }
-                const VbStage<R>* sp = wide ? nullptr : &stage[s];
-                const uint32_t loc = m.x - gi.z + lane, idx = m.x + lane;
-                // the slice's width (warp-uniform) sets the counter size
-                if (width <= 1) count_and_flip<R, 1>(si, sp, loc, width, d, idx, kmin);
-                else if (width <= 3) count_and_flip<R, 2>(si, sp, loc, width, d, idx, kmin);
-                else if (width <= 7) count_and_flip<R, 3>(si, sp, loc, width, d, idx, kmin);
-                else if (width <= 15) count_and_flip<R, 4>(si, sp, loc, width, d, idx, kmin);
-                else if (width <= 31) count_and_flip<R, 5>(si, sp, loc, width, d, idx, kmin);
-                else count_and_flip<R, 6>(si, sp, loc, width, d, idx, kmin);
-                store_words_keep<R>(d.S + ((int64_t)slice * 32 + lane) * R, si, pol_keep);
-            }
-        }
-        __syncthreads();  // stage s is free again
-        if (tid == 0 && g + 2 * stride < g_end) issue_stage(g + 2 * stride, s);
+        asm volatile("cp.async.wait_group %0;" ::"n"(L) : "memory");
+        const int s = (int)(k % NS);
+        const uint4 gi = __ldg(&d.groups[g0 + k * stride]);
+        if (warp < (gi.y & ~kWideGroup)) update_slice<R>(d, stage[s], gi, warp, lane, t, pol_keep);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
     }
-    if (!ok && tid == 0) atomicOr(d.err, 4);
+    if (!ok && lane == 0) atomicOr(d.err, 4);
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
-template <int R>
+template <int R, int NS>
 static size_t colour_smem() {
-    return 2 * sizeof(VbStage<R>) + 2 * sizeof(uint64_t);
+    return NS * sizeof(VbStage<R>) + 2 * NS * sizeof(uint64_t);
 }
 
 static int g_num_sms = 0;
 
-template <int R>
-static void colour_launch(const VbPackedDev& d, uint32_t g_begin, uint32_t g_end,
-                          const uint32_t* clock, uint32_t t_off, cudaStream_t st) {
+// pipeline variants (the handle's autotuner picks one; none changes the results):
+//   variant 0: 4 stages, gathers 2 groups ahead, one CTA per SM
+//   variant 1: 3 stages, gathers 1 group ahead, two CTAs per SM
+template <int R, int NS, int L>
+static void colour_launch_v(const VbPackedDev& d, uint32_t g_begin, uint32_t g_end,
+                            const uint32_t* clock, uint32_t t_off, int per_sm, cudaStream_t st) {
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(k_vb_packed_colour<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)colour_smem<R>());
+        cudaFuncSetAttribute(k_vb_packed_colour<R, NS, L>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)colour_smem<R, NS>());
         configured = true;
     }
     if (!g_num_sms) {
@@ -380,18 +402,26 @@ static void colour_launch(const VbPackedDev& d, uint32_t g_begin, uint32_t g_end
         if (g_num_sms <= 0) g_num_sms = 148;
     }
     const uint32_t ng = g_end - g_begin;
-    const uint32_t cap = (uint32_t)g_num_sms * (R == 4 ? 2u : 3u);
+    const uint32_t cap = (uint32_t)g_num_sms * (uint32_t)per_sm;
     const uint32_t grid = ng < cap ? ng : cap;
-    k_vb_packed_colour<R><<<grid, 256, colour_smem<R>(), st>>>(d, g_begin, g_end, clock, t_off);
+    k_vb_packed_colour<R, NS, L><<<grid, 32 * (kGroupSlices + 1), colour_smem<R, NS>(), st>>>(
+        d, g_begin, g_end, clock, t_off);
+}
+
+template <int R>
+static void colour_launch(const VbPackedDev& d, uint32_t g_begin, uint32_t g_end,
+                          const uint32_t* clock, uint32_t t_off, int variant, cudaStream_t st) {
+    if (variant == 0) colour_launch_v<R, 4, 2>(d, g_begin, g_end, clock, t_off, 1, st);
+    else colour_launch_v<R, 3, 1>(d, g_begin, g_end, clock, t_off, R == 4 ? 1 : 2, st);
 }
 
 int vb_packed_colour(const VbPackedDev& d, uint32_t g_begin, uint32_t g_end,
-                     const uint32_t* clock, uint32_t t_off, cudaStream_t st) {
+                     const uint32_t* clock, uint32_t t_off, int variant, cudaStream_t st) {
     if (g_end <= g_begin) return 0;
     switch (d.R) {
-        case 1: colour_launch<1>(d, g_begin, g_end, clock, t_off, st); break;
-        case 2: colour_launch<2>(d, g_begin, g_end, clock, t_off, st); break;
-        case 4: colour_launch<4>(d, g_begin, g_end, clock, t_off, st); break;
+        case 1: colour_launch<1>(d, g_begin, g_end, clock, t_off, variant, st); break;
+        case 2: colour_launch<2>(d, g_begin, g_end, clock, t_off, variant, st); break;
+        case 4: colour_launch<4>(d, g_begin, g_end, clock, t_off, variant, st); break;
         default: return -1;
     }
     return 1;
