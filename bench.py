@@ -54,10 +54,31 @@ def dist_env():
     return ws, rank, local
 
 
-def instance(rank: int):
-    rp, col, eid = sg_inputs.poisson_graph(N_VERTS, MEAN_DEGREE, 2 + 1000 * rank)
-    jb = sg_inputs.vb_lane_couplings(eid, eid.max() + 1, 2 + 1000 * rank)
+def graph_seed(rank: int) -> int:
+    """Each rank simulates its own independent instance (weak scaling, no data exchange)."""
+    return 2 + 1000 * rank
+
+
+def instance(rank: int, n: int = N_VERTS):
+    rp, col, eid = sg_inputs.poisson_graph(n, MEAN_DEGREE, graph_seed(rank))
+    jb = sg_inputs.vb_lane_couplings(eid, eid.max() + 1, graph_seed(rank))
     return rp, col, jb
+
+
+def max_over_ranks(ms: float, device=None) -> float:
+    """The job time is the slowest rank's (all ranks started after the same barrier)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(updates_per_rank_step: int, steps: int, world: int, ms: float) -> float:
+    """Whole-job throughput: all ranks' spin updates over the slowest rank's time (per ns)."""
+    return world * updates_per_rank_step * steps / (ms * 1e6)
 
 
 def algorithmic_bytes_per_sweep(n, n_entries_directed, R):
@@ -372,12 +393,9 @@ def run_gpu(args):
     launches = sum(r.launches for r in runs) - launches0
     for r in runs:
         r.synchronize()
-    if ws > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     updates_per_step = len(TEMPS) * N_VERTS * LANES * REPLICAS
-    value = ws * updates_per_step * args.steps / (ms * 1e6)
+    value = job_value(updates_per_step, args.steps, ws, ms)
     for r in runs:
         r.close()
 
