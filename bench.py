@@ -226,7 +226,7 @@ def run_profile_case(args):
     from paper_1906_11195_gb300 import _build
     _build.build()
     torch.cuda.set_device(0)
-    rp, col, jb = instance(0)
+    rp, col, jb = instance(0, n=1 << args.profile_log2n)
     temps = [TEMPS[0]] * REPLICAS if args.profile_replicas == 2 else \
         [T for T in TEMPS for _ in range(args.profile_replicas // len(TEMPS))]
     g = dict(row_ptr=rp, col=col, jbits=jb, seed=1, temps=temps)
@@ -509,6 +509,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
                     help="run only the single-instance sweep case used for ncu captures")
+    ap.add_argument("--profile-log2n", type=int, default=22, help="log2 N of the profile case")
     ap.add_argument("--profile-replicas", type=int, default=2, choices=[2, 4],
                     help="replicas of the profile case (4: two per temperature)")
     ap.add_argument("--workload", default="vb", choices=["vb", "sk", "vb_batch"],
