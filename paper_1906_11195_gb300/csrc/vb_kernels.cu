@@ -228,28 +228,19 @@ __device__ __forceinline__ void gather_async(uint64_t* dst, const uint64_t* src,
     }
 }
 
-// One consumer warp's work on one slice of a staged group (neighbour words already gathered).
+// Acceptance constants of one vertex (all replicas): one Philox block per (vertex, sweep) serves
+// replicas 0..3; the accepted m form a prefix 1..m*, so a lane flips iff its unsatisfied count u
+// reaches kmin = ceil((d - m*) / 2).  Independent of the neighbours, so a consumer warp computes
+// it for the next group while the current group's gathers are still in flight.
 template <int R>
-__device__ __forceinline__ void update_slice(const VbPackedDev& d, const VbStage<R>& st,
-                                             const uint4& gi, uint32_t warp, uint32_t lane,
-                                             uint32_t t, uint64_t pol_keep) {
-    const bool wide = (gi.y & kWideGroup) != 0u;
-    const uint32_t slice = gi.x + warp;
+__device__ __forceinline__ void acceptance(const VbStage<R>& st, uint32_t warp, uint32_t lane,
+                                           uint32_t t, int (&kmin)[R]) {
     const uint32_t vi = st.vinfo[warp * 32 + lane];
-    if (vi == kInactive) return;
-    const uint4 m = st.meta[warp];  // first entry, width
-    const uint32_t width = m.y;
-    const int deg = (int)(vi >> kDegShift);
+    const int deg = vi == kInactive ? 0 : (int)(vi >> kDegShift);
     const uint32_t orig = vi & kOrigMask;
     const uint64_t seed = st.seed[0];
-    SpinWords<R> si;
-#pragma unroll
-    for (int r = 0; r < R; ++r) si.v[r] = st.S[(warp * 32 + lane) * R + r];
-    // one Philox block per (vertex, sweep) serves replicas 0..3; the accepted m form a prefix
-    // 1..m*, so a lane flips iff its unsatisfied count u >= ceil((d - m*) / 2)
     const uint4 rnd =
         philox4x32_10(make_uint4(orig, t, 0u, 0u), (uint32_t)seed, (uint32_t)(seed >> 32));
-    int kmin[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const uint32_t r32 = uint4_word(rnd, r);
@@ -257,6 +248,22 @@ __device__ __forceinline__ void update_slice(const VbPackedDev& d, const VbStage
         while (ms < deg && r32 < st.thr[r * kVbThrStride + ms + 1]) ++ms;
         kmin[r] = (deg - ms + 1) >> 1;
     }
+}
+
+// One consumer warp's work on one slice of a staged group (neighbour words already gathered).
+template <int R>
+__device__ __forceinline__ void update_slice(const VbPackedDev& d, const VbStage<R>& st,
+                                             const uint4& gi, uint32_t warp, uint32_t lane,
+                                             const int (&kmin)[R], uint64_t pol_keep) {
+    const bool wide = (gi.y & kWideGroup) != 0u;
+    const uint32_t slice = gi.x + warp;
+    const uint32_t vi = st.vinfo[warp * 32 + lane];
+    if (vi == kInactive) return;
+    const uint4 m = st.meta[warp];  // first entry, width
+    const uint32_t width = m.y;
+    SpinWords<R> si;
+#pragma unroll
+    for (int r = 0; r < R; ++r) si.v[r] = st.S[(warp * 32 + lane) * R + r];
     const VbStage<R>* sp = wide ? nullptr : &st;
     const uint32_t loc = m.x - gi.z + lane, idx = m.x + lane;
     // the slice's width (warp-uniform) sets the counter size
@@ -360,15 +367,22 @@ __global__ void __launch_bounds__(32 * (kGroupSlices + 1))
     };
     bool ok = true;
     for (uint32_t k = 0; k < (uint32_t)L; ++k) ok = ok && gathers(k);
+    int kmin_next[R];
+    if (ok && n_mine) acceptance<R>(stage[0], warp, lane, t, kmin_next);
     for (uint32_t k = 0; ok && k < n_mine; ++k) {
         if (!gathers(k + L)) {
             ok = false;
             break;
         }
+        int kmin[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) kmin[r] = kmin_next[r];
+        // the next group's random numbers and thresholds (its stage landed: k + 1 <= k + L)
+        if (k + 1 < n_mine) acceptance<R>(stage[(k + 1) % NS], warp, lane, t, kmin_next);
         asm volatile("cp.async.wait_group %0;" ::"n"(L) : "memory");
         const int s = (int)(k % NS);
         const uint4 gi = __ldg(&d.groups[g0 + k * stride]);
-        if (warp < (gi.y & ~kWideGroup)) update_slice<R>(d, stage[s], gi, warp, lane, t, pol_keep);
+        if (warp < (gi.y & ~kWideGroup)) update_slice<R>(d, stage[s], gi, warp, lane, kmin, pol_keep);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
     }
@@ -386,6 +400,7 @@ static int g_num_sms = 0;
 // pipeline variants (the handle's autotuner picks one; none changes the results):
 //   variant 0: 4 stages, gathers 2 groups ahead, one CTA per SM
 //   variant 1: 3 stages, gathers 1 group ahead, two CTAs per SM
+//   variant 2: 2 stages, gathers 1 group ahead, three CTAs per SM
 template <int R, int NS, int L>
 static void colour_launch_v(const VbPackedDev& d, uint32_t g_begin, uint32_t g_end,
                             const uint32_t* clock, uint32_t t_off, int per_sm, cudaStream_t st) {
@@ -412,7 +427,8 @@ template <int R>
 static void colour_launch(const VbPackedDev& d, uint32_t g_begin, uint32_t g_end,
                           const uint32_t* clock, uint32_t t_off, int variant, cudaStream_t st) {
     if (variant == 0) colour_launch_v<R, 4, 2>(d, g_begin, g_end, clock, t_off, 1, st);
-    else colour_launch_v<R, 3, 1>(d, g_begin, g_end, clock, t_off, R == 4 ? 1 : 2, st);
+    else if (variant == 1) colour_launch_v<R, 3, 1>(d, g_begin, g_end, clock, t_off, R == 4 ? 1 : 2, st);
+    else colour_launch_v<R, 2, 1>(d, g_begin, g_end, clock, t_off, R == 4 ? 2 : 3, st);
 }
 
 int vb_packed_colour(const VbPackedDev& d, uint32_t g_begin, uint32_t g_end,
