@@ -163,8 +163,8 @@ struct VbCountJob {
 int vb_packed_init(const VbPackedDev& d, cudaStream_t st);
 // sweep index t = *clock + t_off (the clock lives in device memory so that captured CUDA graphs
 // can be replayed at any time)
-// variant selects the pipeline shape (0: 4 stages, 1 CTA/SM; 1: 3 stages, 2 CTAs/SM;
-// 2: 2 stages, 3 CTAs/SM)
+// variant (0 .. kVbColourVariants - 1) selects the pipeline shape: stream stages, gather
+// buffers, gather lookahead and CTAs per SM; every shape gives the same results
 int vb_packed_colour(const VbPackedDev& d, uint32_t group_begin, uint32_t group_end,
                      const uint32_t* clock, uint32_t t_off, int variant, cudaStream_t st);
 constexpr int kVbColourVariants = 3;

@@ -8,6 +8,7 @@
 // Viana-Bray ensemble (Eq. 3).  The random number of a vertex is keyed by its original label,
 // so relabelling and slicing never change the trajectory.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -174,7 +175,11 @@ public:
             for (int b = 0; b < n_inst; ++b) seeds[b] = graphs_[b].seed;
             up((void*)pk_.seeds, seeds.data(), seeds.size() * 8);
             launches += vb_packed_init(pk_, st);
-            tune_variant(st);
+            // SG_VB_COLOUR_VARIANT=<k> pins the pipeline shape (reproducible timings of one
+            // shape); otherwise the autotuner picks the fastest
+            const char* pin = getenv("SG_VB_COLOUR_VARIANT");
+            if (pin && *pin >= '0' && *pin < '0' + kVbColourVariants && !pin[1]) variant_ = *pin - '0';
+            else tune_variant(st);
         } else {
             up((void*)pl_.row_ptr, h_row_ptr_.data(), h_row_ptr_.size() * 4);
             up((void*)pl_.col, h_col_i_.data(), h_col_i_.size() * 4);

@@ -155,60 +155,154 @@ __device__ __forceinline__ uint64_t bitslice_ge(const uint64_t (&p)[P], int k) {
 }
 
 // Pipelined colour-class kernel.  The slices of a colour class are cut into groups of at most
-// kGroupSlices slices (one warp each) and kGroupEntries sliced-ELL entries.  A persistent CTA
-// walks its groups through a two-stage shared-memory pipeline:
-//   * one thread stages a group's vinfo, own spin words, neighbour slots and coupling words with
-//     bulk asynchronous copies (completion on the stage's mbarrier), two groups ahead;
-//   * as soon as a group is staged, every thread starts asynchronous 16-byte copies (cp.async)
-//     of its neighbours' spin words into the stage, one group ahead of the computation;
-//   * the computation of a group reads everything from shared memory.
-// So the random gathers of the next group are in flight while the current group is computed,
-// and no global-memory latency is left on the dependent path.  A group holding one slice wider
-// than the stage (degree > 32, flagged by the host) is computed straight from global memory.
+// kGroupSlices slices (one warp each) and kGroupEntries sliced-ELL entries.  Per group, two kinds
+// of data move into shared memory:
+//   * the stream part (group descriptor, vinfo, own spin words, slice metadata, neighbour slots,
+//     coupling words, the graph's thresholds and key), which depends on nothing the sweep
+//     writes, is staged by bulk asynchronous copies (completion on the stage's mbarrier) several
+//     groups ahead, to cover the DRAM latency;
+//   * the neighbours' spin words, which must be read after the previous colour class finished,
+//     are gathered with 16-byte cp.async copies into a separate, smaller ring of gather buffers,
+//     L groups ahead of the computation, to cover the L2 latency.
+// The computation of a group then reads everything from shared memory.  Keeping the two rings
+// apart lets the stream ring run deep without reserving gather space for groups whose copies
+// are still in flight.  A group holding one slice wider than the stage (degree > 32, flagged by
+// the host) is computed straight from global memory.
 constexpr uint32_t kWideGroup = 0x80000000u;
 
 template <int R>
-struct VbStage {
-    uint64_t gath[kGroupEntries * R];
+struct VbStream {
     uint64_t J[kGroupEntries];
     uint32_t col[kGroupEntries];
     uint64_t S[kGroupSlices * 32 * R];
     uint32_t vinfo[kGroupSlices * 32];
-    uint4 meta[kGroupSlices];  // per slice: first entry, width, graph, 0
+    uint4 meta[kGroupSlices];        // per slice: first entry, width, graph, 0
     uint32_t thr[R * kVbThrStride];  // the group's graph: thresholds of its replicas ...
     uint64_t seed[2];                // ... and its Philox key
+    uint4 gi;                        // group descriptor: first slice, slices (| wide), entry, entries
+};
+
+template <int R>
+struct VbGath {
+    uint64_t v[kGroupEntries * R];
 };
 
 // Count the unsatisfied edges of one vertex (all lanes, all replicas) with a P-plane counter
-// and flip the lanes whose count reaches kmin.  Neighbour words come from the stage, or straight
-// from global memory for a wide slice (stage == nullptr).
+// and flip the lanes whose count reaches kmin.  Neighbour words come from the gather buffer, or
+// straight from global memory for a wide slice (J == nullptr).
 template <int R, int P>
-__device__ __forceinline__ void count_and_flip(SpinWords<R>& si, const VbStage<R>* stage,
-                                               uint32_t loc, uint32_t width, const VbPackedDev& d,
-                                               uint32_t idx, const int (&kmin)[R]) {
+__device__ __forceinline__ void count_and_flip(SpinWords<R>& si, const uint64_t* J,
+                                               const uint64_t* gath, uint32_t loc, uint32_t width,
+                                               const VbPackedDev& d, uint32_t idx,
+                                               const int (&kmin)[R]) {
     uint64_t planes[R][P];
 #pragma unroll
     for (int r = 0; r < R; ++r)
 #pragma unroll
         for (int b = 0; b < P; ++b) planes[r][b] = 0ull;
-    if (stage) {
+    if (J) {
         for (uint32_t e = 0; e < width; ++e, loc += 32) {
-            const uint64_t J = stage->J[loc];
+            const uint64_t Je = J[loc];
 #pragma unroll
-            for (int r = 0; r < R; ++r)
-                bitslice_add<P>(planes[r], si.v[r] ^ stage->gath[loc * R + r] ^ J);
+            for (int r = 0; r < R; ++r) bitslice_add<P>(planes[r], si.v[r] ^ gath[loc * R + r] ^ Je);
         }
     } else {
         for (uint32_t e = 0; e < width; ++e, idx += 32) {
             const uint32_t j = __ldg(d.col + idx);
-            const uint64_t J = __ldg(d.jb + idx);
+            const uint64_t Je = __ldg(d.jb + idx);
             const SpinWords<R> sj = gather_words<R>(d.S + (int64_t)j * R);
 #pragma unroll
-            for (int r = 0; r < R; ++r) bitslice_add<P>(planes[r], si.v[r] ^ sj.v[r] ^ J);
+            for (int r = 0; r < R; ++r) bitslice_add<P>(planes[r], si.v[r] ^ sj.v[r] ^ Je);
         }
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) si.v[r] ^= bitslice_ge<P>(planes[r], kmin[r]);
+}
+
+// --- narrow slices (width <= 8): unrolled carry-save counting --------------------------------
+// full adder and half adder on 64 lanes at once (each lowers to 3-input logic operations)
+__device__ __forceinline__ void full_add(uint64_t a, uint64_t b, uint64_t c, uint64_t& s,
+                                         uint64_t& cy) {
+    s = a ^ b ^ c;
+    cy = (a & b) | (c & (a ^ b));
+}
+
+__device__ __forceinline__ void half_add(uint64_t a, uint64_t b, uint64_t& s, uint64_t& cy) {
+    s = a ^ b;
+    cy = a & b;
+}
+
+// planes needed to count W one-bit inputs
+template <int W>
+struct CountBits { static constexpr int P = W <= 1 ? 1 : W <= 3 ? 2 : W <= 7 ? 3 : 4; };
+
+// p = bit-sliced number of set inputs among x[0..W-1], per lane (carry-save adder trees)
+template <int W>
+__device__ __forceinline__ void count_bits(const uint64_t (&x)[W], uint64_t (&p)[CountBits<W>::P]) {
+    if constexpr (W == 1) {
+        p[0] = x[0];
+    } else if constexpr (W == 2) {
+        half_add(x[0], x[1], p[0], p[1]);
+    } else if constexpr (W == 3) {
+        full_add(x[0], x[1], x[2], p[0], p[1]);
+    } else if constexpr (W == 4 || W == 5) {
+        uint64_t s1, c1, c2;
+        full_add(x[0], x[1], x[2], s1, c1);
+        if constexpr (W == 4) half_add(s1, x[3], p[0], c2);
+        else full_add(s1, x[3], x[4], p[0], c2);
+        half_add(c1, c2, p[1], p[2]);
+    } else if constexpr (W == 6 || W == 7) {
+        uint64_t s1, c1, s2, c2, c3;
+        full_add(x[0], x[1], x[2], s1, c1);
+        full_add(x[3], x[4], x[5], s2, c2);
+        if constexpr (W == 6) half_add(s1, s2, p[0], c3);
+        else full_add(s1, s2, x[6], p[0], c3);
+        full_add(c1, c2, c3, p[1], p[2]);
+    } else {
+        static_assert(W == 8, "narrow path covers widths 1..8");
+        uint64_t s1, c1, s2, c2, s3, c3, c4;
+        full_add(x[0], x[1], x[2], s1, c1);
+        full_add(x[3], x[4], x[5], s2, c2);
+        full_add(s1, s2, x[6], s3, c3);
+        half_add(s3, x[7], p[0], c4);
+        // the four weight-2 carries
+        uint64_t t1, d1, d2;
+        full_add(c1, c2, c3, t1, d1);
+        half_add(t1, c4, p[1], d2);
+        half_add(d1, d2, p[2], p[3]);
+    }
+}
+
+// lanes whose P-plane count u is >= k (0 <= k <= 2^P - 1): the carry out of u + (2^P - k)
+template <int P>
+__device__ __forceinline__ uint64_t at_least(const uint64_t (&p)[P], int k) {
+    const uint32_t c = (1u << P) - (uint32_t)k;
+    uint64_t carry = 0ull;
+#pragma unroll
+    for (int b = 0; b < P; ++b) {
+        const uint64_t cb = ((c >> b) & 1u) ? ~0ull : 0ull;
+        carry = (p[b] & carry) | (cb & (p[b] | carry));
+    }
+    return k == 0 ? ~0ull : carry;
+}
+
+template <int R, int W>
+__device__ __forceinline__ void count_and_flip_narrow(SpinWords<R>& si, const uint64_t* J,
+                                                      const uint64_t* gath, uint32_t loc,
+                                                      const int (&kmin)[R]) {
+    uint64_t x[R][W];
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+        const uint64_t Je = J[loc + 32 * e];
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[r][e] = si.v[r] ^ gath[(loc + 32 * e) * R + r] ^ Je;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        uint64_t p[CountBits<W>::P];
+        count_bits<W>(x[r], p);
+        si.v[r] ^= at_least<CountBits<W>::P>(p, kmin[r]);
+    }
 }
 
 constexpr uint32_t kStagePolls = 1u << 24;
@@ -233,7 +327,7 @@ __device__ __forceinline__ void gather_async(uint64_t* dst, const uint64_t* src,
 // reaches kmin = ceil((d - m*) / 2).  Independent of the neighbours, so a consumer warp computes
 // it for the next group while the current group's gathers are still in flight.
 template <int R>
-__device__ __forceinline__ void acceptance(const VbStage<R>& st, uint32_t warp, uint32_t lane,
+__device__ __forceinline__ void acceptance(const VbStream<R>& st, uint32_t warp, uint32_t lane,
                                            uint32_t t, int (&kmin)[R]) {
     const uint32_t vi = st.vinfo[warp * 32 + lane];
     const int deg = vi == kInactive ? 0 : (int)(vi >> kDegShift);
@@ -252,9 +346,10 @@ __device__ __forceinline__ void acceptance(const VbStage<R>& st, uint32_t warp, 
 
 // One consumer warp's work on one slice of a staged group (neighbour words already gathered).
 template <int R>
-__device__ __forceinline__ void update_slice(const VbPackedDev& d, const VbStage<R>& st,
-                                             const uint4& gi, uint32_t warp, uint32_t lane,
-                                             const int (&kmin)[R], uint64_t pol_keep) {
+__device__ __forceinline__ void update_slice(const VbPackedDev& d, const VbStream<R>& st,
+                                             const uint64_t* gath, const uint4& gi, uint32_t warp,
+                                             uint32_t lane, const int (&kmin)[R],
+                                             uint64_t pol_keep) {
     const bool wide = (gi.y & kWideGroup) != 0u;
     const uint32_t slice = gi.x + warp;
     const uint32_t vi = st.vinfo[warp * 32 + lane];
@@ -264,34 +359,53 @@ __device__ __forceinline__ void update_slice(const VbPackedDev& d, const VbStage
     SpinWords<R> si;
 #pragma unroll
     for (int r = 0; r < R; ++r) si.v[r] = st.S[(warp * 32 + lane) * R + r];
-    const VbStage<R>* sp = wide ? nullptr : &st;
+    const uint64_t* J = wide ? nullptr : st.J;
     const uint32_t loc = m.x - gi.z + lane, idx = m.x + lane;
-    // the slice's width (warp-uniform) sets the counter size
-    if (width <= 1) count_and_flip<R, 1>(si, sp, loc, width, d, idx, kmin);
-    else if (width <= 3) count_and_flip<R, 2>(si, sp, loc, width, d, idx, kmin);
-    else if (width <= 7) count_and_flip<R, 3>(si, sp, loc, width, d, idx, kmin);
-    else if (width <= 15) count_and_flip<R, 4>(si, sp, loc, width, d, idx, kmin);
-    else if (width <= 31) count_and_flip<R, 5>(si, sp, loc, width, d, idx, kmin);
-    else count_and_flip<R, 6>(si, sp, loc, width, d, idx, kmin);
+    // the slice's width (warp-uniform) selects the code: unrolled carry-save counting for the
+    // common narrow slices of a staged group, a ripple counter sized by the width otherwise
+    if (J && width <= 8) {
+        switch (width) {
+            case 0:  // isolated vertices: dE = 0, every lane flips (kmin = 0)
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (kmin[r] == 0) si.v[r] = ~si.v[r];
+                break;
+            case 1: count_and_flip_narrow<R, 1>(si, J, gath, loc, kmin); break;
+            case 2: count_and_flip_narrow<R, 2>(si, J, gath, loc, kmin); break;
+            case 3: count_and_flip_narrow<R, 3>(si, J, gath, loc, kmin); break;
+            case 4: count_and_flip_narrow<R, 4>(si, J, gath, loc, kmin); break;
+            case 5: count_and_flip_narrow<R, 5>(si, J, gath, loc, kmin); break;
+            case 6: count_and_flip_narrow<R, 6>(si, J, gath, loc, kmin); break;
+            case 7: count_and_flip_narrow<R, 7>(si, J, gath, loc, kmin); break;
+            default: count_and_flip_narrow<R, 8>(si, J, gath, loc, kmin); break;
+        }
+    } else if (width <= 1) count_and_flip<R, 1>(si, J, gath, loc, width, d, idx, kmin);
+    else if (width <= 3) count_and_flip<R, 2>(si, J, gath, loc, width, d, idx, kmin);
+    else if (width <= 7) count_and_flip<R, 3>(si, J, gath, loc, width, d, idx, kmin);
+    else if (width <= 15) count_and_flip<R, 4>(si, J, gath, loc, width, d, idx, kmin);
+    else if (width <= 31) count_and_flip<R, 5>(si, J, gath, loc, width, d, idx, kmin);
+    else count_and_flip<R, 6>(si, J, gath, loc, width, d, idx, kmin);
     store_words_keep<R>(d.S + ((int64_t)slice * 32 + lane) * R, si, pol_keep);
 }
 
 // Warp-specialised, persistent colour-class kernel.  Warp kGroupSlices (the producer) stages
-// the CTA's groups into a ring of NS shared-memory stages with bulk asynchronous copies; each
-// stage has a "full" mbarrier (bytes landed) and an "empty" one (released by the consumer
-// warps).  Consumer warp w owns slice w of every group: it starts the cp.async gathers of its
-// neighbours' words for the group L ahead, waits for the gathers of the current group, updates
-// its 32 vertices and releases the stage.  No CTA-wide barrier is on the path, so warps drift
-// independently, and NS stages keep copies in flight while others compute.
-template <int R, int NS, int L>
+// the stream part of the CTA's groups into a ring of NSS stages ("full" mbarrier: bytes landed;
+// "empty": released by the 8 consumer warps).  Consumer warp w owns slice w of every group: it
+// starts the cp.async gathers of its neighbours' words for the group L ahead into gather buffer
+// (k + L) mod NG (once every warp has released that buffer: "gfree" mbarrier), waits for the
+// gathers of the current group, updates its 32 vertices and releases both.  No CTA-wide barrier
+// is on the path, so warps drift independently.
+template <int R, int NSS, int NG, int L>
 __global__ void __launch_bounds__(32 * (kGroupSlices + 1))
     k_vb_packed_colour(VbPackedDev d, uint32_t g_begin, uint32_t g_end,
                        const uint32_t* __restrict__ clock, uint32_t t_off) {
-    static_assert(NS >= L + 1, "the producer must be able to run L groups ahead");
+    static_assert(L >= 1 && L < NG && L < NSS, "gathers run L groups ahead inside both rings");
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    VbStage<R>* stage = reinterpret_cast<VbStage<R>*>(smem_raw);
-    uint64_t* full = reinterpret_cast<uint64_t*>(stage + NS);
-    uint64_t* empty = full + NS;
+    VbStream<R>* stream = reinterpret_cast<VbStream<R>*>(smem_raw);
+    VbGath<R>* gath = reinterpret_cast<VbGath<R>*>(stream + NSS);
+    uint64_t* full = reinterpret_cast<uint64_t*>(gath + NG);
+    uint64_t* empty = full + NSS;
+    uint64_t* gfree = empty + NSS;
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
     const uint32_t t = __ldg(clock) + t_off;
     const uint64_t* __restrict__ S = d.S;
@@ -300,65 +414,82 @@ __global__ void __launch_bounds__(32 * (kGroupSlices + 1))
     const uint32_t n_mine = g0 < g_end ? (g_end - g0 + stride - 1) / stride : 0u;
 
     if (tid == 0) {
-        for (int s = 0; s < NS; ++s) {
+        for (int s = 0; s < NSS; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kGroupSlices);
         }
+        for (int b = 0; b < NG; ++b) mbar_init(&gfree[b], kGroupSlices);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
     if (warp == kGroupSlices) {
         // ------------------------------------------------------------------ producer
-        if (lane == 0) {
+        if (lane == 0 && n_mine) {
+            const uint32_t gtab_bytes = R * kVbThrStride * 4u + 16u;
+            uint4 gi_next = __ldg(&d.groups[g0]);
+            uint32_t graph_next = __ldg(&d.group_graph[g0]);
+            uint32_t issued = 0;
             for (uint32_t k = 0; k < n_mine; ++k) {
-                const int s = (int)(k % NS);
-                if (k >= (uint32_t)NS &&
-                    !mbar_wait(&empty[s], ((k / NS) - 1) & 1u, kStagePolls)) {
+                const uint4 gi = gi_next;
+                const uint32_t graph = graph_next;
+                if (k + 1 < n_mine) {  // the next descriptor's load overlaps this group's issue
+                    gi_next = __ldg(&d.groups[g0 + (k + 1) * stride]);
+                    graph_next = __ldg(&d.group_graph[g0 + (k + 1) * stride]);
+                }
+                const int s = (int)(k % NSS);
+                if (k >= (uint32_t)NSS &&
+                    !mbar_wait(&empty[s], ((k / NSS) - 1) & 1u, kStagePolls)) {
                     atomicOr(d.err, 4);
                     break;
                 }
-                const uint32_t g = g0 + k * stride;
-                const uint4 gi = d.groups[g];  // first slice, slices (| wide), entry, entries
                 const uint32_t nsl = gi.y & ~kWideGroup;
                 const bool wide = (gi.y & kWideGroup) != 0u;
                 const uint32_t nslot = nsl * 32u;
-                const uint32_t gtab_bytes = R * kVbThrStride * 4u + 16u;
                 const uint32_t bytes = nslot * 4u + nslot * R * 8u + nsl * 16u + gtab_bytes +
                                        (wide ? 0u : gi.w * 12u);
+                stream[s].gi = gi;  // published by the arrive below (release semantics)
                 mbar_expect_tx(&full[s], bytes);
-                bulk_copy_g2s_hint(stage[s].meta, d.slice_meta + gi.x, nsl * 16u, &full[s],
-                                   pol_stream);
-                bulk_copy_g2s(stage[s].thr, d.gtab + (size_t)d.group_graph[g] * gtab_bytes,
-                              gtab_bytes, &full[s]);
-                bulk_copy_g2s_hint(stage[s].vinfo, d.vinfo + (int64_t)gi.x * 32, nslot * 4u,
+                bulk_copy_g2s_hint(stream[s].meta, d.slice_meta + gi.x, nsl * 16u,
                                    &full[s], pol_stream);
-                bulk_copy_g2s_hint(stage[s].S, S + (int64_t)gi.x * 32 * R, nslot * R * 8u,
+                bulk_copy_g2s(stream[s].thr, d.gtab + (size_t)graph * gtab_bytes, gtab_bytes,
+                              &full[s]);
+                bulk_copy_g2s_hint(stream[s].vinfo, d.vinfo + (int64_t)gi.x * 32, nslot * 4u,
+                                   &full[s], pol_stream);
+                bulk_copy_g2s_hint(stream[s].S, S + (int64_t)gi.x * 32 * R, nslot * R * 8u,
                                    &full[s], pol_keep);
                 if (gi.w && !wide) {
-                    bulk_copy_g2s_hint(stage[s].col, d.col + gi.z, gi.w * 4u, &full[s],
+                    bulk_copy_g2s_hint(stream[s].col, d.col + gi.z, gi.w * 4u, &full[s],
                                        pol_stream);
-                    bulk_copy_g2s_hint(stage[s].J, d.jb + gi.z, gi.w * 8u, &full[s], pol_stream);
+                    bulk_copy_g2s_hint(stream[s].J, d.jb + gi.z, gi.w * 8u, &full[s], pol_stream);
                 }
+                issued = k + 1;
             }
+            // no copy may still be landing in shared memory when the CTA exits (the consumers
+            // wait for every stage they use; this matters only after a timeout)
+            for (uint32_t k = issued > (uint32_t)NSS ? issued - NSS : 0u; k < issued; ++k)
+                if (!mbar_wait(&full[k % NSS], (k / NSS) & 1u, kStagePolls)) atomicOr(d.err, 4);
         }
         return;
     }
 
     // ---------------------------------------------------------------------- consumers
-    // start the gathers of this warp's slice of group k (its stage has landed)
+    // start the gathers of this warp's slice of group k (its stream stage has landed and every
+    // warp has released the gather buffer's previous group)
     auto gathers = [&](uint32_t k) -> bool {
         if (k < n_mine) {
-            const int s = (int)(k % NS);
-            if (!mbar_wait(&full[s], (k / NS) & 1u, kStagePolls)) return false;
-            const uint4 gi = __ldg(&d.groups[g0 + k * stride]);
+            const int s = (int)(k % NSS), b = (int)(k % NG);
+            if (!mbar_wait(&full[s], (k / NSS) & 1u, kStagePolls)) return false;
+            if (k >= (uint32_t)NG && !mbar_wait(&gfree[b], ((k / NG) - 1) & 1u, kStagePolls))
+                return false;
+            const uint4 gi = stream[s].gi;
             const uint32_t nsl = gi.y & ~kWideGroup;
             if (warp < nsl && !(gi.y & kWideGroup) &&
-                stage[s].vinfo[warp * 32 + lane] != kInactive) {
-                const uint4 m = stage[s].meta[warp];
+                stream[s].vinfo[warp * 32 + lane] != kInactive) {
+                const uint4 m = stream[s].meta[warp];
                 uint32_t loc = m.x - gi.z + lane;
                 for (uint32_t e = 0; e < m.y; ++e, loc += 32)
-                    gather_async<R>(&stage[s].gath[loc * R], S + (int64_t)stage[s].col[loc] * R,
+                    gather_async<R>(&gath[b].v[loc * R], S + (int64_t)stream[s].col[loc] * R,
                                     pol_keep);
             }
         }
@@ -366,11 +497,12 @@ __global__ void __launch_bounds__(32 * (kGroupSlices + 1))
         return true;
     };
     bool ok = true;
-    for (uint32_t k = 0; k < (uint32_t)L; ++k) ok = ok && gathers(k);
+    // every give-up decision is taken by the whole warp (the loop holds __syncwarp)
+    for (uint32_t k = 0; k < (uint32_t)L; ++k) ok = ok && __all_sync(0xFFFFFFFFu, gathers(k));
     int kmin_next[R];
-    if (ok && n_mine) acceptance<R>(stage[0], warp, lane, t, kmin_next);
+    if (ok && n_mine) acceptance<R>(stream[0], warp, lane, t, kmin_next);
     for (uint32_t k = 0; ok && k < n_mine; ++k) {
-        if (!gathers(k + L)) {
+        if (!__all_sync(0xFFFFFFFFu, gathers(k + L))) {
             ok = false;
             break;
         }
@@ -378,36 +510,38 @@ __global__ void __launch_bounds__(32 * (kGroupSlices + 1))
 #pragma unroll
         for (int r = 0; r < R; ++r) kmin[r] = kmin_next[r];
         // the next group's random numbers and thresholds (its stage landed: k + 1 <= k + L)
-        if (k + 1 < n_mine) acceptance<R>(stage[(k + 1) % NS], warp, lane, t, kmin_next);
+        if (k + 1 < n_mine) acceptance<R>(stream[(k + 1) % NSS], warp, lane, t, kmin_next);
         asm volatile("cp.async.wait_group %0;" ::"n"(L) : "memory");
-        const int s = (int)(k % NS);
-        const uint4 gi = __ldg(&d.groups[g0 + k * stride]);
-        if (warp < (gi.y & ~kWideGroup)) update_slice<R>(d, stage[s], gi, warp, lane, kmin, pol_keep);
+        const int s = (int)(k % NSS), b = (int)(k % NG);
+        const uint4 gi = stream[s].gi;
+        if (warp < (gi.y & ~kWideGroup))
+            update_slice<R>(d, stream[s], gath[b].v, gi, warp, lane, kmin, pol_keep);
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
+        if (lane == 0) {
+            mbar_arrive(&empty[s]);
+            mbar_arrive(&gfree[b]);
+        }
     }
     if (!ok && lane == 0) atomicOr(d.err, 4);
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
-template <int R, int NS>
-static size_t colour_smem() {
-    return NS * sizeof(VbStage<R>) + 2 * NS * sizeof(uint64_t);
+template <int R, int NSS, int NG>
+static constexpr size_t colour_smem() {
+    return NSS * sizeof(VbStream<R>) + NG * sizeof(VbGath<R>) + (2 * NSS + NG) * sizeof(uint64_t);
 }
 
 static int g_num_sms = 0;
 
-// pipeline variants (the handle's autotuner picks one; none changes the results):
-//   variant 0: 4 stages, gathers 2 groups ahead, one CTA per SM
-//   variant 1: 3 stages, gathers 1 group ahead, two CTAs per SM
-//   variant 2: 2 stages, gathers 1 group ahead, three CTAs per SM
-template <int R, int NS, int L>
+template <int R, int NSS, int NG, int L>
 static void colour_launch_v(const VbPackedDev& d, uint32_t g_begin, uint32_t g_end,
                             const uint32_t* clock, uint32_t t_off, int per_sm, cudaStream_t st) {
+    constexpr size_t smem = colour_smem<R, NSS, NG>();
+    static_assert(smem <= 227 * 1024, "pipeline shape exceeds the shared memory of one CTA");
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(k_vb_packed_colour<R, NS, L>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)colour_smem<R, NS>());
+        cudaFuncSetAttribute(k_vb_packed_colour<R, NSS, NG, L>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured = true;
     }
     if (!g_num_sms) {
@@ -419,16 +553,26 @@ static void colour_launch_v(const VbPackedDev& d, uint32_t g_begin, uint32_t g_e
     const uint32_t ng = g_end - g_begin;
     const uint32_t cap = (uint32_t)g_num_sms * (uint32_t)per_sm;
     const uint32_t grid = ng < cap ? ng : cap;
-    k_vb_packed_colour<R, NS, L><<<grid, 32 * (kGroupSlices + 1), colour_smem<R, NS>(), st>>>(
+    k_vb_packed_colour<R, NSS, NG, L><<<grid, 32 * (kGroupSlices + 1), smem, st>>>(
         d, g_begin, g_end, clock, t_off);
 }
 
+// pipeline shapes (the handle's autotuner picks one; none changes the results), as
+// (stream stages, gather buffers, gather lookahead, CTAs per SM):
+//   R = 1, 2: variant 0 (3, 2, 1, 2), variant 1 (4, 2, 1, 2), variant 2 (2, 2, 1, 3)
+//   R = 4:    variant 0 (4, 2, 1, 1), variant 1 (2, 2, 1, 2), variant 2 (3, 2, 1, 1)
 template <int R>
 static void colour_launch(const VbPackedDev& d, uint32_t g_begin, uint32_t g_end,
                           const uint32_t* clock, uint32_t t_off, int variant, cudaStream_t st) {
-    if (variant == 0) colour_launch_v<R, 4, 2>(d, g_begin, g_end, clock, t_off, 1, st);
-    else if (variant == 1) colour_launch_v<R, 3, 1>(d, g_begin, g_end, clock, t_off, R == 4 ? 1 : 2, st);
-    else colour_launch_v<R, 2, 1>(d, g_begin, g_end, clock, t_off, R == 4 ? 2 : 3, st);
+    if constexpr (R == 4) {
+        if (variant == 0) colour_launch_v<R, 4, 2, 1>(d, g_begin, g_end, clock, t_off, 1, st);
+        else if (variant == 1) colour_launch_v<R, 2, 2, 1>(d, g_begin, g_end, clock, t_off, 2, st);
+        else colour_launch_v<R, 3, 2, 1>(d, g_begin, g_end, clock, t_off, 1, st);
+    } else {
+        if (variant == 0) colour_launch_v<R, 3, 2, 1>(d, g_begin, g_end, clock, t_off, 2, st);
+        else if (variant == 1) colour_launch_v<R, 4, 2, 1>(d, g_begin, g_end, clock, t_off, 2, st);
+        else colour_launch_v<R, 2, 2, 1>(d, g_begin, g_end, clock, t_off, 3, st);
+    }
 }
 
 int vb_packed_colour(const VbPackedDev& d, uint32_t g_begin, uint32_t g_end,

@@ -108,6 +108,19 @@ def test_packed_various_shapes(n, c, R, temps, sweeps):
     assert_matches_oracle(g, 64, R, sg.SG_VB_PACKED, sweeps, tw, tm, spins, C, q, E)
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("R,temps", [(1, [0.8]), (2, [1.0, 0.6]), (4, [1.0, 1.0, 0.6, 0.6])])
+def test_packed_every_pipeline_shape(monkeypatch, variant, R, temps):
+    """Each pipeline shape of the colour kernel, pinned (no autotuner), on a graph large enough
+    that every CTA wraps around its stream and gather rings several times (1.5 M vertices:
+    about 2000 groups in the largest colour class); lanes 0..3 compared with the oracle."""
+    monkeypatch.setenv("SG_VB_COLOUR_VARIANT", str(variant))
+    g = vb_instance(1_500_001, 4.0, 77, temps, 2**40 + 7)
+    tw, tm = sg_inputs.log_schedule([0, 1], 3)
+    spins, C, q, E, _ = run_gpu([g], 4, R, sg.SG_VB_PACKED, 3, tw, tm)
+    assert_matches_oracle(g, 4, R, sg.SG_VB_PACKED, 3, tw, tm, spins, C, q, E)
+
+
 def test_packed_isolated_vertices_and_max_degree():
     # a star with 63 leaves (maximum degree), a path, and isolated vertices (always flip: dE = 0)
     n = 100
