@@ -126,13 +126,18 @@ struct VbPackedDev {
     const uint4* slice_meta;     // [n_slices] {first entry, width, graph, 0}
     const uint32_t* group_graph; // [n_groups] graph of each group (groups never mix graphs)
     const uint8_t* gtab;         // [n_graphs] {uint32 thr[R][64]; uint64 seed; uint64 pad}
+    const uint32_t* colour_groups;  // [n_colours+1] first group of each colour class
     int* err;                    // device status word (bounded waits)
+    uint32_t* gbar;              // [2] grid-barrier arrivals and exits of a fused sweep (zeroed)
     uint64_t* S;                 // [n_slots][R]
     uint64_t* snap;              // [n_tw][n_slots][R]
     int64_t n_slots;
     int32_t n_slices;
     int32_t R;
+    int32_t n_colours;
 };
+
+constexpr int kVbMaxColours = 64;  // greedy colouring with degree <= 63
 
 // Viana-Bray plain layout (one graph, colour-major CSR, int8 spins per lane).
 struct VbPlainDev {
@@ -163,10 +168,13 @@ struct VbCountJob {
 int vb_packed_init(const VbPackedDev& d, cudaStream_t st);
 // sweep index t = *clock + t_off (the clock lives in device memory so that captured CUDA graphs
 // can be replayed at any time)
-// variant (0 .. kVbColourVariants - 1) selects the pipeline shape: stream stages, gather
-// buffers, gather lookahead and CTAs per SM; every shape gives the same results
-int vb_packed_colour(const VbPackedDev& d, uint32_t group_begin, uint32_t group_end,
-                     const uint32_t* clock, uint32_t t_off, int variant, cudaStream_t st);
+// One sweep of every colour class in colour order.  variant (0 .. kVbColourVariants - 1)
+// selects the pipeline shape (stream stages, gather buffers, gather lookahead, CTAs per SM);
+// fused runs the classes in one cooperative launch with grid-wide barriers between them
+// (R = 2, 4), else one launch per class.  colour_groups is the host copy of d.colour_groups.
+// No choice changes the results.  Returns the launches queued, or -1.
+int vb_packed_sweep(const VbPackedDev& d, const uint32_t* colour_groups, const uint32_t* clock,
+                    uint32_t t_off, int variant, bool fused, cudaStream_t st);
 constexpr int kVbColourVariants = 3;
 int vb_packed_snapshot(const VbPackedDev& d, int w, cudaStream_t st);
 int vb_packed_count(const VbPackedDev& d, const VbCountJob& job, cudaStream_t st);

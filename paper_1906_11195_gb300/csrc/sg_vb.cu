@@ -170,16 +170,25 @@ public:
             up((void*)pk_.group_graph, h_group_graph_.data(), h_group_graph_.size() * 4);
             up((void*)pk_.gtab, h_gtab_.data(), h_gtab_.size());
             check_cuda(cudaMemsetAsync(pk_.err, 0, 4, st), "memset");
+            up((void*)pk_.colour_groups, colour_group_.data(), colour_group_.size() * 4);
+            check_cuda(cudaMemsetAsync(pk_.gbar, 0, 8, st), "memset");
             up((void*)pk_.jb, h_jb_.data(), h_jb_.size() * 8);
             std::vector<uint64_t> seeds(n_inst);
             for (int b = 0; b < n_inst; ++b) seeds[b] = graphs_[b].seed;
             up((void*)pk_.seeds, seeds.data(), seeds.size() * 8);
             launches += vb_packed_init(pk_, st);
-            // SG_VB_COLOUR_VARIANT=<k> pins the pipeline shape (reproducible timings of one
-            // shape); otherwise the autotuner picks the fastest
+            // SG_VB_COLOUR_VARIANT=<k> and SG_VB_FUSED=<0|1> pin the pipeline shape and the
+            // launch form (reproducible timings of one choice); otherwise the autotuner picks
             const char* pin = getenv("SG_VB_COLOUR_VARIANT");
-            if (pin && *pin >= '0' && *pin < '0' + kVbColourVariants && !pin[1]) variant_ = *pin - '0';
-            else tune_variant(st);
+            const char* pin_f = getenv("SG_VB_FUSED");
+            const bool pinned = pin && *pin >= '0' && *pin < '0' + kVbColourVariants && !pin[1];
+            const bool pinned_f = pin_f && (*pin_f == '0' || *pin_f == '1') && !pin_f[1];
+            if (pinned && pinned_f) {
+                variant_ = *pin - '0';
+                fused_ = *pin_f == '1';
+            } else {
+                tune_variant(st, pinned ? *pin - '0' : -1, pinned_f ? *pin_f - '0' : -1);
+            }
         } else {
             up((void*)pl_.row_ptr, h_row_ptr_.data(), h_row_ptr_.size() * 4);
             up((void*)pl_.col, h_col_i_.data(), h_col_i_.size() * 4);
@@ -194,42 +203,63 @@ public:
         check_cuda(cudaStreamSynchronize(st), "attach");
     }
 
-    // Autotuner: time two sweeps with each pipeline shape of the colour kernel and keep the
-    // fastest, then redraw the initial spins (the trial sweeps leave no trace: the initial
-    // configuration is a pure function of the seed, and no measurement was taken).
-    void tune_variant(cudaStream_t st) {
+    // Autotuner: time two sweeps with each pipeline shape of the colour kernel, launched per
+    // colour class and (R = 2, 4) fused into one cooperative launch per sweep, and keep the
+    // fastest; then redraw the initial spins (the trial sweeps leave no trace: the initial
+    // configuration is a pure function of the seed, and no measurement was taken).  A choice
+    // whose launch is refused (e.g. a cooperative grid that cannot be resident) is skipped.
+    // only_v / only_f >= 0 restrict the search to one shape / launch form.
+    void tune_variant(cudaStream_t st, int only_v, int only_f) {
         cudaEvent_t e0, e1;
         check_cuda(cudaEventCreate(&e0), "cudaEventCreate");
         check_cuda(cudaEventCreate(&e1), "cudaEventCreate");
         float best = 0.f;
-        int best_v = 0;
-        for (int v = 0; v < kVbColourVariants; ++v) {
-            variant_ = v;
-            check_cuda(cudaMemsetAsync(clock_dev, 0, 4, st), "memset");
-            sweep(0, st);  // warm-up
-            check_cuda(cudaEventRecord(e0, st), "cudaEventRecord");
-            sweep(1, st);
-            sweep(2, st);
-            check_cuda(cudaEventRecord(e1, st), "cudaEventRecord");
-            check_cuda(cudaEventSynchronize(e1), "cudaEventSynchronize");
-            float ms = 0.f;
-            check_cuda(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
-            if (v == 0 || ms < best) {
-                best = ms;
-                best_v = v;
+        int best_v = -1;
+        bool best_f = false;
+        const bool can_fuse = R != 1 && colour_group_.size() > 2;
+        for (int f = 0; f < (can_fuse ? 2 : 1); ++f) {
+            if (only_f >= 0 && f != only_f) continue;
+            for (int v = 0; v < kVbColourVariants; ++v) {
+                if (only_v >= 0 && v != only_v) continue;
+                variant_ = v;
+                fused_ = f == 1;
+                float ms = 0.f;
+                try {
+                    check_cuda(cudaMemsetAsync(clock_dev, 0, 4, st), "memset");
+                    sweep(0, st);  // warm-up
+                    check_cuda(cudaEventRecord(e0, st), "cudaEventRecord");
+                    sweep(1, st);
+                    sweep(2, st);
+                    check_cuda(cudaEventRecord(e1, st), "cudaEventRecord");
+                    check_cuda(cudaEventSynchronize(e1), "cudaEventSynchronize");
+                    check_cuda(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+                } catch (const Error&) {
+                    cudaGetLastError();
+                    check_cuda(cudaStreamSynchronize(st), "autotuner");
+                    continue;
+                }
+                if (best_v < 0 || ms < best) {
+                    best = ms;
+                    best_v = v;
+                    best_f = fused_;
+                }
             }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        if (best_v < 0) fail(SG_ECUDA, "no colour-kernel configuration could be launched");
+        if (device_status(st)) fail(SG_ETIMEOUT, "device wait expired while tuning the colour kernel");
         variant_ = best_v;
+        fused_ = best_f;
         launches += vb_packed_init(pk_, st);
     }
 
     void sweep(uint32_t t_off, cudaStream_t st) override {
         if (kernel_ == SG_VB_PACKED) {
-            for (size_t c = 0; c + 1 < colour_group_.size(); ++c)
-                launches += vb_packed_colour(pk_, colour_group_[c], colour_group_[c + 1], clock_dev,
-                                             t_off, variant_, st);
+            const int n = vb_packed_sweep(pk_, colour_group_.data(), clock_dev, t_off, variant_,
+                                          fused_, st);
+            if (n < 0) fail(SG_ECUDA, "colour kernel launch failed");
+            launches += n;
         } else {
             for (size_t c = 0; c + 1 < colour_begin_.size(); ++c)
                 launches += vb_plain_colour(pl_, colour_begin_[c], colour_begin_[c + 1], clock_dev,
@@ -424,6 +454,8 @@ private:
             pk_.group_graph = c.take<uint32_t>(h_group_graph_.size());
             pk_.gtab = c.take<uint8_t>(h_gtab_.size());
             pk_.err = c.take<int>(1);
+            pk_.colour_groups = c.take<uint32_t>(colour_group_.size());
+            pk_.gbar = c.take<uint32_t>(2);
             pk_.jb = c.take<uint64_t>(h_jb_.size());
             pk_.seeds = c.take<uint64_t>(n_inst);
             pk_.S = c.take<uint64_t>((size_t)n_slots_ * R);
@@ -432,6 +464,8 @@ private:
             pk_.n_slots = n_slots_;
             pk_.n_slices = (int32_t)(n_slots_ / 32);
             pk_.R = R;
+            pk_.n_colours = (int32_t)colour_group_.size() - 1;
+            if (pk_.n_colours > kVbMaxColours) fail(SG_EINVAL, "more colour classes than supported");
         } else {
             const Graph& g = graphs_[0];
             pl_.row_ptr = c.take<int32_t>(h_row_ptr_.size());
@@ -620,7 +654,8 @@ private:
     }
 
     int kernel_ = SG_VB_PACKED;
-    int variant_ = 0;  // colour-kernel pipeline shape chosen by the autotuner at attach
+    int variant_ = 0;     // colour-kernel pipeline shape chosen by the autotuner at attach
+    bool fused_ = false;  // one cooperative launch per sweep (else one launch per colour class)
     int Lc_ = 64;
     size_t ws_bytes_ = 0;
     std::vector<Graph> graphs_;

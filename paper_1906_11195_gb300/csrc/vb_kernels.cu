@@ -74,29 +74,12 @@ __device__ __forceinline__ SpinWords<R> gather_words(const uint64_t* p) {
     if constexpr (R == 1) {
         s.v[0] = __ldg(p);
     } else if constexpr (R == 2) {
-        const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(p));
+        const ulonglong2 a = __ldcg(reinterpret_cast<const ulonglong2*>(p));
         s.v[0] = a.x; s.v[1] = a.y;
     } else {
-        const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(p));
-        const ulonglong2 b = __ldg(reinterpret_cast<const ulonglong2*>(p) + 1);
+        const ulonglong2 a = __ldcg(reinterpret_cast<const ulonglong2*>(p));
+        const ulonglong2 b = __ldcg(reinterpret_cast<const ulonglong2*>(p) + 1);
         s.v[0] = a.x; s.v[1] = a.y; s.v[2] = b.x; s.v[3] = b.y;
-    }
-    return s;
-}
-
-// gather of a neighbour's words through the read-only path with an L2 evict-last policy
-template <int R>
-__device__ __forceinline__ SpinWords<R> gather_words_keep(const uint64_t* p, uint64_t pol) {
-    SpinWords<R> s;
-    if constexpr (R == 1) {
-        asm volatile("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;"
-                     : "=l"(s.v[0]) : "l"(p), "l"(pol));
-    } else {
-#pragma unroll
-        for (int h = 0; h < R / 2; ++h)
-            asm volatile("ld.global.nc.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
-                         : "=l"(s.v[2 * h]), "=l"(s.v[2 * h + 1])
-                         : "l"(p + 2 * h), "l"(pol));
     }
     return s;
 }
@@ -112,18 +95,6 @@ __device__ __forceinline__ void store_words_keep(uint64_t* p, const SpinWords<R>
             asm volatile("st.global.L2::cache_hint.v2.u64 [%0], {%1, %2}, %3;" ::"l"(p + 2 * h),
                          "l"(s.v[2 * h]), "l"(s.v[2 * h + 1]), "l"(pol)
                          : "memory");
-    }
-}
-
-template <int R>
-__device__ __forceinline__ void store_words(uint64_t* p, const SpinWords<R>& s) {
-    if constexpr (R == 1) {
-        p[0] = s.v[0];
-    } else if constexpr (R == 2) {
-        *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(s.v[0], s.v[1]);
-    } else {
-        reinterpret_cast<ulonglong2*>(p)[0] = make_ulonglong2(s.v[0], s.v[1]);
-        reinterpret_cast<ulonglong2*>(p)[1] = make_ulonglong2(s.v[2], s.v[3]);
     }
 }
 
@@ -388,19 +359,73 @@ __device__ __forceinline__ void update_slice(const VbPackedDev& d, const VbStrea
     store_words_keep<R>(d.S + ((int64_t)slice * 32 + lane) * R, si, pol_keep);
 }
 
-// Warp-specialised, persistent colour-class kernel.  Warp kGroupSlices (the producer) stages
-// the stream part of the CTA's groups into a ring of NSS stages ("full" mbarrier: bytes landed;
-// "empty": released by the 8 consumer warps).  Consumer warp w owns slice w of every group: it
-// starts the cp.async gathers of its neighbours' words for the group L ahead into gather buffer
-// (k + L) mod NG (once every warp has released that buffer: "gfree" mbarrier), waits for the
-// gathers of the current group, updates its 32 vertices and releases both.  No CTA-wide barrier
-// is on the path, so warps drift independently.
+// Grid-wide barrier between colour classes of one launch, taken by the 256 consumer threads of
+// every CTA (the producer warp keeps staging).  `alive` is this thread's health; the CTA joins
+// the grid barrier only if every consumer thread is alive, so a CTA that gave up makes the
+// others time out (bounded) instead of hanging.  Returns the same value to all consumers.
+constexpr uint32_t kGridPolls = 1u << 22;
+
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool consumers_all(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, 256, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0u;
+}
+
+__device__ __forceinline__ bool grid_barrier(uint32_t* count, uint32_t target, int* err,
+                                             uint32_t tid, bool alive) {
+    __shared__ int passed;
+    if (!consumers_all(alive)) return false;  // also orders this CTA's spin stores before the fence
+    if (tid == 0) {
+        __threadfence();
+        atomicAdd(count, 1u);
+        int ok = 1;
+        for (uint32_t polls = 0; ld_acquire_gpu(count) < target; ++polls) {
+            if (polls >= kGridPolls) {
+                atomicOr(err, 8);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+        passed = ok;
+    }
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+    return passed != 0;
+}
+
+// Warp-specialised, persistent colour-class kernel over the colour classes [c_begin, c_end) of
+// one sweep.  Warp kGroupSlices (the producer) stages the stream part of the CTA's groups, in
+// colour order, into a ring of NSS stages ("full" mbarrier: bytes landed; "empty": released by
+// the 8 consumer warps); it runs ahead across colour boundaries, which is safe because the
+// stream part holds nothing a colour class writes (a class writes only its own vertices' words,
+// staged when that class is reached).  Consumer warp w owns slice w of every group: it starts
+// the cp.async gathers of its neighbours' words for the group L ahead (within the class) into
+// gather buffer (k + L) mod NG once every warp has released it ("gfree" mbarrier), waits for the
+// gathers of the current group, updates its 32 vertices and releases both.  Between two classes
+// the consumers of all CTAs meet at a grid-wide barrier, so no gather of class c + 1 is issued
+// before every word of class c is written; such launches are cooperative (all CTAs resident).
 template <int R, int NSS, int NG, int L>
 __global__ void __launch_bounds__(32 * (kGroupSlices + 1))
-    k_vb_packed_colour(VbPackedDev d, uint32_t g_begin, uint32_t g_end,
+    k_vb_packed_colour(VbPackedDev d, uint32_t c_begin, uint32_t c_end,
                        const uint32_t* __restrict__ clock, uint32_t t_off) {
     static_assert(L >= 1 && L < NG && L < NSS, "gathers run L groups ahead inside both rings");
     extern __shared__ __align__(128) uint8_t smem_raw[];
+    __shared__ uint32_t s_kc[kVbMaxColours + 1];  // first ring index of each class (this CTA)
+    __shared__ uint32_t s_cg[kVbMaxColours];      // first group of each class
     VbStream<R>* stream = reinterpret_cast<VbStream<R>*>(smem_raw);
     VbGath<R>* gath = reinterpret_cast<VbGath<R>*>(stream + NSS);
     uint64_t* full = reinterpret_cast<uint64_t*>(gath + NG);
@@ -410,8 +435,7 @@ __global__ void __launch_bounds__(32 * (kGroupSlices + 1))
     const uint32_t t = __ldg(clock) + t_off;
     const uint64_t* __restrict__ S = d.S;
     const uint64_t pol_stream = l2_evict_first(), pol_keep = l2_evict_last();
-    const uint32_t g0 = g_begin + blockIdx.x, stride = gridDim.x;
-    const uint32_t n_mine = g0 < g_end ? (g_end - g0 + stride - 1) / stride : 0u;
+    const uint32_t nc = c_end - c_begin;
 
     if (tid == 0) {
         for (int s = 0; s < NSS; ++s) {
@@ -420,22 +444,39 @@ __global__ void __launch_bounds__(32 * (kGroupSlices + 1))
         }
         for (int b = 0; b < NG; ++b) mbar_init(&gfree[b], kGroupSlices);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        uint32_t acc = 0;
+        for (uint32_t j = 0; j < nc; ++j) {
+            const uint32_t a = __ldg(&d.colour_groups[c_begin + j]);
+            const uint32_t b = __ldg(&d.colour_groups[c_begin + j + 1]);
+            s_cg[j] = a;
+            s_kc[j] = acc;
+            acc += a + blockIdx.x < b ? (b - a - blockIdx.x + gridDim.x - 1) / gridDim.x : 0u;
+        }
+        s_kc[nc] = acc;
     }
     __syncthreads();
+    const uint32_t n_mine = s_kc[nc];
 
     if (warp == kGroupSlices) {
         // ------------------------------------------------------------------ producer
         if (lane == 0 && n_mine) {
             const uint32_t gtab_bytes = R * kVbThrStride * 4u + 16u;
-            uint4 gi_next = __ldg(&d.groups[g0]);
-            uint32_t graph_next = __ldg(&d.group_graph[g0]);
+            auto group_of = [&](uint32_t k, uint32_t& j) -> uint32_t {
+                while (k >= s_kc[j + 1]) ++j;
+                return s_cg[j] + blockIdx.x + (k - s_kc[j]) * gridDim.x;
+            };
+            uint32_t jn = 0;
+            uint32_t g_next = group_of(0, jn);
+            uint4 gi_next = __ldg(&d.groups[g_next]);
+            uint32_t graph_next = __ldg(&d.group_graph[g_next]);
             uint32_t issued = 0;
             for (uint32_t k = 0; k < n_mine; ++k) {
                 const uint4 gi = gi_next;
                 const uint32_t graph = graph_next;
                 if (k + 1 < n_mine) {  // the next descriptor's load overlaps this group's issue
-                    gi_next = __ldg(&d.groups[g0 + (k + 1) * stride]);
-                    graph_next = __ldg(&d.group_graph[g0 + (k + 1) * stride]);
+                    g_next = group_of(k + 1, jn);
+                    gi_next = __ldg(&d.groups[g_next]);
+                    graph_next = __ldg(&d.group_graph[g_next]);
                 }
                 const int s = (int)(k % NSS);
                 if (k >= (uint32_t)NSS &&
@@ -450,8 +491,8 @@ __global__ void __launch_bounds__(32 * (kGroupSlices + 1))
                                        (wide ? 0u : gi.w * 12u);
                 stream[s].gi = gi;  // published by the arrive below (release semantics)
                 mbar_expect_tx(&full[s], bytes);
-                bulk_copy_g2s_hint(stream[s].meta, d.slice_meta + gi.x, nsl * 16u,
-                                   &full[s], pol_stream);
+                bulk_copy_g2s_hint(stream[s].meta, d.slice_meta + gi.x, nsl * 16u, &full[s],
+                                   pol_stream);
                 bulk_copy_g2s(stream[s].thr, d.gtab + (size_t)graph * gtab_bytes, gtab_bytes,
                               &full[s]);
                 bulk_copy_g2s_hint(stream[s].vinfo, d.vinfo + (int64_t)gi.x * 32, nslot * 4u,
@@ -474,10 +515,10 @@ __global__ void __launch_bounds__(32 * (kGroupSlices + 1))
     }
 
     // ---------------------------------------------------------------------- consumers
-    // start the gathers of this warp's slice of group k (its stream stage has landed and every
-    // warp has released the gather buffer's previous group)
-    auto gathers = [&](uint32_t k) -> bool {
-        if (k < n_mine) {
+    // start the gathers of this warp's slice of group k if k < k_end (its stream stage has
+    // landed and every warp has released the gather buffer's previous group)
+    auto gathers = [&](uint32_t k, uint32_t k_end) -> bool {
+        if (k < k_end) {
             const int s = (int)(k % NSS), b = (int)(k % NG);
             if (!mbar_wait(&full[s], (k / NSS) & 1u, kStagePolls)) return false;
             if (k >= (uint32_t)NG && !mbar_wait(&gfree[b], ((k / NG) - 1) & 1u, kStagePolls))
@@ -496,34 +537,61 @@ __global__ void __launch_bounds__(32 * (kGroupSlices + 1))
         asm volatile("cp.async.commit_group;" ::: "memory");
         return true;
     };
-    bool ok = true;
     // every give-up decision is taken by the whole warp (the loop holds __syncwarp)
-    for (uint32_t k = 0; k < (uint32_t)L; ++k) ok = ok && __all_sync(0xFFFFFFFFu, gathers(k));
+    bool ok = true;
     int kmin_next[R];
-    if (ok && n_mine) acceptance<R>(stream[0], warp, lane, t, kmin_next);
-    for (uint32_t k = 0; ok && k < n_mine; ++k) {
-        if (!__all_sync(0xFFFFFFFFu, gathers(k + L))) {
-            ok = false;
-            break;
+    if (n_mine) {
+        ok = __all_sync(0xFFFFFFFFu, mbar_wait(&full[0], 0u, kStagePolls));
+        if (ok) acceptance<R>(stream[0], warp, lane, t, kmin_next);
+    }
+    for (uint32_t j = 0; j < nc; ++j) {
+        const uint32_t kb = s_kc[j], ke = s_kc[j + 1];
+        if (j > 0) {
+            ok = grid_barrier(d.gbar, j * gridDim.x, d.err, tid, ok);
+            if (!ok) break;
         }
-        int kmin[R];
+        for (uint32_t k = kb; ok && k < kb + L; ++k) ok = __all_sync(0xFFFFFFFFu, gathers(k, ke));
+        for (uint32_t k = kb; ok && k < ke; ++k) {
+            if (!__all_sync(0xFFFFFFFFu, gathers(k + L, ke))) {
+                ok = false;
+                break;
+            }
+            int kmin[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) kmin[r] = kmin_next[r];
-        // the next group's random numbers and thresholds (its stage landed: k + 1 <= k + L)
-        if (k + 1 < n_mine) acceptance<R>(stream[(k + 1) % NSS], warp, lane, t, kmin_next);
-        asm volatile("cp.async.wait_group %0;" ::"n"(L) : "memory");
-        const int s = (int)(k % NSS), b = (int)(k % NG);
-        const uint4 gi = stream[s].gi;
-        if (warp < (gi.y & ~kWideGroup))
-            update_slice<R>(d, stream[s], gath[b].v, gi, warp, lane, kmin, pol_keep);
-        __syncwarp();
-        if (lane == 0) {
-            mbar_arrive(&empty[s]);
-            mbar_arrive(&gfree[b]);
+            for (int r = 0; r < R; ++r) kmin[r] = kmin_next[r];
+            // the next group's random numbers and thresholds; inside the class its stage has
+            // landed (k + 1 <= k + L), across a class boundary it is waited for here
+            if (k + 1 < n_mine) {
+                const uint32_t kn = k + 1;
+                if (kn >= ke)
+                    ok = __all_sync(0xFFFFFFFFu, mbar_wait(&full[kn % NSS], (kn / NSS) & 1u,
+                                                           kStagePolls));
+                if (ok) acceptance<R>(stream[kn % NSS], warp, lane, t, kmin_next);
+            }
+            asm volatile("cp.async.wait_group %0;" ::"n"(L) : "memory");
+            if (!ok) break;
+            const int s = (int)(k % NSS), b = (int)(k % NG);
+            const uint4 gi = stream[s].gi;
+            if (warp < (gi.y & ~kWideGroup))
+                update_slice<R>(d, stream[s], gath[b].v, gi, warp, lane, kmin, pol_keep);
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&empty[s]);
+                mbar_arrive(&gfree[b]);
+            }
         }
     }
-    if (!ok && lane == 0) atomicOr(d.err, 4);
     asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (!ok && lane == 0) atomicOr(d.err, 4);
+    if (nc > 1) {
+        // the last CTA past every barrier of this launch rearms the counters for the next one
+        if (consumers_all(ok) && tid == 0) {
+            if (atomicAdd(&d.gbar[1], 1u) == gridDim.x - 1) {
+                atomicExch(&d.gbar[0], 0u);
+                atomicExch(&d.gbar[1], 0u);
+            }
+        }
+    }
 }
 
 template <int R, int NSS, int NG>
@@ -533,28 +601,53 @@ static constexpr size_t colour_smem() {
 
 static int g_num_sms = 0;
 
-template <int R, int NSS, int NG, int L>
-static void colour_launch_v(const VbPackedDev& d, uint32_t g_begin, uint32_t g_end,
-                            const uint32_t* clock, uint32_t t_off, int per_sm, cudaStream_t st) {
-    constexpr size_t smem = colour_smem<R, NSS, NG>();
-    static_assert(smem <= 227 * 1024, "pipeline shape exceeds the shared memory of one CTA");
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncSetAttribute(k_vb_packed_colour<R, NSS, NG, L>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        configured = true;
-    }
+static int num_sms() {
     if (!g_num_sms) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
         if (g_num_sms <= 0) g_num_sms = 148;
     }
-    const uint32_t ng = g_end - g_begin;
-    const uint32_t cap = (uint32_t)g_num_sms * (uint32_t)per_sm;
-    const uint32_t grid = ng < cap ? ng : cap;
-    k_vb_packed_colour<R, NSS, NG, L><<<grid, 32 * (kGroupSlices + 1), smem, st>>>(
-        d, g_begin, g_end, clock, t_off);
+    return g_num_sms;
+}
+
+// one launch per colour class (c_end = c_begin + 1), or one cooperative launch for the classes
+// [c_begin, c_end) with every CTA resident
+template <int R, int NSS, int NG, int L>
+static int colour_launch_v(const VbPackedDev& d, uint32_t c_begin, uint32_t c_end, uint32_t ng,
+                           const uint32_t* clock, uint32_t t_off, int per_sm, cudaStream_t st) {
+    constexpr size_t smem = colour_smem<R, NSS, NG>();
+    static_assert(smem <= 227 * 1024, "pipeline shape exceeds the shared memory of one CTA");
+    auto kern = k_vb_packed_colour<R, NSS, NG, L>;
+    static int resident = -1;
+    if (resident < 0) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 32 * (kGroupSlices + 1), smem) !=
+            cudaSuccess)
+            n = 0;
+        resident = n;
+    }
+    const int cps = per_sm < resident ? per_sm : resident;
+    if (cps <= 0) return -1;
+    const uint32_t cap = (uint32_t)num_sms() * (uint32_t)cps;
+    if (c_end == c_begin + 1) {
+        if (!ng) return 0;
+        const uint32_t grid = ng < cap ? ng : cap;
+        kern<<<grid, 32 * (kGroupSlices + 1), smem, st>>>(d, c_begin, c_end, clock, t_off);
+        return 1;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cap);
+    cfg.blockDim = dim3(32 * (kGroupSlices + 1));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, d, c_begin, c_end, clock, t_off) == cudaSuccess ? 1 : -1;
 }
 
 // pipeline shapes (the handle's autotuner picks one; none changes the results), as
@@ -562,30 +655,48 @@ static void colour_launch_v(const VbPackedDev& d, uint32_t g_begin, uint32_t g_e
 //   R = 1, 2: variant 0 (3, 2, 1, 2), variant 1 (4, 2, 1, 2), variant 2 (2, 2, 1, 3)
 //   R = 4:    variant 0 (4, 2, 1, 1), variant 1 (2, 2, 1, 2), variant 2 (3, 2, 1, 1)
 template <int R>
-static void colour_launch(const VbPackedDev& d, uint32_t g_begin, uint32_t g_end,
-                          const uint32_t* clock, uint32_t t_off, int variant, cudaStream_t st) {
+static int colour_launch(const VbPackedDev& d, uint32_t c_begin, uint32_t c_end, uint32_t ng,
+                         const uint32_t* clock, uint32_t t_off, int variant, cudaStream_t st) {
     if constexpr (R == 4) {
-        if (variant == 0) colour_launch_v<R, 4, 2, 1>(d, g_begin, g_end, clock, t_off, 1, st);
-        else if (variant == 1) colour_launch_v<R, 2, 2, 1>(d, g_begin, g_end, clock, t_off, 2, st);
-        else colour_launch_v<R, 3, 2, 1>(d, g_begin, g_end, clock, t_off, 1, st);
+        if (variant == 0) return colour_launch_v<R, 4, 2, 1>(d, c_begin, c_end, ng, clock, t_off, 1, st);
+        if (variant == 1) return colour_launch_v<R, 2, 2, 1>(d, c_begin, c_end, ng, clock, t_off, 2, st);
+        return colour_launch_v<R, 3, 2, 1>(d, c_begin, c_end, ng, clock, t_off, 1, st);
     } else {
-        if (variant == 0) colour_launch_v<R, 3, 2, 1>(d, g_begin, g_end, clock, t_off, 2, st);
-        else if (variant == 1) colour_launch_v<R, 4, 2, 1>(d, g_begin, g_end, clock, t_off, 2, st);
-        else colour_launch_v<R, 2, 2, 1>(d, g_begin, g_end, clock, t_off, 3, st);
+        if (variant == 0) return colour_launch_v<R, 3, 2, 1>(d, c_begin, c_end, ng, clock, t_off, 2, st);
+        if (variant == 1) return colour_launch_v<R, 4, 2, 1>(d, c_begin, c_end, ng, clock, t_off, 2, st);
+        return colour_launch_v<R, 2, 2, 1>(d, c_begin, c_end, ng, clock, t_off, 3, st);
     }
 }
 
-int vb_packed_colour(const VbPackedDev& d, uint32_t g_begin, uint32_t g_end,
-                     const uint32_t* clock, uint32_t t_off, int variant, cudaStream_t st) {
-    if (g_end <= g_begin) return 0;
-    switch (d.R) {
-        case 1: colour_launch<1>(d, g_begin, g_end, clock, t_off, variant, st); break;
-        case 2: colour_launch<2>(d, g_begin, g_end, clock, t_off, variant, st); break;
-        case 4: colour_launch<4>(d, g_begin, g_end, clock, t_off, variant, st); break;
-        default: return -1;
+// One sweep (fused: one cooperative launch over all colour classes; else one launch per class).
+// The fused form needs coherent gathers across classes inside a launch, which the 16-byte
+// L2-only copies give for R = 2 and 4; R = 1 (8-byte copies through L1) uses one launch per class.
+int vb_packed_sweep(const VbPackedDev& d, const uint32_t* colour_groups, const uint32_t* clock,
+                    uint32_t t_off, int variant, bool fused, cudaStream_t st) {
+    const uint32_t nc = (uint32_t)d.n_colours;
+    if (!nc) return 0;
+    if (fused && nc > 1 && d.R != 1) {
+        int r = -1;
+        if (d.R == 2) r = colour_launch<2>(d, 0, nc, 0, clock, t_off, variant, st);
+        else if (d.R == 4) r = colour_launch<4>(d, 0, nc, 0, clock, t_off, variant, st);
+        return r;
     }
-    return 1;
+    int n = 0;
+    for (uint32_t c = 0; c < nc; ++c) {
+        const uint32_t ng = colour_groups[c + 1] - colour_groups[c];
+        int r = -1;
+        switch (d.R) {
+            case 1: r = colour_launch<1>(d, c, c + 1, ng, clock, t_off, variant, st); break;
+            case 2: r = colour_launch<2>(d, c, c + 1, ng, clock, t_off, variant, st); break;
+            case 4: r = colour_launch<4>(d, c, c + 1, ng, clock, t_off, variant, st); break;
+            default: return -1;
+        }
+        if (r < 0) return -1;
+        n += r;
+    }
+    return n;
 }
+
 
 // ---------------------------------------------------------------------------------------------
 // snapshot copy (16-byte vectors; the regions are 256-byte aligned and a multiple of 16 bytes)

@@ -108,17 +108,35 @@ def test_packed_various_shapes(n, c, R, temps, sweeps):
     assert_matches_oracle(g, 64, R, sg.SG_VB_PACKED, sweeps, tw, tm, spins, C, q, E)
 
 
+@pytest.mark.parametrize("fused", [0, 1])
 @pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("R,temps", [(1, [0.8]), (2, [1.0, 0.6]), (4, [1.0, 1.0, 0.6, 0.6])])
-def test_packed_every_pipeline_shape(monkeypatch, variant, R, temps):
-    """Each pipeline shape of the colour kernel, pinned (no autotuner), on a graph large enough
-    that every CTA wraps around its stream and gather rings several times (1.5 M vertices:
-    about 2000 groups in the largest colour class); lanes 0..3 compared with the oracle."""
+def test_packed_every_pipeline_shape(monkeypatch, variant, fused, R, temps):
+    """Each pipeline shape of the colour kernel, launched per colour class and fused into one
+    cooperative launch per sweep (R = 1 always runs per class), pinned (no autotuner), on a
+    graph large enough that every CTA wraps around its stream and gather rings several times
+    (1.5 M vertices: about 2000 groups in the largest colour class); lanes 0..3 compared with
+    the oracle."""
     monkeypatch.setenv("SG_VB_COLOUR_VARIANT", str(variant))
+    monkeypatch.setenv("SG_VB_FUSED", str(fused))
     g = vb_instance(1_500_001, 4.0, 77, temps, 2**40 + 7)
     tw, tm = sg_inputs.log_schedule([0, 1], 3)
     spins, C, q, E, _ = run_gpu([g], 4, R, sg.SG_VB_PACKED, 3, tw, tm)
     assert_matches_oracle(g, 4, R, sg.SG_VB_PACKED, 3, tw, tm, spins, C, q, E)
+
+
+@pytest.mark.parametrize("fused", [0, 1])
+def test_packed_fused_small_and_batched(monkeypatch, fused):
+    """Fused sweeps where most CTAs own no group of a colour class (small uneven graphs in one
+    batch), with measurements between the sweeps; each graph equals its own oracle run."""
+    monkeypatch.setenv("SG_VB_COLOUR_VARIANT", "2")
+    monkeypatch.setenv("SG_VB_FUSED", str(fused))
+    sizes = sg_inputs.log_uniform_sizes(5, 4, 12, 8)
+    graphs = [vb_instance(int(n), 4.0, 700 + i, [1.0, 0.6], 70 + i) for i, n in enumerate(sizes)]
+    tw, tm = sg_inputs.log_schedule([0, 3], 40)
+    spins, C, q, E, _ = run_gpu(graphs, 64, 2, sg.SG_VB_PACKED, 40, tw, tm, chunks=[1, 5, 7])
+    for b, g in enumerate(graphs):
+        assert_matches_oracle(g, 64, 2, sg.SG_VB_PACKED, 40, tw, tm, spins, C, q, E, b=b)
 
 
 def test_packed_isolated_vertices_and_max_degree():
