@@ -120,21 +120,31 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0, int prev_b0
     // this warp's replica state first (independent loads, in flight during the staging)
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const bool active = r < d.R;
+    // every load of this warp's state is issued before any result is used
     int h[NC];
     int kst[NC];
-    uint32_t sw[NC];
+    uint32_t sw[NC], pF[NC], psn[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         const int i = b0 + 32 * c + lane;
         h[c] = active ? d.H[(int64_t)r * d.Np + i] : 0;
         kst[c] = active ? d.kst[(int64_t)r * d.Np + i] : 0;
         sw[c] = active ? d.S[(int64_t)r * words + wb + c] : 0u;
+        const bool pv = active && prev_b0 >= 0;
+        pF[c] = pv ? d.flips[(int64_t)r * words + pwb + c] : 0u;
+        psn[c] = pv ? d.S[(int64_t)r * words + pwb + c] : 0u;
     }
+    // the block's coupling bits (own columns, previous block's columns) land in shared memory
+    // through asynchronous copies, all in flight together
     for (int k = threadIdx.x; k < 32 * NC * nw; k += blockDim.x) {
         const int row = k / nw, w = k % nw;
         const int col_word = w < NC ? wb + w : pwb + (w - NC);
-        jblk[row * W + w] = d.Jbits[(int64_t)(b0 + row) * words + col_word];
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(&jblk[row * W + w])),
+                     "l"(d.Jbits + (int64_t)(b0 + row) * words + col_word)
+                     : "memory");
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     if (!active) return;
     if (prev_b0 >= 0) {
@@ -144,9 +154,9 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0, int prev_b0
         for (int c = 0; c < NC; ++c) dh[c] = 0;
 #pragma unroll
         for (int cp = 0; cp < NC; ++cp) {
-            const uint32_t F = d.flips[(int64_t)r * words + pwb + cp];
+            const uint32_t F = pF[cp];
             if (!F) continue;
-            const uint32_t sn = d.S[(int64_t)r * words + pwb + cp];
+            const uint32_t sn = psn[cp];
             const int pf = __popc(F);
 #pragma unroll
             for (int c = 0; c < NC; ++c)
