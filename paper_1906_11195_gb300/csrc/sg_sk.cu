@@ -323,6 +323,9 @@ private:
     void set_block(int B) {
         B_ = B;
         kw_ = B >= 128 ? 128 : 64;
+        // replica tile of the field GEMM: 64 columns for the short (K <= 128) updates, which
+        // doubles the CTAs sharing each row tile's epilogue; 128 for the longer ones
+        NT_ = R <= 64 ? R : (B <= 128 && R % 64 == 0 ? 64 : std::min(R, 128));
         if (sk_field_prepare(B_, kw_, NT_) != 0)
             fail(SG_ECUDA, "cannot raise the field kernel's shared memory limit");
         make_map_2d(&mapJ_, d_.J8, Np_, Np_, Np_, kw_, 128);

@@ -110,13 +110,15 @@ int sk_kstar_sweep(const SkDev& d, const uint32_t* clock, uint32_t t_off, cudaSt
 // --------------------------------------------------------------------------------------------
 template <int NC>
 __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0, int prev_b0) {
-    extern __shared__ uint32_t jblk[];  // [32 * NC rows][2 * NC words]: own cols, previous cols
-    constexpr int W = 2 * NC;
+    // [32 * NC rows][2 * NC words + 1]: own cols, previous cols; the odd row stride keeps the
+    // 32 lanes (32 consecutive rows) on 32 different banks
+    extern __shared__ uint32_t jblk[];
+    constexpr int W = 2 * NC + 1;
     const int lane = threadIdx.x & 31;
     const int words = d.Np / 32;
     const int wb = b0 / 32;
     const int pwb = prev_b0 >= 0 ? prev_b0 / 32 : 0;
-    const int nw = prev_b0 >= 0 ? W : NC;
+    const int nw = prev_b0 >= 0 ? 2 * NC : NC;  // words staged per row
     // this warp's replica state first (independent loads, in flight during the staging)
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const bool active = r < d.R;
@@ -174,16 +176,20 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0, int prev_b0
         const uint32_t sbit = (sw[c] >> lane) & 1u;
         const int x = sbit ? -h[c] : h[c];
         const uint32_t neg = jblk[(32 * c + lane) * W + c] ^ sw[c] ^ (sbit ? 0xFFFFFFFFu : 0u);
-        uint32_t F = 0;
-        int resolved = 0;
-        while (resolved < 32) {
-            const int cur = x - 2 * (__popc(F) - 2 * __popc(F & neg));
-            const bool tent = (lane >= resolved) && (cur <= kst[c]);
+        // Resolve the chunk's 32 sequential decisions: every lane past the last accepted flip
+        // decides with the fields as they stand; the lowest lane that flips is accepted (the
+        // lanes below it keep their decision), its flip moves every later lane's k by +2 or -2 (by
+        // that lane's coupling bit), and the rest is decided again.  Only ALU work and a ballot per accepted flip.
+        uint32_t F = 0, last = 0;  // accepted flips; lowest-bit mask of the last one (0: none)
+        const uint32_t lane_bit = 1u << lane;
+        int cur = x;
+        for (;;) {
+            const bool tent = lane_bit > last && cur <= kst[c];
             const uint32_t bm = __ballot_sync(0xFFFFFFFFu, tent);
             if (bm == 0u) break;
-            const int p = __ffs(bm) - 1;
-            F |= 1u << p;
-            resolved = p + 1;
+            last = bm & (0u - bm);
+            F |= last;
+            cur += (neg & last) ? 2 : -2;
         }
         const uint32_t nsw = sw[c] ^ F;
         // changes D_i = (s' - s)/2 for the field GEMM: -s_old where flipped
@@ -209,7 +215,7 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0, int prev_b0
 int sk_inblock(const SkDev& d, int b0, int prev_b0, int B, cudaStream_t st) {
     const unsigned nb = (unsigned)((d.R + 7) / 8);
     const int nc = B / 32;
-    const size_t smem = (size_t)32 * nc * 2 * nc * 4;
+    const size_t smem = (size_t)32 * nc * (2 * nc + 1) * 4;
     switch (nc) {
         case 2: k_sk_inblock<2><<<nb, 256, smem, st>>>(d, b0, prev_b0); break;
         case 4: k_sk_inblock<4><<<nb, 256, smem, st>>>(d, b0, prev_b0); break;
@@ -223,7 +229,7 @@ int sk_inblock(const SkDev& d, int b0, int prev_b0, int B, cudaStream_t st) {
 int sk_inblock_prepare() {
     const cudaError_t e = cudaFuncSetAttribute(k_sk_inblock<16>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               32 * 16 * 32 * 4);
+                                               32 * 16 * 33 * 4);
     return e == cudaSuccess ? 0 : -1;
 }
 
