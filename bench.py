@@ -330,8 +330,9 @@ def run_vb_batch(args):
 
 def run_sk(args):
     """SK workload (not the headline line): N = 8192, +-1 couplings, 256 replicas sharing J,
-    T = 0.4, block B = 128; one step = one sweep.  Prints one JSON line with the blocked
-    (tensor-core) and plain kernels' throughput."""
+    T = 0.4; one step = one sweep.  The line's value is the configured block B (--sk-block,
+    default 128); the same sweep with the other block sizes and with the autotuner's choice
+    (block = 0) is reported beside it (B never changes the trajectory), with the plain kernel."""
     import torch
 
     import paper_1906_11195_gb300 as sg
@@ -340,27 +341,40 @@ def run_sk(args):
     torch.cuda.set_device(0)
     J = sg_inputs.sk_couplings(SK_N, 3)
     stream = torch.cuda.current_stream()
-    out = {"metric": "spin updates/ns", "unit": "spin updates/ns",
-           "config": {"workload": f"sk_blocked_N{SK_N}_R{SK_R}_T{SK_T}_B{args.sk_block}"}}
-    run = sg.SKRun(J, [SK_T] * SK_R, 1, kernel=sg.SG_SK_BLOCKED, block=args.sk_block)
-    run.sweep(args.warmup)
-    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0 = run.launches
-    nvtx_push("timed_region")
-    e0.record(stream)
-    run.sweep(args.steps)
-    e1.record(stream)
-    nvtx_pop()
-    torch.cuda.synchronize()
-    run.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    launches = run.launches - l0
-    run.close()
+
+    def timed(block):
+        run = sg.SKRun(J, [SK_T] * SK_R, 1, kernel=sg.SG_SK_BLOCKED, block=block)
+        run.sweep(args.warmup)
+        torch.cuda.synchronize()
+        l0 = run.launches
+        nvtx_push("timed_region")
+        e0.record(stream)
+        run.sweep(args.steps)
+        e1.record(stream)
+        nvtx_pop()
+        torch.cuda.synchronize()
+        run.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        launches = run.launches - l0
+        run.close()
+        return ms, launches
+
+    ms, launches = timed(args.sk_block)
     flops = 2.0 * SK_N * SK_N * SK_R  # field update per sweep (all rows, all blocks)
-    out.update({"value": SK_N * SK_R / (ms * 1e6), "ms_per_step": ms, "steps": args.steps,
-                "warmup": args.warmup, "gpu_launches": launches,
-                "field_gemm_tflops_over_sweep": flops / (ms * 1e-3) / 1e12})
+    out = {"metric": "spin updates/ns", "unit": "spin updates/ns",
+           "config": {"workload": f"sk_blocked_N{SK_N}_R{SK_R}_T{SK_T}_B{args.sk_block}"},
+           "value": SK_N * SK_R / (ms * 1e6), "ms_per_step": ms, "steps": args.steps,
+           "warmup": args.warmup, "gpu_launches": launches,
+           "field_gemm_tflops_over_sweep": flops / (ms * 1e-3) / 1e12}
+    others = {}
+    for b in (64, 128, 256, 512, 0):
+        if b == args.sk_block:
+            continue
+        bms, _ = timed(b)
+        others["autotuned" if b == 0 else f"B{b}"] = {
+            "value": SK_N * SK_R / (bms * 1e6), "ms_per_step": bms}
+    out["other_blocks"] = others
     if not args.skip_plain:
         pr = sg.SKRun(J, [SK_T] * SK_R, 1, kernel=sg.SG_SK_PLAIN)
         pr.sweep(1)
@@ -376,167 +390,49 @@ def run_sk(args):
     return 0
 
 
-def run_gpu(args):
+def run_sk_batch(args):
+    """Batched uneven SK workload (not the headline line): 32 samples, N = round(2^U),
+    U ~ Uniform[9, 14], +-1 couplings, R = 128 replicas (64 at T = 0.4, 64 at T = 0.6), block
+    chosen per sample by the autotuner; all samples advance in lock-step, one CUDA graph
+    branch per sample.  One step = one sweep of every sample."""
     import torch
 
     import paper_1906_11195_gb300 as sg
     from paper_1906_11195_gb300 import _build
-
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
-    dev = torch.device("cuda", torch.cuda.current_device())
-    if rank == 0:
-        _build.build()
-    if ws > 1:
-        dist.barrier()
     _build.build()
-
-    rp, col, jb = instance(rank)
-    tw, tm = sg_inputs.log_schedule(TW, T_MAX)
-    graphs = [dict(row_ptr=rp, col=col, jbits=jb, seed=1 + rank, temps=[T] * REPLICAS) for T in TEMPS]
-    stream = torch.cuda.current_stream(dev)
-
-    runs = [sg.VBRun([g], n_lanes=LANES, n_replicas=REPLICAS, kernel=sg.SG_VB_PACKED, tw=tw, tm=tm,
-                     device=dev, stream=stream) for g in graphs]
-    for r in runs:
-        r.sweep(args.warmup)
-    torch.cuda.synchronize()
-    launches0 = sum(r.launches for r in runs)
-
-    sampler = ClockSampler(local)
-    sampler.start()
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    nvtx_push("timed_region")  # lets a profiler capture exactly the timed launches
-    ev0.record(stream)
-    for r in runs:
-        r.sweep(args.steps)
-    ev1.record(stream)
-    nvtx_pop()
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    launches = sum(r.launches for r in runs) - launches0
-    for r in runs:
-        r.synchronize()
-    ms = max_over_ranks(ms, dev)
-    updates_per_step = len(TEMPS) * N_VERTS * LANES * REPLICAS
-    value = job_value(updates_per_step, args.steps, ws, ms)
-    for r in runs:
-        r.close()
-
-    # roofline of the colour kernel: a handle with no measurement schedule times pure sweeps
-    kr = max(20, min(args.steps, 200))
-    rl = sg.VBRun([graphs[0]], n_lanes=LANES, n_replicas=REPLICAS, kernel=sg.SG_VB_PACKED,
-                  device=dev, stream=stream)
-    rl.sweep(3)
+    torch.cuda.set_device(0)
+    sizes = [int(x) for x in sg_inputs.log_uniform_sizes(32, 9, 14, 5)]
+    R = 128
+    t0 = time.perf_counter()
+    samples = [dict(J=sg_inputs.sk_couplings(n, (5 << 20) + k), seed=(5 << 20) + k,
+                    temps=[0.4] * (R // 2) + [0.6] * (R // 2)) for k, n in enumerate(sizes)]
+    log(f"generated {len(samples)} SK samples, sum N = {sum(sizes)} in {time.perf_counter() - t0:.1f} s")
+    t0 = time.perf_counter()
+    run = sg.SKBatchRun(samples, R, kernel=sg.SG_SK_BLOCKED, block=0)
+    log(f"created, attached and tuned in {time.perf_counter() - t0:.1f} s")
+    stream = torch.cuda.current_stream()
+    run.sweep(args.warmup)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = run.launches
+    nvtx_push("timed_region")
     e0.record(stream)
-    rl.sweep(kr)
+    run.sweep(args.steps)
     e1.record(stream)
+    nvtx_pop()
     torch.cuda.synchronize()
-    sweep_ms = e0.elapsed_time(e1) / kr
-    rl.close()
-    bytes_sweep = algorithmic_bytes_per_sweep(N_VERTS, int(rp[-1]), REPLICAS)
-    peak, peak_kind = peaks()
-    # achieved: the colour kernel's algorithmic bytes of every sweep in the timed region over the
-    # whole timed region (the few snapshot/measurement launches in it count against the kernel,
-    # so this is a lower bound); achieved_isolated: the same over sweeps timed alone
-    sweep_ms_timed = ms / (args.steps * len(TEMPS))
-    achieved = bytes_sweep / (sweep_ms_timed * 1e-3) / 1e9
-    traffic = recorded_traffic()
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                "kernel": "k_vb_packed_colour<2>, one unit = one sweep (all colour classes)",
-                "algorithmic_bytes_per_sweep": bytes_sweep, "ms_per_sweep": sweep_ms_timed,
-                "achieved_isolated": bytes_sweep / (sweep_ms * 1e-3) / 1e9,
-                "ms_per_sweep_isolated": sweep_ms}
-
-    # the plain one-thread-per-(vertex, lane, replica) kernel on the same graph, T = 1.0
-    plain = None
-    if not args.skip_plain:
-        pr = sg.VBRun([graphs[0]], n_lanes=LANES, n_replicas=REPLICAS, kernel=sg.SG_VB_PLAIN,
-                      device=dev, stream=stream)
-        pr.sweep(1)
-        torch.cuda.synchronize()
-        kp = 3
-        e0.record(stream)
-        pr.sweep(kp)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        pms = e0.elapsed_time(e1) / kp
-        pr.close()
-        plain = {"value": N_VERTS * LANES * REPLICAS / (pms * 1e6), "unit": "spin updates/ns",
-                 "ms_per_sweep": pms, "sweeps": kp}
-
-    # end to end through the public API: H2D of the prepared instances, K sweeps each, D2H of
-    # the measurement counts; host-side instance preparation (validation, colouring, layout)
-    # happens before the timed region
-    handles, bufs = [], []
-    for g in graphs:
-        h = sg.sg_create_vb([g], LANES, REPLICAS, sg.SG_VB_PACKED, tw, tm)
-        nb = sg.sg_workspace_bytes(h)
-        handles.append((h, nb))
-        bufs.append(torch.empty(nb, dtype=torch.uint8, device=dev))
-    h2d = sum(nb for _, nb in handles)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for (h, nb), buf in zip(handles, bufs):
-        sg.sg_attach(h, buf.data_ptr(), nb, stream.cuda_stream)
-    for h, _ in handles:
-        sg.sg_sweep(h, args.warmup + args.steps)
-    d2h = 0
-    for h, _ in handles:
-        C, q, E = sg.sg_read_results(h)
-        d2h += C.nbytes + q.nbytes + E.nbytes
-    e2e_s = time.perf_counter() - t0
-    for h, _ in handles:
-        sg.sg_destroy(h)
-    e2e_steps = args.warmup + args.steps
-    e2e = {"value": ws * updates_per_step * e2e_steps / (e2e_s * 1e9), "unit": "spin updates/ns",
-           "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
-           "note": "H2D of the device image of both instances + sweeps + D2H of all counts, "
-                   "bytes spread over the steps"}
-
-    cpu = None
-    if rank == 0 and ws == 1 and not args.skip_cpu:
-        cpu = cpu_baseline_sample(rp, col, jb)
-
-    if ws > 1:
-        dist.barrier()
-        dist.destroy_process_group()
-    if rank != 0:
-        return 0
-    line = {
-        "metric": "spin updates/ns", "value": value, "unit": "spin updates/ns", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": N_VERTS, "mean_degree": MEAN_DEGREE, "lanes": LANES,
-                   "replicas": REPLICAS, "temps": list(TEMPS), "step": "1 sweep of each temperature",
-                   "schedule": f"tw=2^4..2^15, log-spaced measurements to 2^16 ({len(tm)} times)",
-                   "l2": "inputs larger than L2: 201 MB of graph streamed per sweep (spins, 64 MiB, "
-                         "are meant to stay in L2)",
-                   "parallelism": f"replicas only, {ws} independent instance(s)"},
-        "roofline": roofline,
-        "gpu_launches": launches,
-        "clocks": clocks,
-        "e2e": e2e,
-        "cpu_baseline": cpu,
-        "plain_kernel": plain,
-        "speedup_vs_plain": (value / ws) / plain["value"] if plain else None,
-    }
-    print(json.dumps(line), flush=True)
+    run.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    updates = sum(sizes) * R
+    flops = sum(2.0 * n * n * R for n in sizes)
+    out = {"metric": "spin updates/ns", "unit": "spin updates/ns",
+           "value": updates / (ms * 1e6), "ms_per_step": ms, "steps": args.steps,
+           "warmup": args.warmup, "gpu_launches": run.launches - l0,
+           "config": {"workload": "sk_batch_32_samples_N2^9..2^14_R128_T0.4+0.6_autotuned_B",
+                      "sizes": sizes},
+           "field_gemm_tflops_over_sweep": flops / (ms * 1e-3) / 1e12}
+    run.close()
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -555,9 +451,10 @@ def main():
     ap.add_argument("--profile-log2n", type=int, default=22, help="log2 N of the profile case")
     ap.add_argument("--profile-replicas", type=int, default=2, choices=[2, 4],
                     help="replicas of the profile case (4: two per temperature)")
-    ap.add_argument("--workload", default="vb", choices=["vb", "sk", "vb_batch"],
+    ap.add_argument("--workload", default="vb", choices=["vb", "sk", "vb_batch", "sk_batch"],
                     help="vb: the headline bit-packed Viana-Bray line; sk: the SK blocked line; "
-                         "vb_batch: the uneven batch of Viana-Bray graphs")
+                         "vb_batch: the uneven batch of Viana-Bray graphs; sk_batch: the uneven "
+                         "batch of SK samples")
     ap.add_argument("--batch", type=int, default=512, help="graphs in the vb_batch workload")
     ap.add_argument("--sk-block", type=int, default=SK_B)
     args = ap.parse_args()
@@ -571,6 +468,8 @@ def main():
         return run_sk(args)
     if args.workload == "vb_batch":
         return run_vb_batch(args)
+    if args.workload == "sk_batch":
+        return run_sk_batch(args)
     return run_gpu(args)
 
 

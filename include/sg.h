@@ -111,7 +111,8 @@ int sg_create_vb(const sg_vb_graph *graphs, int32_t n_graphs, int32_t n_lanes,
  *   seed       Philox key
  *   kernel     SG_SK_PLAIN or SG_SK_BLOCKED
  *   block      spins per block B for SG_SK_BLOCKED: 64, 128, 256 or 512, or 0 to let the
- *              autotuner choose among 64, 128 and 256 at attach; ignored by SG_SK_PLAIN
+ *              autotuner choose at attach among 64, 128, 256 and, for n >= 2048, 512 (n is
+ *              then padded to a multiple of 512, else of 256); ignored by SG_SK_PLAIN
  *   tw, tm     schedule, as for sg_create_vb */
 int sg_create_sk(int32_t n, const int8_t *J, int32_t n_replicas, const double *temps,
                  uint64_t seed, int32_t kernel, int32_t block, const int64_t *tw, int32_t n_tw,
@@ -129,8 +130,8 @@ typedef struct {
 /* Create a batch of independent SK samples of uneven size (the uneven-N runs used for the
  * extrapolation in N of SI section 1) that advance in lock-step; each sweep is one CUDA graph
  * whose branches, one per sample, run concurrently.  Arguments as for sg_create_sk; every sample
- * has n_replicas replicas.  block = 0 lets an autotuner pick B in {64, 128, 256} per sample by
- * timing trial sweeps at attach (the trajectory does not depend on B).  Results are laid out
+ * has n_replicas replicas.  block = 0 lets an autotuner pick B per sample, as for sg_create_sk,
+ * by timing trial sweeps at attach (the trajectory does not depend on B).  Results are laid out
  * with n_inst = n_samples; spins concatenate int8[R][n_s] over the samples. */
 int sg_create_sk_batch(const sg_sk_sample *samples, int32_t n_samples, int32_t n_replicas,
                        int32_t kernel, int32_t block, const int64_t *tw, int32_t n_tw,

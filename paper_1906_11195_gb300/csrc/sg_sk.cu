@@ -75,8 +75,9 @@ public:
             B_ = autotune_ ? 128 : block;
             kw_ = B_ >= 128 ? 128 : 64;
             NT_ = R <= 128 ? R : 128;
-            // autotuning picks among 64, 128 and 256, which all divide a multiple of 256
-            const int unit = autotune_ ? 256 : std::max(128, B_);
+            // autotuning picks among 64, 128, 256 and (for n >= 2048, where the padding to a
+            // multiple of 512 costs at most a quarter more) 512
+            const int unit = autotune_ ? (n >= 2048 ? 512 : 256) : std::max(128, B_);
             Np_ = (n + unit - 1) / unit * unit;
         } else {
             Np_ = (n + 127) / 128 * 128;
@@ -179,7 +180,7 @@ public:
         if (B_ < 128) {
             // a row tile spans two blocks: plain sequence in-block(b) -> full field update
             for (int b = 0; b < nblocks; ++b) {
-                if (sk_inblock(d_, b * B_, -1, B_, st) < 0) fail(SG_EINVAL, "unsupported block size");
+                if (sk_inblock(d_, b * B_, -1, B_, false, st) < 0) fail(SG_ECUDA, "in-block launch failed");
                 ++launches;
                 launches += sk_field_update(d_, mapJ_, mapD_, b * B_, B_, kw_, NT_, 2, st);
             }
@@ -196,8 +197,8 @@ public:
                 check_cuda(cudaStreamWaitEvent(st, side_done_[b & 1], 0), "cudaStreamWaitEvent");
                 pending[b & 1] = false;
             }
-            if (sk_inblock(d_, b0, b > 0 ? b0 - B_ : -1, B_, st) < 0)
-                fail(SG_EINVAL, "unsupported block size");
+            if (sk_inblock(d_, b0, b > 0 ? b0 - B_ : -1, B_, b > 0, st) < 0)
+                fail(SG_ECUDA, "in-block launch failed");
             ++launches;
             // rows of block b+1 are left to in-block(b+1); the last block updates every row.
             // The rows written here are disjoint from those in-block(b+1) writes concurrently,
@@ -358,7 +359,7 @@ private:
         check_cuda(cudaEventCreate(&e1), "cudaEventCreate");
         float best_ms = 0.f;
         int best = 128;
-        for (int B : {64, 128, 256}) {
+        for (int B : {64, 128, 256, 512}) {
             if (Np_ % B) continue;
             set_block(B);
             init_state(st);

@@ -28,7 +28,9 @@ struct SkDev {
 int sk_init(const SkDev& d, cudaStream_t st);
 int sk_kstar_sweep(const SkDev& d, const uint32_t* clock, uint32_t t_off, cudaStream_t st);
 // prev_b0 < 0: no previous-block update folded in (the caller's field GEMM covered those rows)
-int sk_inblock(const SkDev& d, int b0, int prev_b0, int B, cudaStream_t st);
+// after_inblock: the launch directly follows the previous block's in-block kernel in stream
+// order (programmatic dependent launch); otherwise a plain launch
+int sk_inblock(const SkDev& d, int b0, int prev_b0, int B, bool after_inblock, cudaStream_t st);
 int sk_inblock_prepare();
 size_t sk_field_smem_bytes(int B, int kw, int NT);
 int sk_field_prepare(int B, int kw, int NT);

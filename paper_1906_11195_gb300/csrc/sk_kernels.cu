@@ -119,23 +119,16 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0, int prev_b0
     const int wb = b0 / 32;
     const int pwb = prev_b0 >= 0 ? prev_b0 / 32 : 0;
     const int nw = prev_b0 >= 0 ? 2 * NC : NC;  // words staged per row
-    // this warp's replica state first (independent loads, in flight during the staging)
+    // A programmatic launch after the previous block's in-block kernel: let the next block's
+    // kernel start its own prologue now (it reads nothing of ours before its dependency wait).
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const bool active = r < d.R;
-    // every load of this warp's state is issued before any result is used
-    int h[NC];
+    // Prologue on data no in-block kernel writes (couplings, the sweep's K* table): may run
+    // while the previous block is still being updated.
     int kst[NC];
-    uint32_t sw[NC], pF[NC], psn[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        const int i = b0 + 32 * c + lane;
-        h[c] = active ? d.H[(int64_t)r * d.Np + i] : 0;
-        kst[c] = active ? d.kst[(int64_t)r * d.Np + i] : 0;
-        sw[c] = active ? d.S[(int64_t)r * words + wb + c] : 0u;
-        const bool pv = active && prev_b0 >= 0;
-        pF[c] = pv ? d.flips[(int64_t)r * words + pwb + c] : 0u;
-        psn[c] = pv ? d.S[(int64_t)r * words + pwb + c] : 0u;
-    }
+    for (int c = 0; c < NC; ++c) kst[c] = active ? d.kst[(int64_t)r * d.Np + b0 + 32 * c + lane] : 0;
     // the block's coupling bits (own columns, previous block's columns) land in shared memory
     // through asynchronous copies, all in flight together
     for (int k = threadIdx.x; k < 32 * NC * nw; k += blockDim.x) {
@@ -146,6 +139,20 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0, int prev_b0
                      : "memory");
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
+    // Everything below depends on the previous block (spins, flips, fields): wait until that
+    // kernel has completed and its writes are visible (immediate for a plain launch).
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    int h[NC];
+    uint32_t sw[NC], pF[NC], psn[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int i = b0 + 32 * c + lane;
+        h[c] = active ? d.H[(int64_t)r * d.Np + i] : 0;
+        sw[c] = active ? d.S[(int64_t)r * words + wb + c] : 0u;
+        const bool pv = active && prev_b0 >= 0;
+        pF[c] = pv ? d.flips[(int64_t)r * words + pwb + c] : 0u;
+        psn[c] = pv ? d.S[(int64_t)r * words + pwb + c] : 0u;
+    }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     if (!active) return;
@@ -212,18 +219,30 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0, int prev_b0
     }
 }
 
-int sk_inblock(const SkDev& d, int b0, int prev_b0, int B, cudaStream_t st) {
+int sk_inblock(const SkDev& d, int b0, int prev_b0, int B, bool after_inblock, cudaStream_t st) {
     const unsigned nb = (unsigned)((d.R + 7) / 8);
     const int nc = B / 32;
-    const size_t smem = (size_t)32 * nc * (2 * nc + 1) * 4;
+    void (*kern)(SkDev, int, int) = nullptr;
     switch (nc) {
-        case 2: k_sk_inblock<2><<<nb, 256, smem, st>>>(d, b0, prev_b0); break;
-        case 4: k_sk_inblock<4><<<nb, 256, smem, st>>>(d, b0, prev_b0); break;
-        case 8: k_sk_inblock<8><<<nb, 256, smem, st>>>(d, b0, prev_b0); break;
-        case 16: k_sk_inblock<16><<<nb, 256, smem, st>>>(d, b0, prev_b0); break;
+        case 2: kern = k_sk_inblock<2>; break;
+        case 4: kern = k_sk_inblock<4>; break;
+        case 8: kern = k_sk_inblock<8>; break;
+        case 16: kern = k_sk_inblock<16>; break;
         default: return -1;
     }
-    return 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nb);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = (size_t)32 * nc * (2 * nc + 1) * 4;
+    cfg.stream = st;
+    // directly after the previous block's in-block kernel: programmatic dependent launch, so
+    // the launch and the prologue overlap that kernel
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = after_inblock ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, d, b0, prev_b0) == cudaSuccess ? 1 : -1;
 }
 
 int sk_inblock_prepare() {

@@ -93,6 +93,17 @@ def test_zero_and_infinite_temperature(T):
     check(J, temps, 3, 10, tw, tm, got)
 
 
+def test_autotuned_block_with_512_padding():
+    """n >= 2048 with block = 0: n is padded to a multiple of 512 and the autotuner may pick
+    B = 512 (the ragged last block holds padding spins that never flip)."""
+    n, R = 2100, 32
+    J = sg_inputs.sk_couplings(n, 77)
+    temps = [0.4] * (R // 2) + [0.8] * (R // 2)
+    tw, tm = sg_inputs.log_schedule([0, 2], 10)
+    got = run_sk(J, temps, 6, sg.SG_SK_BLOCKED, 0, 10, tw, tm)
+    check(J, temps, 6, 10, tw, tm, got)
+
+
 def test_thresholds_exported_match_oracle():
     n = 512
     J = sg_inputs.sk_couplings(n, 1)
