@@ -71,6 +71,36 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, uint32_
     return false;
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// try_wait with a suspend-time hint: an incomplete phase suspends the thread in hardware until
+// the phase completes or about hint_ns pass, instead of spinning on the issue slots
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t phase, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(phase), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
+// wait bounded in time: false if the phase did not complete within budget_ns (global timer)
+__device__ __forceinline__ bool mbar_wait_timed(uint64_t* bar, uint32_t phase, uint64_t budget_ns) {
+    if (mbar_try_wait(bar, phase)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait_sleep(bar, phase, 1000000u)) return true;
+        if (global_ns() - t0 > budget_ns) return false;
+    }
+}
+
 // 1-D bulk copy global -> shared (TMA engine), completion counted on an mbarrier in bytes.
 // Both addresses must be 16-byte aligned and bytes a multiple of 16.
 __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,

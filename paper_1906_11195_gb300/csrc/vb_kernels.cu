@@ -276,7 +276,7 @@ __device__ __forceinline__ void count_and_flip_narrow(SpinWords<R>& si, const ui
     }
 }
 
-constexpr uint32_t kStagePolls = 1u << 24;
+constexpr uint64_t kStageWaitNs = 2000000000ull;  // 2 s: a stage is late only if something broke
 
 template <int R>
 __device__ __forceinline__ void gather_async(uint64_t* dst, const uint64_t* src, uint64_t pol) {
@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(32 * (kGroupSlices + 1))
                 }
                 const int s = (int)(k % NSS);
                 if (k >= (uint32_t)NSS &&
-                    !mbar_wait(&empty[s], ((k / NSS) - 1) & 1u, kStagePolls)) {
+                    !mbar_wait_timed(&empty[s], ((k / NSS) - 1) & 1u, kStageWaitNs)) {
                     atomicOr(d.err, 4);
                     break;
                 }
@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(32 * (kGroupSlices + 1))
             // no copy may still be landing in shared memory when the CTA exits (the consumers
             // wait for every stage they use; this matters only after a timeout)
             for (uint32_t k = issued > (uint32_t)NSS ? issued - NSS : 0u; k < issued; ++k)
-                if (!mbar_wait(&full[k % NSS], (k / NSS) & 1u, kStagePolls)) atomicOr(d.err, 4);
+                if (!mbar_wait_timed(&full[k % NSS], (k / NSS) & 1u, kStageWaitNs)) atomicOr(d.err, 4);
         }
         return;
     }
@@ -520,8 +520,8 @@ __global__ void __launch_bounds__(32 * (kGroupSlices + 1))
     auto gathers = [&](uint32_t k, uint32_t k_end) -> bool {
         if (k < k_end) {
             const int s = (int)(k % NSS), b = (int)(k % NG);
-            if (!mbar_wait(&full[s], (k / NSS) & 1u, kStagePolls)) return false;
-            if (k >= (uint32_t)NG && !mbar_wait(&gfree[b], ((k / NG) - 1) & 1u, kStagePolls))
+            if (!mbar_wait_timed(&full[s], (k / NSS) & 1u, kStageWaitNs)) return false;
+            if (k >= (uint32_t)NG && !mbar_wait_timed(&gfree[b], ((k / NG) - 1) & 1u, kStageWaitNs))
                 return false;
             const uint4 gi = stream[s].gi;
             const uint32_t nsl = gi.y & ~kWideGroup;
@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(32 * (kGroupSlices + 1))
     bool ok = true;
     int kmin_next[R];
     if (n_mine) {
-        ok = __all_sync(0xFFFFFFFFu, mbar_wait(&full[0], 0u, kStagePolls));
+        ok = __all_sync(0xFFFFFFFFu, mbar_wait_timed(&full[0], 0u, kStageWaitNs));
         if (ok) acceptance<R>(stream[0], warp, lane, t, kmin_next);
     }
     for (uint32_t j = 0; j < nc; ++j) {
@@ -564,8 +564,8 @@ __global__ void __launch_bounds__(32 * (kGroupSlices + 1))
             if (k + 1 < n_mine) {
                 const uint32_t kn = k + 1;
                 if (kn >= ke)
-                    ok = __all_sync(0xFFFFFFFFu, mbar_wait(&full[kn % NSS], (kn / NSS) & 1u,
-                                                           kStagePolls));
+                    ok = __all_sync(0xFFFFFFFFu, mbar_wait_timed(&full[kn % NSS], (kn / NSS) & 1u,
+                                                           kStageWaitNs));
                 if (ok) acceptance<R>(stream[kn % NSS], warp, lane, t, kmin_next);
             }
             asm volatile("cp.async.wait_group %0;" ::"n"(L) : "memory");
