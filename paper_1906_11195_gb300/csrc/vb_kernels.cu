@@ -293,6 +293,17 @@ __device__ __forceinline__ void gather_async(uint64_t* dst, const uint64_t* src,
     }
 }
 
+// the W neighbour gathers of one lane of a narrow slice: slots first, then the copies
+template <int R, int W>
+__device__ __forceinline__ void gather_n(uint64_t* gath, const uint32_t* col, uint32_t loc,
+                                         const uint64_t* S, uint64_t pol) {
+    uint32_t j[W];
+#pragma unroll
+    for (int e = 0; e < W; ++e) j[e] = col[loc + 32 * e];
+#pragma unroll
+    for (int e = 0; e < W; ++e) gather_async<R>(&gath[(loc + 32 * e) * R], S + (int64_t)j[e] * R, pol);
+}
+
 // Acceptance constants of one vertex (all replicas): one Philox block per (vertex, sweep) serves
 // replicas 0..3; the accepted m form a prefix 1..m*, so a lane flips iff its unsatisfied count u
 // reaches kmin = ceil((d - m*) / 2).  Independent of the neighbours, so a consumer warp computes
@@ -306,11 +317,19 @@ __device__ __forceinline__ void acceptance(const VbStream<R>& st, uint32_t warp,
     const uint64_t seed = st.seed[0];
     const uint4 rnd =
         philox4x32_10(make_uint4(orig, t, 0u, 0u), (uint32_t)seed, (uint32_t)(seed >> 32));
+    // thr is non-increasing, so most draws stop at m = 1: read that entry for every replica
+    // at once, and walk on only where it is accepted
+    uint32_t t1[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) t1[r] = st.thr[r * kVbThrStride + 1];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const uint32_t r32 = uint4_word(rnd, r);
         int ms = 0;
-        while (ms < deg && r32 < st.thr[r * kVbThrStride + ms + 1]) ++ms;
+        if (deg > 0 && r32 < t1[r]) {
+            ms = 1;
+            while (ms < deg && r32 < st.thr[r * kVbThrStride + ms + 1]) ++ms;
+        }
         kmin[r] = (deg - ms + 1) >> 1;
     }
 }
@@ -528,10 +547,21 @@ __global__ void __launch_bounds__(32 * (kGroupSlices + 1))
             if (warp < nsl && !(gi.y & kWideGroup) &&
                 stream[s].vinfo[warp * 32 + lane] != kInactive) {
                 const uint4 m = stream[s].meta[warp];
-                uint32_t loc = m.x - gi.z + lane;
-                for (uint32_t e = 0; e < m.y; ++e, loc += 32)
-                    gather_async<R>(&gath[b].v[loc * R], S + (int64_t)stream[s].col[loc] * R,
-                                    pol_keep);
+                const uint32_t loc = m.x - gi.z + lane;
+                switch (m.y) {  // narrow slices: every slot read before the first copy is issued
+                    case 1: gather_n<R, 1>(gath[b].v, stream[s].col, loc, S, pol_keep); break;
+                    case 2: gather_n<R, 2>(gath[b].v, stream[s].col, loc, S, pol_keep); break;
+                    case 3: gather_n<R, 3>(gath[b].v, stream[s].col, loc, S, pol_keep); break;
+                    case 4: gather_n<R, 4>(gath[b].v, stream[s].col, loc, S, pol_keep); break;
+                    case 5: gather_n<R, 5>(gath[b].v, stream[s].col, loc, S, pol_keep); break;
+                    case 6: gather_n<R, 6>(gath[b].v, stream[s].col, loc, S, pol_keep); break;
+                    case 7: gather_n<R, 7>(gath[b].v, stream[s].col, loc, S, pol_keep); break;
+                    case 8: gather_n<R, 8>(gath[b].v, stream[s].col, loc, S, pol_keep); break;
+                    default:
+                        for (uint32_t e = 0, l = loc; e < m.y; ++e, l += 32)
+                            gather_async<R>(&gath[b].v[l * R], S + (int64_t)stream[s].col[l] * R,
+                                            pol_keep);
+                }
             }
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
