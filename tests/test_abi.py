@@ -111,3 +111,46 @@ def test_sk_create_and_validation_without_gpu(lib):
         with pytest.raises(sg.SGError) as e:
             sg.sg_create_sk(args[0], args[1], [0.4] * args[1], 1, args[2], args[3], [], [])
         assert e.value.code == sg.SG_EINVAL
+
+
+def test_size_limits_are_rejected_before_any_array_is_read(lib):
+    """n outside [2, SG_VB_MAX_N] (VB) or [2, 32768] (SK), no graphs, too many lanes: SG_EINVAL,
+    decided from the sizes alone (the arrays passed are far too small to be read)."""
+    import ctypes
+    L = sg._load()
+    tiny_i = np.zeros(4, dtype=np.int32)
+    tiny_u = np.zeros(4, dtype=np.uint64)
+    temps = np.ones(2, dtype=np.float64)
+    h = ctypes.c_void_p()
+    for n in (0, 1, (1 << 26), (1 << 26) + 5):
+        g = (sg.sg_vb_graph * 1)()
+        g[0] = sg.sg_vb_graph(n, tiny_i.ctypes.data, tiny_i.ctypes.data, tiny_u.ctypes.data, 1,
+                              temps.ctypes.data)
+        rc = L.sg_create_vb(ctypes.cast(g, ctypes.c_void_p), 1, 64, 2, sg.SG_VB_PACKED, None, 0,
+                            None, 0, ctypes.byref(h))
+        assert rc == sg.SG_EINVAL, n
+    g = (sg.sg_vb_graph * 1)()
+    g[0] = sg.sg_vb_graph(2, tiny_i.ctypes.data, tiny_i.ctypes.data, tiny_u.ctypes.data, 1,
+                          temps.ctypes.data)
+    for n_graphs, lanes in ((0, 64), (1, 0), (1, 65)):
+        rc = L.sg_create_vb(ctypes.cast(g, ctypes.c_void_p), n_graphs, lanes, 2, sg.SG_VB_PACKED,
+                            None, 0, None, 0, ctypes.byref(h))
+        assert rc == sg.SG_EINVAL, (n_graphs, lanes)
+    tiny_j = np.zeros(4, dtype=np.int8)
+    for n in (0, 1, 32769):
+        rc = L.sg_create_sk(n, tiny_j.ctypes.data, 16, temps.ctypes.data, 1, sg.SG_SK_BLOCKED, 128,
+                            None, 0, None, 0, ctypes.byref(h))
+        assert rc == sg.SG_EINVAL, n
+    assert sg.sg_last_error()
+
+
+def test_edgeless_graph_is_accepted(lib):
+    """A graph with no edges at all (every vertex isolated) is a valid, degenerate instance."""
+    n = 1000
+    rp = np.zeros(n + 1, dtype=np.int32)
+    g = dict(row_ptr=rp, col=np.zeros(0, dtype=np.int32), jbits=np.zeros(0, dtype=np.uint64),
+             seed=3, temps=[1.0, 0.5])
+    for kernel in (sg.SG_VB_PLAIN, sg.SG_VB_PACKED):
+        h = sg.sg_create_vb([g], 64, 2, kernel, [0], [0, 1, 2])
+        assert sg.sg_workspace_bytes(h) > 0
+        sg.sg_destroy(h)

@@ -152,6 +152,26 @@ def test_packed_isolated_vertices_and_max_degree():
     assert_matches_oracle(g, 64, 2, sg.SG_VB_PACKED, 40, tw, tm, spins, C, q, E)
 
 
+@pytest.mark.parametrize("kernel", ["plain", "packed"])
+def test_edgeless_graph_flips_every_spin_every_sweep(kernel):
+    """No edges: dE = 0 for every move, so every lane flips every sweep.  Closed form:
+    C(t_w, t_w + t) = (-1)^t N, E = 0, q constant; and the oracle's trajectory."""
+    n, L = 1000, 64
+    g = dict(row_ptr=np.zeros(n + 1, dtype=np.int32), col=np.zeros(0, dtype=np.int32),
+             jbits=np.zeros(0, dtype=np.uint64), seed=3, temps=[1.0, 0.5])
+    tw, tm = sg_inputs.log_schedule([0, 1, 2], 9)
+    k = sg.SG_VB_PLAIN if kernel == "plain" else sg.SG_VB_PACKED
+    lanes = 8 if kernel == "plain" else L
+    spins, C, q, E, _ = run_gpu([g], lanes, 2, k, 9, tw, tm)
+    assert_matches_oracle(g, lanes, 2, k, 9, tw, tm, spins, C, q, E)
+    for a, t_w in enumerate(tw):
+        for b, t_m in enumerate(tm):
+            if t_m >= t_w:
+                assert np.all(C[0][:, :lanes, a, b] == (-1) ** int(t_m - t_w) * n)
+    assert np.all(E[0][:, :lanes] == 0)
+    assert np.all(q[0][:, :lanes] == q[0][:, :lanes, :1])
+
+
 @pytest.mark.parametrize("T", [0.0, math.inf])
 def test_packed_zero_and_infinite_temperature(T):
     g = vb_instance(3000, 4.0, 7, [T, T], 12)
