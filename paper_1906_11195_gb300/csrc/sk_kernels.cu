@@ -110,6 +110,7 @@ int sk_kstar_sweep(const SkDev& d, const uint32_t* clock, uint32_t t_off, cudaSt
 // --------------------------------------------------------------------------------------------
 template <int NC>
 __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0, int prev_b0) {
+    static_assert(NC == 2 || NC == 4 || NC == 8 || NC == 16, "B = 64, 128, 256 or 512");
     // [32 * NC rows][2 * NC words + 1]: own cols, previous cols; the odd row stride keeps the
     // 32 lanes (32 consecutive rows) on 32 different banks
     extern __shared__ uint32_t jblk[];
@@ -131,8 +132,10 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0, int prev_b0
     for (int c = 0; c < NC; ++c) kst[c] = active ? d.kst[(int64_t)r * d.Np + b0 + 32 * c + lane] : 0;
     // the block's coupling bits (own columns, previous block's columns) land in shared memory
     // through asynchronous copies, all in flight together
+    // nw is NC or 2 NC, a power of two: row and word by shift and mask
+    const int nw_log = (prev_b0 >= 0 ? 1 : 0) + (NC == 2 ? 1 : NC == 4 ? 2 : NC == 8 ? 3 : 4);
     for (int k = threadIdx.x; k < 32 * NC * nw; k += blockDim.x) {
-        const int row = k / nw, w = k % nw;
+        const int row = k >> nw_log, w = k & (nw - 1);
         const int col_word = w < NC ? wb + w : pwb + (w - NC);
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(&jblk[row * W + w])),
                      "l"(d.Jbits + (int64_t)(b0 + row) * words + col_word)
