@@ -436,6 +436,170 @@ def run_sk_batch(args):
     return 0
 
 
+def run_gpu(args):
+    import torch
+
+    import paper_1906_11195_gb300 as sg
+    from paper_1906_11195_gb300 import _build
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        _build.build()
+    if ws > 1:
+        dist.barrier()
+    _build.build()
+
+    rp, col, jb = instance(rank)
+    tw, tm = sg_inputs.log_schedule(TW, T_MAX)
+    graphs = [dict(row_ptr=rp, col=col, jbits=jb, seed=1 + rank, temps=[T] * REPLICAS) for T in TEMPS]
+    stream = torch.cuda.current_stream(dev)
+
+    runs = [sg.VBRun([g], n_lanes=LANES, n_replicas=REPLICAS, kernel=sg.SG_VB_PACKED, tw=tw, tm=tm,
+                     device=dev, stream=stream) for g in graphs]
+    for r in runs:
+        r.sweep(args.warmup)
+    torch.cuda.synchronize()
+    launches0 = sum(r.launches for r in runs)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nvtx_push("timed_region")  # lets a profiler capture exactly the timed launches
+    ev0.record(stream)
+    for r in runs:
+        r.sweep(args.steps)
+    ev1.record(stream)
+    nvtx_pop()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    launches = sum(r.launches for r in runs) - launches0
+    for r in runs:
+        r.synchronize()
+    ms = max_over_ranks(ms, dev)
+    updates_per_step = len(TEMPS) * N_VERTS * LANES * REPLICAS
+    value = job_value(updates_per_step, args.steps, ws, ms)
+    for r in runs:
+        r.close()
+
+    # roofline of the colour kernel: a handle with no measurement schedule times pure sweeps
+    kr = max(20, min(args.steps, 200))
+    rl = sg.VBRun([graphs[0]], n_lanes=LANES, n_replicas=REPLICAS, kernel=sg.SG_VB_PACKED,
+                  device=dev, stream=stream)
+    rl.sweep(3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rl.sweep(kr)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sweep_ms = e0.elapsed_time(e1) / kr
+    rl.close()
+    bytes_sweep = algorithmic_bytes_per_sweep(N_VERTS, int(rp[-1]), REPLICAS)
+    peak, peak_kind = peaks()
+    # achieved: the colour kernel's algorithmic bytes of every sweep in the timed region over the
+    # whole timed region (the few snapshot/measurement launches in it count against the kernel,
+    # so this is a lower bound); achieved_isolated: the same over sweeps timed alone
+    sweep_ms_timed = ms / (args.steps * len(TEMPS))
+    achieved = bytes_sweep / (sweep_ms_timed * 1e-3) / 1e9
+    traffic = recorded_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                "kernel": "k_vb_packed_colour<2>, one unit = one sweep (all colour classes)",
+                "algorithmic_bytes_per_sweep": bytes_sweep, "ms_per_sweep": sweep_ms_timed,
+                "achieved_isolated": bytes_sweep / (sweep_ms * 1e-3) / 1e9,
+                "ms_per_sweep_isolated": sweep_ms}
+
+    # the plain one-thread-per-(vertex, lane, replica) kernel on the same graph, T = 1.0
+    plain = None
+    if not args.skip_plain:
+        pr = sg.VBRun([graphs[0]], n_lanes=LANES, n_replicas=REPLICAS, kernel=sg.SG_VB_PLAIN,
+                      device=dev, stream=stream)
+        pr.sweep(1)
+        torch.cuda.synchronize()
+        kp = 3
+        e0.record(stream)
+        pr.sweep(kp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / kp
+        pr.close()
+        plain = {"value": N_VERTS * LANES * REPLICAS / (pms * 1e6), "unit": "spin updates/ns",
+                 "ms_per_sweep": pms, "sweeps": kp}
+
+    # end to end through the public API: H2D of the prepared instances, K sweeps each, D2H of
+    # the measurement counts; host-side instance preparation (validation, colouring, layout)
+    # happens before the timed region
+    handles, bufs = [], []
+    for g in graphs:
+        h = sg.sg_create_vb([g], LANES, REPLICAS, sg.SG_VB_PACKED, tw, tm)
+        nb = sg.sg_workspace_bytes(h)
+        handles.append((h, nb))
+        bufs.append(torch.empty(nb, dtype=torch.uint8, device=dev))
+    h2d = sum(nb for _, nb in handles)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for (h, nb), buf in zip(handles, bufs):
+        sg.sg_attach(h, buf.data_ptr(), nb, stream.cuda_stream)
+    for h, _ in handles:
+        sg.sg_sweep(h, args.warmup + args.steps)
+    d2h = 0
+    for h, _ in handles:
+        C, q, E = sg.sg_read_results(h)
+        d2h += C.nbytes + q.nbytes + E.nbytes
+    e2e_s = time.perf_counter() - t0
+    for h, _ in handles:
+        sg.sg_destroy(h)
+    e2e_steps = args.warmup + args.steps
+    e2e = {"value": ws * updates_per_step * e2e_steps / (e2e_s * 1e9), "unit": "spin updates/ns",
+           "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
+           "note": "H2D of the device image of both instances + sweeps + D2H of all counts, "
+                   "bytes spread over the steps"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        cpu = cpu_baseline_sample(rp, col, jb)
+
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "spin updates/ns", "value": value, "unit": "spin updates/ns", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N_VERTS, "mean_degree": MEAN_DEGREE, "lanes": LANES,
+                   "replicas": REPLICAS, "temps": list(TEMPS), "step": "1 sweep of each temperature",
+                   "schedule": f"tw=2^4..2^15, log-spaced measurements to 2^16 ({len(tm)} times)",
+                   "l2": "inputs larger than L2: 201 MB of graph streamed per sweep (spins, 64 MiB, "
+                         "are meant to stay in L2)",
+                   "parallelism": f"replicas only, {ws} independent instance(s)"},
+        "roofline": roofline,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "plain_kernel": plain,
+        "speedup_vs_plain": (value / ws) / plain["value"] if plain else None,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
