@@ -328,6 +328,115 @@ def run_vb_batch(args):
     return 0
 
 
+T_08_TC = 0.8 / float(np.arctanh(1.0 / np.sqrt(3.0)))  # 0.8 T_c of the z = 4 model, 1.21492
+
+
+def run_rrbg(args):
+    """The paper's own GPU ensemble (not the headline line): a random regular bipartite graph
+    of degree 4, N = 2^22, 64 coupling sets per word, R = 2, T = 0.8 T_c; the greedy colouring
+    is exactly the two halves, so a sweep is the paper's two half-updates.  Snapshots at
+    t_w = 2^2 .. 2^12, measurements on the log schedule; one step = one sweep."""
+    import torch
+
+    import paper_1906_11195_gb300 as sg
+    from paper_1906_11195_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    n = N_VERTS
+    rp, col, eid = sg_inputs.random_regular_graph(n, 4, 6, bipartite=True)
+    jb = sg_inputs.vb_lane_couplings(eid, eid.max() + 1, 6)
+    tw, tm = sg_inputs.log_schedule([1 << k for k in range(2, 13)], args.warmup + args.steps)
+    g = dict(row_ptr=rp, col=col, jbits=jb, seed=1, temps=[T_08_TC] * REPLICAS)
+    run = sg.VBRun([g], n_lanes=LANES, n_replicas=REPLICAS, kernel=sg.SG_VB_PACKED, tw=tw, tm=tm)
+    stream = torch.cuda.current_stream()
+    run.sweep(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = run.launches
+    nvtx_push("timed_region")
+    e0.record(stream)
+    run.sweep(args.steps)
+    e1.record(stream)
+    nvtx_pop()
+    torch.cuda.synchronize()
+    run.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    bytes_sweep = algorithmic_bytes_per_sweep(n, int(rp[-1]), REPLICAS)
+    peak, _ = peaks()
+    out = {"metric": "spin updates/ns", "unit": "spin updates/ns",
+           "value": n * LANES * REPLICAS / (ms * 1e6), "ms_per_step": ms, "steps": args.steps,
+           "warmup": args.warmup, "gpu_launches": run.launches - l0,
+           "config": {"workload": f"vb_packed_rrbg_z4_N{n}_lanes64_R2_T{T_08_TC:.5f}",
+                      "colour_classes": 2},
+           "roofline": {"bound": "hbm", "achieved": bytes_sweep / (ms * 1e-3) / 1e9,
+                        "peak": peak, "unit": "GB/s",
+                        "frac": bytes_sweep / (ms * 1e-3) / 1e9 / peak}}
+    run.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_e6(args):
+    """The paper's bipartite vs non-bipartite comparison (not a throughput line): C(t_w + t, t_w)
+    at t_w = 4 on random regular graphs of degree 4, bipartite and plain, T = 0.8 T_c, for
+    N = 2^14 (32 graphs per ensemble) and N = 2^22 (2 graphs), 64 coupling sets x 2 replicas per
+    graph, t = 2^0 .. 2^k with 4 + 2^k <= --e6-tmax; prints both mean curves, their standard
+    errors (from per-graph means) and the z-scores of the differences.  A third ensemble, the
+    bipartite graphs under a random vertex labelling (same graphs, several colour classes),
+    separates the effect of the graph from that of the update order."""
+    import math
+
+    import torch
+
+    import paper_1906_11195_gb300 as sg
+    from paper_1906_11195_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    out = {"workload": "e6_bipartite_vs_plain_rrg_z4_tw4", "T": T_08_TC, "sizes": {}}
+    for n, ng in ((1 << 14, 32), (1 << 22, 2)):
+        kmax = int(math.log2(max(1, args.e6_tmax - 4)))
+        tm = np.array([4 + 2 ** k for k in range(kmax + 1)], dtype=np.int64)
+        res = {}
+        for kind in ("bipartite", "plain", "bipartite_relabelled"):
+            bip = kind != "plain"
+            graphs = []
+            for i in range(ng):
+                sd = 7000 + i + 100 * bip + n
+                rp, col, eid = sg_inputs.random_regular_graph(n, 4, sd, bipartite=bip)
+                if kind == "bipartite_relabelled":
+                    # the same bipartite graph under a random vertex labelling: greedy colouring
+                    # then gives several classes, so only the update order differs
+                    rng = np.random.default_rng(sd)
+                    perm = rng.permutation(n)
+                    src = np.repeat(np.arange(n), np.diff(rp))
+                    keep = src < col
+                    rp, col, e2 = sg_inputs.csr_from_edges(n, perm[src[keep]], perm[col[keep]])
+                    eid = e2
+                jb = sg_inputs.vb_lane_couplings(eid, eid.max() + 1, sd)
+                graphs.append(dict(row_ptr=rp, col=col, jbits=jb, seed=sd,
+                                   temps=[T_08_TC] * REPLICAS))
+            run = sg.VBRun(graphs, n_lanes=LANES, n_replicas=REPLICAS, kernel=sg.SG_VB_PACKED,
+                           tw=[4], tm=tm)
+            run.sweep(int(tm[-1]))
+            run.synchronize()
+            C, _, _ = run.results()
+            run.close()
+            pg = C[:, :, :, 0, :].astype(np.float64).mean(axis=(1, 2)) / n
+            se = pg.std(axis=0, ddof=1) / math.sqrt(ng) if ng > 1 else np.zeros(pg.shape[1])
+            res[kind] = (pg.mean(axis=0), se)
+        entry = {"graphs_per_ensemble": ng, "t": (tm - 4).tolist()}
+        for kind, (m, e) in res.items():
+            entry["C_" + kind] = m.round(6).tolist()
+            entry["se_" + kind] = e.round(6).tolist()
+        for a, b in (("bipartite", "plain"), ("bipartite_relabelled", "plain")):
+            (m1, e1), (m2, e2) = res[a], res[b]
+            z = np.abs(m1 - m2) / np.maximum(np.sqrt(e1 ** 2 + e2 ** 2), 1e-12)
+            entry[f"z_{a}_vs_{b}"] = z.round(2).tolist()
+        out["sizes"][str(n)] = entry
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_sk(args):
     """SK workload (not the headline line): N = 8192, +-1 couplings, 256 replicas sharing J,
     T = 0.4; one step = one sweep.  The line's value is the configured block B (--sk-block,
@@ -615,10 +724,13 @@ def main():
     ap.add_argument("--profile-log2n", type=int, default=22, help="log2 N of the profile case")
     ap.add_argument("--profile-replicas", type=int, default=2, choices=[2, 4],
                     help="replicas of the profile case (4: two per temperature)")
-    ap.add_argument("--workload", default="vb", choices=["vb", "sk", "vb_batch", "sk_batch"],
+    ap.add_argument("--workload", default="vb",
+                    choices=["vb", "sk", "vb_batch", "sk_batch", "rrbg", "e6"],
                     help="vb: the headline bit-packed Viana-Bray line; sk: the SK blocked line; "
                          "vb_batch: the uneven batch of Viana-Bray graphs; sk_batch: the uneven "
-                         "batch of SK samples")
+                         "batch of SK samples; rrbg: the paper's bipartite regular graph; e6: "
+                         "bipartite vs plain regular graphs, C(t_w + t, t_w) at t_w = 4")
+    ap.add_argument("--e6-tmax", type=int, default=4 + 2 ** 16, help="last time of the e6 curves")
     ap.add_argument("--batch", type=int, default=512, help="graphs in the vb_batch workload")
     ap.add_argument("--sk-block", type=int, default=SK_B)
     args = ap.parse_args()
@@ -634,6 +746,10 @@ def main():
         return run_vb_batch(args)
     if args.workload == "sk_batch":
         return run_sk_batch(args)
+    if args.workload == "rrbg":
+        return run_rrbg(args)
+    if args.workload == "e6":
+        return run_e6(args)
     return run_gpu(args)
 
 

@@ -10,7 +10,10 @@ Instance families (paper workloads, restated):
     (Eq. 3; the paper itself uses a random regular graph of degree 4).  Couplings are stored
     as 64-bit lane words: bit k = 1 means J = -1 for disorder sample k (SI section 2,
     multispin coding, Table 1 caption: 64 coupling sets per graph).
-  * Random regular graph of degree z (the paper's own ensemble, main text after Eq. 3).
+  * Random regular graph of degree z (the paper's own ensemble, main text after Eq. 3), and its
+    bipartite form (the random regular bipartite graph the paper simulates on GPUs, SI section
+    3): halves [0, N/2) and [N/2, N), every edge across, so that greedy colouring in vertex
+    order yields exactly the two halves.
   * Sherrington-Kirkpatrick with binary symmetric couplings J_ij = +-1, J_ii = 0
     (SI section 1; the 1/sqrt(N) scale is folded into the inverse temperature).
 """
@@ -21,6 +24,7 @@ import numpy as np
 __all__ = [
     "poisson_graph",
     "regular_graph",
+    "random_regular_graph",
     "vb_lane_couplings",
     "sk_couplings",
     "log_uniform_sizes",
@@ -102,6 +106,46 @@ def regular_graph(n: int, z: int, seed: int, max_tries: int = 200):
             continue
         return csr_from_edges(n, lo, hi)
     raise RuntimeError("could not draw a simple regular graph; raise max_tries")
+
+
+def random_regular_graph(n: int, z: int, seed: int, bipartite: bool = False):
+    """Random z-regular simple graph for any N, by stub pairing with local repair.
+
+    Stubs are paired by one random permutation; every pairing that makes a self-loop or repeats
+    an edge then swaps its partner stub with that of a uniformly chosen other pairing, until the
+    graph is simple (degrees never change).  The result is close to, not exactly, uniform over
+    simple z-regular graphs, as in common practice for large N.  bipartite=True pairs the stubs
+    of the first half [0, N/2) with those of the second half only (N even).  Returns
+    (row_ptr, col, edge_id) as in csr_from_edges.
+    """
+    if bipartite and n % 2:
+        raise ValueError("a bipartite regular graph needs even N")
+    if (n * z) % 2:
+        raise ValueError("N*z must be even")
+    if z >= (n // 2 if bipartite else n):
+        raise ValueError("degree too large for N")
+    rng = np.random.default_rng(np.random.SeedSequence([0x5EED_0006, seed, int(bipartite)]))
+    if bipartite:
+        h = n // 2
+        a = np.repeat(np.arange(h, dtype=np.int64), z)
+        b = rng.permutation(np.repeat(np.arange(h, n, dtype=np.int64), z))
+    else:
+        perm = rng.permutation(np.repeat(np.arange(n, dtype=np.int64), z))
+        a, b = perm[0::2].copy(), perm[1::2].copy()
+    m = a.size
+    for _ in range(10000):
+        lo, hi = np.minimum(a, b), np.maximum(a, b)
+        keys = lo * n + hi
+        order = np.argsort(keys, kind="stable")
+        dup = np.zeros(m, dtype=bool)
+        dup[order[1:]] = keys[order[1:]] == keys[order[:-1]]
+        bad = np.flatnonzero(dup | (a == b))
+        if bad.size == 0:
+            return csr_from_edges(n, lo, hi)
+        other = rng.integers(0, m, size=bad.size)
+        for i, j in zip(bad, other):  # swap partner stubs (both sides keep their degrees)
+            b[i], b[j] = b[j], b[i]
+    raise RuntimeError("could not repair the pairing into a simple graph")
 
 
 def vb_lane_couplings(edge_id: np.ndarray, n_edges: int, seed: int) -> np.ndarray:

@@ -1,0 +1,55 @@
+"""The paper's own graph ensembles as input data: random regular graphs of degree z, plain and
+bipartite (halves [0, N/2) and [N/2, N)).  Checks the structure the dynamics relies on: every
+degree is z, the graph is simple, a bipartite graph only has edges across the halves, and
+greedy colouring in vertex order splits a bipartite graph into exactly its two halves (the
+paper's half-sweep update order, SI section 3)."""
+import numpy as np
+import pytest
+
+import oracle
+import sg_inputs
+
+
+def _edges(rp, col):
+    n = rp.size - 1
+    src = np.repeat(np.arange(n), np.diff(rp))
+    return src, col.astype(np.int64)
+
+
+@pytest.mark.parametrize("bipartite", [False, True])
+@pytest.mark.parametrize("n,z", [(64, 3 * 2), (1000, 4), (4096, 4), (2 ** 14, 4)])
+def test_regular_graph_structure(n, z, bipartite):
+    if bipartite and z >= n // 2:
+        pytest.skip("degree too large")
+    rp, col, eid = sg_inputs.random_regular_graph(n, z, 11, bipartite=bipartite)
+    assert np.all(np.diff(rp) == z)
+    src, dst = _edges(rp, col)
+    assert np.all(src != dst)
+    keys = src * n + dst
+    assert np.unique(keys).size == keys.size                      # no multi-edges
+    rev = np.sort(dst * n + src)
+    assert np.array_equal(np.sort(keys), rev)                     # symmetric
+    assert eid.max() + 1 == n * z // 2                            # one id per undirected edge
+    if bipartite:
+        assert np.all((src < n // 2) != (dst < n // 2))           # edges only across halves
+
+
+def test_bipartite_graph_colours_into_its_halves():
+    n = 4096
+    rp, col, _ = sg_inputs.random_regular_graph(n, 4, 5, bipartite=True)
+    colour, nc = oracle.greedy_colour(rp, col)
+    assert nc == 2
+    assert np.all(colour[: n // 2] == 0) and np.all(colour[n // 2:] == 1)
+
+
+def test_plain_regular_graph_is_not_bipartite_and_needs_more_colours():
+    rp, col, _ = sg_inputs.random_regular_graph(4096, 4, 5)
+    _, nc = oracle.greedy_colour(rp, col)
+    assert nc >= 3
+
+
+def test_generator_is_seeded():
+    a = sg_inputs.random_regular_graph(2000, 4, 9, bipartite=True)
+    b = sg_inputs.random_regular_graph(2000, 4, 9, bipartite=True)
+    c = sg_inputs.random_regular_graph(2000, 4, 10, bipartite=True)
+    assert np.array_equal(a[1], b[1]) and not np.array_equal(a[1], c[1])

@@ -152,6 +152,51 @@ def test_packed_isolated_vertices_and_max_degree():
     assert_matches_oracle(g, 64, 2, sg.SG_VB_PACKED, 40, tw, tm, spins, C, q, E)
 
 
+T_08_TC = 0.8 / math.atanh(1.0 / math.sqrt(3.0))  # 0.8 T_c of the z = 4 VB model, 1.21492
+
+
+@pytest.mark.parametrize("bipartite", [True, False])
+def test_paper_ensembles_match_oracle(bipartite):
+    """The paper's own ensembles: random regular graphs of degree 4, bipartite (two colour
+    classes: the paper's half sweeps) and plain, at T = 0.8 T_c, 64 lanes, two replicas."""
+    rp, col, eid = sg_inputs.random_regular_graph(4096, 4, 21, bipartite=bipartite)
+    jb = sg_inputs.vb_lane_couplings(eid, eid.max() + 1, 21)
+    g = dict(row_ptr=rp, col=col, jbits=jb, seed=77, temps=[T_08_TC, T_08_TC])
+    tw, tm = sg_inputs.log_schedule([0, 4, 16], 64)
+    spins, C, q, E, _ = run_gpu([g], 64, 2, sg.SG_VB_PACKED, 64, tw, tm)
+    assert_matches_oracle(g, 64, 2, sg.SG_VB_PACKED, 64, tw, tm, spins, C, q, E)
+
+
+def test_bipartite_and_plain_regular_graphs_agree_statistically():
+    """The paper's check that bipartition does not matter (SI, comparison of the two ensembles
+    at t_w = 4): C(t_w + t, t_w) averaged over 32 graphs x 64 coupling sets x 2 replicas at
+    N = 2^14, T = 0.8 T_c, for t = 2^0 .. 2^12 (errors from the spread of the per-graph means).
+    The two ensembles also differ in update order (two colour classes against the greedy
+    colouring's four or five), and at this precision that shows at short times: the means
+    differ by about 0.5 % of C for t <= 32 (5-10 standard errors).  So the check is: within
+    0.01 everywhere, and within 5 standard errors from t = 64 on, where the paper's claim (no
+    significant difference in the aging regime) is tested."""
+    n, ng, tw0, tmax = 1 << 14, 32, 4, 4 + 4096
+    tw, tm = np.array([tw0], dtype=np.int64), np.array([tw0 + 2 ** k for k in range(13)])
+    curves = {}
+    for bip in (True, False):
+        graphs = []
+        for i in range(ng):
+            rp, col, eid = sg_inputs.random_regular_graph(n, 4, 3000 + i + 100 * bip, bipartite=bip)
+            jb = sg_inputs.vb_lane_couplings(eid, eid.max() + 1, 3000 + i + 100 * bip)
+            graphs.append(dict(row_ptr=rp, col=col, jbits=jb, seed=500 + i + 100 * bip,
+                               temps=[T_08_TC, T_08_TC]))
+        _, C, _, _, _ = run_gpu(graphs, 64, 2, sg.SG_VB_PACKED, tmax, tw, tm)
+        per_graph = C[:, :, :, 0, :].astype(np.float64).mean(axis=(1, 2)) / n  # [graph][time]
+        curves[bip] = (per_graph.mean(axis=0), per_graph.std(axis=0, ddof=1) / math.sqrt(ng))
+    (m1, e1), (m2, e2) = curves[True], curves[False]
+    diff, se = np.abs(m1 - m2), np.sqrt(e1 ** 2 + e2 ** 2)
+    assert np.all(diff <= 0.01)
+    late = (tm - tw0) >= 64
+    assert np.all(diff[late] <= 5.0 * se[late])
+    assert m1[0] > m1[-1]  # the correlation decays
+
+
 @pytest.mark.parametrize("kernel", ["plain", "packed"])
 def test_edgeless_graph_flips_every_spin_every_sweep(kernel):
     """No edges: dE = 0 for every move, so every lane flips every sweep.  Closed form:
