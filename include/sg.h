@@ -167,6 +167,24 @@ int sg_result_shape(sg_handle h, int32_t *shape5);
 int sg_read_results(sg_handle h, int64_t *C, size_t C_len, int64_t *q, size_t q_len,
                     int64_t *E, size_t E_len);
 
+/* Window-averaged measurement (the estimator of the main text, "Extrapolation to large sizes
+ * and large times": each point is the average of the measurements over a geometric window of
+ * times, e.g. [t/2^(1/4), t]; SI section 1 lumps SK data in tritone windows the same way).
+ * bounds[0] < bounds[1] < ... < bounds[n_bounds-1] (int64, host, >= 0, <= 2^32) cut time into
+ * n_bounds-1 windows; window m holds the sweeps tau with bounds[m] <= tau < bounds[m+1].  Every
+ * such tau is measured (after the snapshots due at tau) and its C, q, E are added into window m.
+ * Must be called before sg_attach (the workspace size grows with the window count); otherwise
+ * SG_ESTATE.  Invalid bounds: SG_EINVAL.  The point schedule (tw, tm) is unchanged. */
+int sg_set_windows(sg_handle h, const int64_t *bounds, int32_t n_bounds);
+
+/* Copy the window sums to the host (synchronises).  With n_bins = n_bounds - 1, layouts (int64):
+ *   C[n_inst][R][L][n_tw][n_bins]  sum over measured tau in window m of C(tau, tw)
+ *   q[n_inst][R/2][L][n_bins], E[n_inst][R][L][n_bins]  sums of q(tau), E(tau)
+ *   n_meas[n_tw + 1][n_bins]  rows 0..n_tw-1: the number of taus summed into C for snapshot w
+ *                             (tau >= tw[w], tau <= the current time); last row: for q and E
+ * The window averages are C / n_meas.  SG_ESTATE if no windows were set. */
+int sg_read_windows(sg_handle h, int64_t *C, int64_t *q, int64_t *E, int64_t *n_meas);
+
 /* Measure now, at the current tau, against every snapshot taken so far (synchronises).
  * C[n_inst][R][L][n_tw] (0 for snapshots not yet taken), q[n_inst][R/2][L], E[n_inst][R][L]. */
 int sg_measure(sg_handle h, int64_t *C, size_t C_len, int64_t *q, size_t q_len, int64_t *E,

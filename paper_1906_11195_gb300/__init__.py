@@ -36,7 +36,7 @@ EXPORTED = [
     "sg_attach",
     "sg_sweep", "sg_time", "sg_synchronize", "sg_result_shape", "sg_read_results", "sg_measure",
     "sg_get_spins", "sg_get_thresholds", "sg_state_bytes", "sg_save_state", "sg_load_state",
-    "sg_destroy", "sg_launch_count", "sg_sk_fields_noalloc",
+    "sg_destroy", "sg_launch_count", "sg_sk_fields_noalloc", "sg_set_windows", "sg_read_windows",
 ]
 
 
@@ -96,6 +96,8 @@ def _load():
                 "sg_destroy": (ctypes.c_int, [H]),
                 "sg_launch_count": (ctypes.c_int, [H, P]),
                 "sg_sk_fields_noalloc": (ctypes.c_int, [P, P, i32, i32, P, P]),
+                "sg_set_windows": (ctypes.c_int, [H, P, i32]),
+                "sg_read_windows": (ctypes.c_int, [H, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -225,6 +227,22 @@ def sg_measure(h):
     return C, q, E
 
 
+def sg_set_windows(h, bounds):
+    b = _i64(bounds)
+    _check(_load().sg_set_windows(h, _p(b), int(b.size)))
+
+
+def sg_read_windows(h, n_bins: int):
+    """Window sums C[n_inst][R][L][n_tw][n_bins], q, E and n_meas[n_tw + 1][n_bins]."""
+    n_inst, R, L, ntw, _ = sg_result_shape(h)
+    C = np.zeros((n_inst, R, L, ntw, n_bins), dtype=np.int64)
+    q = np.zeros((n_inst, R // 2, L, n_bins), dtype=np.int64)
+    E = np.zeros((n_inst, R, L, n_bins), dtype=np.int64)
+    n = np.zeros((ntw + 1, n_bins), dtype=np.int64)
+    _check(_load().sg_read_windows(h, _p(C), _p(q), _p(E), _p(n)))
+    return C, q, E, n
+
+
 def sg_get_spins(h, nbytes: int, dtype):
     out = np.zeros(nbytes // np.dtype(dtype).itemsize, dtype=dtype)
     _check(_load().sg_get_spins(h, _p(out), out.nbytes))
@@ -273,13 +291,17 @@ def sg_sk_fields_noalloc(J_dev: int, s_dev: int, n: int, n_replicas: int, h_dev:
 # convenience owners: allocate the workspace with PyTorch and bind the current stream
 # ----------------------------------------------------------------------------------------------
 class _Run:
-    def __init__(self, handle, device=None, stream=None):
+    def __init__(self, handle, device=None, stream=None, windows=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libsg needs a CUDA device")
         self.h = None
         self.device = torch.device(device or "cuda")
+        self.n_bins = 0
         try:
+            if windows is not None:
+                sg_set_windows(handle, windows)
+                self.n_bins = len(windows) - 1
             nbytes = sg_workspace_bytes(handle)
             # 256-byte alignment: PyTorch's caching allocator returns 512-byte aligned blocks
             self.workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=self.device)
@@ -308,6 +330,10 @@ class _Run:
     def measure(self):
         return sg_measure(self.h)
 
+    def windows(self):
+        """Window sums C, q, E and the measurement counts n_meas (see sg_read_windows)."""
+        return sg_read_windows(self.h, self.n_bins)
+
     def save_state(self):
         return sg_save_state(self.h)
 
@@ -335,10 +361,11 @@ class VBRun(_Run):
     """A batch of Viana-Bray graphs (Eq. 3) evolving in lock-step under Metropolis dynamics."""
 
     def __init__(self, graphs, n_lanes=64, n_replicas=2, kernel=SG_VB_PACKED, tw=(), tm=(),
-                 device=None, stream=None):
+                 device=None, stream=None, windows=None):
         self.sizes = [int(np.asarray(g["row_ptr"]).size - 1) for g in graphs]
         self.n_replicas = n_replicas
-        super().__init__(sg_create_vb(graphs, n_lanes, n_replicas, kernel, tw, tm), device, stream)
+        super().__init__(sg_create_vb(graphs, n_lanes, n_replicas, kernel, tw, tm), device, stream,
+                         windows)
 
     def spins(self):
         """uint64 spins per graph: list of [R][n] arrays in the caller's vertex order."""
@@ -359,11 +386,11 @@ class SKBatchRun(_Run):
     """Independent SK samples of uneven size advancing in lock-step (one graph per sweep)."""
 
     def __init__(self, samples, n_replicas, kernel=SG_SK_BLOCKED, block=0, tw=(), tm=(),
-                 device=None, stream=None):
+                 device=None, stream=None, windows=None):
         self.sizes = [int(np.asarray(x["J"]).shape[0]) for x in samples]
         self.n_replicas = n_replicas
         super().__init__(sg_create_sk_batch(samples, n_replicas, kernel, block, tw, tm), device,
-                         stream)
+                         stream, windows)
 
     def spins(self):
         flat = sg_get_spins(self.h, sum(self.sizes) * self.n_replicas, np.int8)
@@ -378,11 +405,11 @@ class SKRun(_Run):
     """A Sherrington-Kirkpatrick sample (Eq. 1, binary couplings) with R replicas sharing J."""
 
     def __init__(self, J, temps, seed, kernel=SG_SK_BLOCKED, block=128, tw=(), tm=(), device=None,
-                 stream=None):
+                 stream=None, windows=None):
         self.n = int(np.asarray(J).shape[0])
         self.n_replicas = len(temps)
         super().__init__(sg_create_sk(J, len(temps), temps, seed, kernel, block, tw, tm), device,
-                         stream)
+                         stream, windows)
 
     def spins(self):
         return sg_get_spins(self.h, self.n * self.n_replicas, np.int8).reshape(self.n_replicas, self.n)

@@ -41,6 +41,7 @@ static const int64_t kMaxGraphNodes = 4096;
 struct sg_ctx {
     std::unique_ptr<sg::Model> model;
     std::vector<int64_t> tw, tm;
+    std::vector<int64_t> wb;  // window bounds (window m: wb[m] <= tau < wb[m+1]); empty: none
     int64_t tau = 0;
     bool attached = false;
     cudaStream_t stream = nullptr;
@@ -165,7 +166,18 @@ static void events_at_tau(sg_handle h) {
         m.measure_scheduled((int)h->next_tm, h->tau, h->stream);
         ++h->next_tm;
     }
+    if (!h->wb.empty() && h->tau >= h->wb.front() && h->tau < h->wb.back()) {
+        const int w = (int)(std::upper_bound(h->wb.begin(), h->wb.end(), h->tau) - h->wb.begin()) - 1;
+        m.measure_window(w, h->tau, h->stream);
+    }
     sg::check_cuda(cudaGetLastError(), "kernel launch");
+}
+
+// the next time after tau at which a window measurement is due (or -1)
+static int64_t next_window_tau(const sg_ctx* h) {
+    if (h->wb.empty()) return -1;
+    const int64_t t = std::max(h->tau + 1, h->wb.front());
+    return t < h->wb.back() ? t : -1;
 }
 
 extern "C" {
@@ -258,11 +270,49 @@ int sg_sweep(sg_handle h, int64_t n) {
             int64_t stop = end;
             if (h->next_tw < h->tw.size()) stop = std::min(stop, h->tw[h->next_tw]);
             if (h->next_tm < h->tm.size()) stop = std::min(stop, h->tm[h->next_tm]);
+            const int64_t tw_next = next_window_tau(h);
+            if (tw_next >= 0) stop = std::min(stop, tw_next);
             run_sweeps(h, h->tau, stop - h->tau);
             sg::check_cuda(cudaGetLastError(), "sweep launch");
             h->tau = stop;
             events_at_tau(h);
         }
+    });
+}
+
+int sg_set_windows(sg_handle h, const int64_t* bounds, int32_t n_bounds) {
+    return guarded([&] {
+        if (!h) sg::fail(SG_EINVAL, "null handle");
+        if (h->attached) sg::fail(SG_ESTATE, "windows must be set before sg_attach");
+        if (!bounds || n_bounds < 2 || n_bounds > (1 << 16))
+            sg::fail(SG_EINVAL, "need 2 .. 65536 window bounds");
+        std::vector<int64_t> b(bounds, bounds + n_bounds);
+        if (b[0] < 0) sg::fail(SG_EINVAL, "window bounds must be >= 0");
+        for (int32_t i = 1; i < n_bounds; ++i)
+            if (b[i] <= b[i - 1]) sg::fail(SG_EINVAL, "window bounds must increase strictly");
+        if (b.back() > (int64_t(1) << 32)) sg::fail(SG_EINVAL, "window bounds beyond 2^32 sweeps");
+        h->model->set_windows(n_bounds - 1);
+        h->wb = std::move(b);
+    });
+}
+
+int sg_read_windows(sg_handle h, int64_t* C, int64_t* q, int64_t* E, int64_t* n_meas) {
+    return guarded([&] {
+        require_attached(h);
+        if (h->wb.empty()) sg::fail(SG_ESTATE, "no measurement windows were set");
+        if (!C || !q || !E || !n_meas) sg::fail(SG_EINVAL, "null output array");
+        sg::Model& m = *h->model;
+        const int64_t nb = (int64_t)h->wb.size() - 1, ntw = (int64_t)h->tw.size();
+        // sweeps measured so far in each window: tau' in [wb[m], wb[m+1]) with tau' <= tau
+        // (and tau' >= tw[w] for the correlation with snapshot w)
+        std::vector<int64_t> cnt((size_t)(ntw + 1) * nb);
+        for (int64_t k = 0; k < nb; ++k) {
+            const int64_t lo = h->wb[k], hi = std::min(h->wb[k + 1], h->tau + 1);
+            for (int64_t w = 0; w < ntw; ++w) cnt[w * nb + k] = std::max<int64_t>(0, hi - std::max(lo, h->tw[w]));
+            cnt[ntw * nb + k] = std::max<int64_t>(0, hi - lo);
+        }
+        m.read_windows(cnt.data(), cnt.data() + ntw * nb, C, q, E, h->stream);
+        std::copy(cnt.begin(), cnt.end(), n_meas);
     });
 }
 

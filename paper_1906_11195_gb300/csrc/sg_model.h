@@ -62,6 +62,17 @@ public:
     // device-side error word (0 = fine), read after synchronisation
     virtual int device_status(cudaStream_t st) { (void)st; return 0; }
 
+    // Window-averaged measurement (set before attach): n_bins windows of sweeps; every sweep
+    // inside window m adds its point values into window m's sums.
+    virtual void set_windows(int64_t n_bins) = 0;
+    // add the point values at time tau into window m
+    virtual void measure_window(int m, int64_t tau, cudaStream_t st) = 0;
+    // copy the window sums to the host and finalise them into sums of C, q, E; cnt_c[w][m] and
+    // cnt_q[m] are the numbers of sweeps measured in window m (with tw[w] <= tau for C)
+    virtual void read_windows(const int64_t* cnt_c, const int64_t* cnt_q, int64_t* C, int64_t* q,
+                              int64_t* E, cudaStream_t st) = 0;
+    int64_t n_bins = 0;
+
     int n_inst = 1, R = 1, L = 1;
     uint32_t* clock_dev = nullptr;  // device word holding the index of the next sweep
     std::vector<int64_t> tw, tm;

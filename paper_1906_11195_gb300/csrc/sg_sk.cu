@@ -221,12 +221,48 @@ public:
 
     void snapshot(int w, cudaStream_t st) override { launches += sk_snapshot(d_, w, st); }
 
-    void measure_scheduled(int u, int64_t tau, cudaStream_t st) override {
-        const int64_t ntw = (int64_t)tw.size(), ntm = (int64_t)tm.size();
+    // add the raw values at time tau into column u of arrays with ncol columns
+    void measure_into(int64_t* Cb, int64_t* Qb, int64_t* Eb, int64_t ncol, int64_t u, int64_t tau,
+                      cudaStream_t st) {
+        const int64_t ntw = (int64_t)tw.size();
         int active = 0;
         while (active < (int)ntw && tw[active] <= tau) ++active;
-        launches += sk_measure(d_, active, dC_ + u, ntw * ntm, ntm, R >= 2 ? dQ_ + u : nullptr, ntm,
-                               dE_ + u, ntm, st);
+        launches += sk_measure(d_, active, Cb + u, ntw * ncol, ncol, R >= 2 ? Qb + u : nullptr, ncol,
+                               Eb + u, ncol, st);
+    }
+
+    void measure_scheduled(int u, int64_t tau, cudaStream_t st) override {
+        measure_into(dC_, dQ_, dE_, (int64_t)tm.size(), u, tau, st);
+    }
+
+    void set_windows(int64_t nb) override {
+        n_bins = nb;
+        Carver c;
+        carve(c);
+        ws_bytes_ = c.off;
+    }
+
+    void measure_window(int m, int64_t tau, cudaStream_t st) override {
+        measure_into(wC_, wQ_, wE_, n_bins, m, tau, st);
+    }
+
+    void read_windows(const int64_t* cnt_c, const int64_t* cnt_q, int64_t* C, int64_t* q,
+                      int64_t* E, cudaStream_t st) override {
+        std::vector<int64_t> c(nwC()), qq(nwQ()), e(nwE());
+        down(c.data(), wC_, c.size() * 8, st);
+        down(qq.data(), wQ_, qq.size() * 8, st);
+        down(e.data(), wE_, e.size() * 8, st);
+        check_cuda(cudaStreamSynchronize(st), "read windows");
+        const int64_t ntw = (int64_t)tw.size(), nb = n_bins;
+        for (int r = 0; r < R; ++r)
+            for (int64_t m = 0; m < nb; ++m) {
+                for (int64_t w = 0; w < ntw; ++w) {
+                    const int64_t k = ((int64_t)r * ntw + w) * nb + m;
+                    C[k] = cnt_c[w * nb + m] * n_ - 2 * c[k];
+                }
+                E[(int64_t)r * nb + m] = e[(int64_t)r * nb + m];
+                if (r < R / 2) q[(int64_t)r * nb + m] = cnt_q[m] * n_ - 2 * qq[(int64_t)r * nb + m];
+            }
     }
 
     void measure_now(int64_t tau, cudaStream_t st) override {
@@ -234,6 +270,8 @@ public:
         int active = 0;
         while (active < (int)ntw && tw[active] <= tau) ++active;
         check_cuda(cudaMemsetAsync(mC_, 0, nmC() * 8, st), "memset");
+        if (nmQ()) check_cuda(cudaMemsetAsync(mQ_, 0, nmQ() * 8, st), "memset");
+        check_cuda(cudaMemsetAsync(mE_, 0, nmE() * 8, st), "memset");
         launches += sk_measure(d_, active, mC_, ntw, 1, R >= 2 ? mQ_ : nullptr, 1, mE_, 1, st);
     }
 
@@ -295,7 +333,8 @@ public:
     std::vector<std::pair<void*, size_t>> state_regions() override {
         const size_t sw = (size_t)R * (Np_ / 32) * 4;
         return {{d_.S, sw}, {d_.H, (size_t)R * Np_ * 4}, {d_.snap, tw.size() * sw},
-                {dC_, nC() * 8}, {dQ_, nQ() * 8}, {dE_, nE() * 8}};
+                {dC_, nC() * 8}, {dQ_, nQ() * 8}, {dE_, nE() * 8},
+                {wC_, nwC() * 8}, {wQ_, nwQ() * 8}, {wE_, nwE() * 8}};
     }
 
     int device_status(cudaStream_t st) override {
@@ -314,6 +353,9 @@ private:
     size_t nmC() const { return (size_t)R * tw.size(); }
     size_t nmQ() const { return (size_t)(R / 2); }
     size_t nmE() const { return (size_t)R; }
+    size_t nwC() const { return (size_t)R * tw.size() * n_bins; }
+    size_t nwQ() const { return (size_t)(R / 2) * n_bins; }
+    size_t nwE() const { return (size_t)R * n_bins; }
 
     static void down(void* dst, const void* src, size_t bytes, cudaStream_t st) {
         if (bytes) check_cuda(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st), "D2H copy");
@@ -340,6 +382,11 @@ private:
         check_cuda(cudaMemsetAsync(dC_, 0, nC() * 8, st), "memset");
         check_cuda(cudaMemsetAsync(dQ_, 0, nQ() * 8, st), "memset");
         check_cuda(cudaMemsetAsync(dE_, 0, nE() * 8, st), "memset");
+        if (n_bins) {
+            check_cuda(cudaMemsetAsync(wC_, 0, nwC() * 8, st), "memset");
+            check_cuda(cudaMemsetAsync(wQ_, 0, nwQ() * 8, st), "memset");
+            check_cuda(cudaMemsetAsync(wE_, 0, nwE() * 8, st), "memset");
+        }
         launches += sk_init(d_, st);
         if (kernel_ == SG_SK_BLOCKED) {
             // initial fields h = J s, one block of columns at a time (D holds s)
@@ -407,6 +454,9 @@ private:
         mC_ = c.take<int64_t>(nmC());
         mQ_ = c.take<int64_t>(nmQ());
         mE_ = c.take<int64_t>(nmE());
+        wC_ = c.take<int64_t>(nwC());
+        wQ_ = c.take<int64_t>(nwQ());
+        wE_ = c.take<int64_t>(nwE());
     }
 
     int kernel_ = SG_SK_BLOCKED;
@@ -424,6 +474,7 @@ private:
     CUtensorMap mapJ_{}, mapD_{};
     int64_t *dC_ = nullptr, *dQ_ = nullptr, *dE_ = nullptr;
     int64_t *mC_ = nullptr, *mQ_ = nullptr, *mE_ = nullptr;
+    int64_t *wC_ = nullptr, *wQ_ = nullptr, *wE_ = nullptr;  // window sums
 };
 
 // h_i = sum_j J_ij s_j on CUDA cores (initial fields of the plain path)
@@ -532,6 +583,24 @@ public:
     void measure_now(int64_t tau, cudaStream_t st) override {
         for (auto& m : subs_) m->measure_now(tau, st);
         collect();
+    }
+
+    void set_windows(int64_t nb) override {
+        n_bins = nb;
+        for (auto& m : subs_) m->set_windows(nb);
+    }
+
+    void measure_window(int mw, int64_t tau, cudaStream_t st) override {
+        for (auto& m : subs_) m->measure_window(mw, tau, st);
+        collect();
+    }
+
+    void read_windows(const int64_t* cnt_c, const int64_t* cnt_q, int64_t* C, int64_t* q,
+                      int64_t* E, cudaStream_t st) override {
+        const size_t nc = (size_t)R * tw.size() * n_bins, nq = (size_t)(R / 2) * n_bins,
+                     ne = (size_t)R * n_bins;
+        for (size_t b = 0; b < subs_.size(); ++b)
+            subs_[b]->read_windows(cnt_c, cnt_q, C + b * nc, q + b * nq, E + b * ne, st);
     }
 
     void read_scheduled(int64_t tau, int64_t* C, int64_t* q, int64_t* E, cudaStream_t st) override {

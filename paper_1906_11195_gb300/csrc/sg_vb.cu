@@ -199,6 +199,11 @@ public:
         check_cuda(cudaMemsetAsync(dC_, 0, nC() * 8, st), "memset");
         check_cuda(cudaMemsetAsync(dQ_, 0, nQ() * 8, st), "memset");
         check_cuda(cudaMemsetAsync(dE_, 0, nE() * 8, st), "memset");
+        if (n_bins) {
+            check_cuda(cudaMemsetAsync(wC_, 0, nwC() * 8, st), "memset");
+            check_cuda(cudaMemsetAsync(wQ_, 0, nwQ() * 8, st), "memset");
+            check_cuda(cudaMemsetAsync(wE_, 0, nwE() * 8, st), "memset");
+        }
         check_cuda(cudaGetLastError(), "init launch");
         check_cuda(cudaStreamSynchronize(st), "attach");
     }
@@ -272,20 +277,67 @@ public:
         else if (vb_plain_snapshot(pl_, w, st) < 0) fail(SG_ECUDA, "snapshot copy failed");
     }
 
-    void measure_scheduled(int u, int64_t tau, cudaStream_t st) override {
-        const int64_t ntw = (int64_t)tw.size(), ntm = (int64_t)tm.size();
+    // add the raw counts at time tau into column u of count arrays with ncol columns
+    void measure_into(int64_t* Cb, int64_t* Qb, int64_t* Eb, int64_t ncol, int64_t u, int64_t tau,
+                      cudaStream_t st) {
+        const int64_t ntw = (int64_t)tw.size();
         for (int64_t w = 0; w < ntw; ++w) {
             if (tw[w] > tau) break;
-            VbCountJob j{0, (int)w, dC_ + w * ntm + u, (int64_t)R * Lc_ * ntw * ntm,
-                         (int64_t)Lc_ * ntw * ntm, ntw * ntm};
+            VbCountJob j{0, (int)w, Cb + w * ncol + u, (int64_t)R * Lc_ * ntw * ncol,
+                         (int64_t)Lc_ * ntw * ncol, ntw * ncol};
             run_job(j, st);
         }
         if (R >= 2) {
-            VbCountJob j{1, 0, dQ_ + u, (int64_t)(R / 2) * Lc_ * ntm, (int64_t)Lc_ * ntm, ntm};
+            VbCountJob j{1, 0, Qb + u, (int64_t)(R / 2) * Lc_ * ncol, (int64_t)Lc_ * ncol, ncol};
             run_job(j, st);
         }
-        VbCountJob j{2, 0, dE_ + u, (int64_t)R * Lc_ * ntm, (int64_t)Lc_ * ntm, ntm};
+        VbCountJob j{2, 0, Eb + u, (int64_t)R * Lc_ * ncol, (int64_t)Lc_ * ncol, ncol};
         run_job(j, st);
+    }
+
+    void measure_scheduled(int u, int64_t tau, cudaStream_t st) override {
+        measure_into(dC_, dQ_, dE_, (int64_t)tm.size(), u, tau, st);
+    }
+
+    void set_windows(int64_t nb) override {
+        n_bins = nb;
+        Carver c;
+        carve(c);
+        ws_bytes_ = c.off;
+    }
+
+    void measure_window(int m, int64_t tau, cudaStream_t st) override {
+        measure_into(wC_, wQ_, wE_, n_bins, m, tau, st);
+    }
+
+    void read_windows(const int64_t* cnt_c, const int64_t* cnt_q, int64_t* C, int64_t* q,
+                      int64_t* E, cudaStream_t st) override {
+        std::vector<int64_t> c(nwC()), qq(nwQ()), e(nwE());
+        down(c.data(), wC_, c.size() * 8, st);
+        down(qq.data(), wQ_, qq.size() * 8, st);
+        down(e.data(), wE_, e.size() * 8, st);
+        check_cuda(cudaStreamSynchronize(st), "read windows");
+        const int64_t ntw = (int64_t)tw.size(), nb = n_bins;
+        for (int b = 0; b < n_inst; ++b) {
+            const int64_t N = graphs_[b].n, M = graphs_[b].edges;
+            for (int r = 0; r < R; ++r)
+                for (int k = 0; k < L; ++k)
+                    for (int64_t m = 0; m < nb; ++m) {
+                        for (int64_t w = 0; w < ntw; ++w) {
+                            const int64_t src = ((((int64_t)b * R + r) * Lc_ + k) * ntw + w) * nb + m;
+                            const int64_t dst = ((((int64_t)b * R + r) * L + k) * ntw + w) * nb + m;
+                            C[dst] = cnt_c[w * nb + m] * N - 2 * c[src];
+                        }
+                        const int64_t se = (((int64_t)b * R + r) * Lc_ + k) * nb + m;
+                        const int64_t de = (((int64_t)b * R + r) * L + k) * nb + m;
+                        E[de] = cnt_q[m] * M - e[se];
+                        if (r < R / 2) {
+                            const int64_t sq = (((int64_t)b * (R / 2) + r) * Lc_ + k) * nb + m;
+                            const int64_t dq = (((int64_t)b * (R / 2) + r) * L + k) * nb + m;
+                            q[dq] = cnt_q[m] * N - 2 * qq[sq];
+                        }
+                    }
+        }
     }
 
     void measure_now(int64_t tau, cudaStream_t st) override {
@@ -421,6 +473,11 @@ public:
         v.push_back({dC_, nC() * 8});
         v.push_back({dQ_, nQ() * 8});
         v.push_back({dE_, nE() * 8});
+        if (n_bins) {
+            v.push_back({wC_, nwC() * 8});
+            v.push_back({wQ_, nwQ() * 8});
+            v.push_back({wE_, nwE() * 8});
+        }
         return v;
     }
 
@@ -429,6 +486,9 @@ private:
     size_t nQ() const { return (size_t)n_inst * (R / 2) * Lc_ * tm.size(); }
     size_t nE() const { return (size_t)n_inst * R * Lc_ * tm.size(); }
     size_t nmC() const { return (size_t)n_inst * R * Lc_ * tw.size(); }
+    size_t nwC() const { return (size_t)n_inst * R * Lc_ * tw.size() * n_bins; }
+    size_t nwQ() const { return (size_t)n_inst * (R / 2) * Lc_ * n_bins; }
+    size_t nwE() const { return (size_t)n_inst * R * Lc_ * n_bins; }
     size_t nmQ() const { return (size_t)n_inst * (R / 2) * Lc_; }
     size_t nmE() const { return (size_t)n_inst * R * Lc_; }
 
@@ -486,6 +546,9 @@ private:
         mC_ = c.take<int64_t>(nmC());
         mQ_ = c.take<int64_t>(nmQ());
         mE_ = c.take<int64_t>(nmE());
+        wC_ = c.take<int64_t>(nwC());
+        wQ_ = c.take<int64_t>(nwQ());
+        wE_ = c.take<int64_t>(nwE());
     }
 
     // colour-major CSR of the single graph (plain kernel)
@@ -678,6 +741,7 @@ private:
     uint32_t* d_thr_ = nullptr;
     int64_t *dC_ = nullptr, *dQ_ = nullptr, *dE_ = nullptr;
     int64_t *mC_ = nullptr, *mQ_ = nullptr, *mE_ = nullptr;
+    int64_t *wC_ = nullptr, *wQ_ = nullptr, *wE_ = nullptr;  // window sums of raw counts
 };
 
 }  // namespace

@@ -44,6 +44,7 @@ int sk_field_update_rows(const SkDev& d, const CUtensorMap& mapJ, const CUtensor
 size_t sk_plain_smem_bytes(int Np);
 int sk_plain_prepare(int Np);
 int sk_plain_sweep(const SkDev& d, const uint32_t* clock, uint32_t t_off, cudaStream_t st);
+// adds the raw counts (C and q differences, E = 1/2 sum s h) into the destinations
 int sk_measure(const SkDev& d, int n_active, int64_t* cdst, int64_t c_stride_r,
                int64_t c_stride_w, int64_t* qdst, int64_t q_stride_p, int64_t* edst,
                int64_t e_stride_r, cudaStream_t st);

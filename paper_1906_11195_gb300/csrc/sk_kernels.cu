@@ -551,14 +551,14 @@ __global__ void k_sk_measure(SkDev d, int n_active, int64_t* cdst, int64_t c_str
         long long acc = 0;
         for (int k = threadIdx.x; k < words; k += blockDim.x) acc += __popc(S[k] ^ P[k]);
         const long long tot = block_sum(acc, red);
-        if (threadIdx.x == 0) cdst[r * c_stride_r + w * c_stride_w] = tot;
+        if (threadIdx.x == 0) cdst[r * c_stride_r + w * c_stride_w] += tot;
     }
     if ((r & 1) == 0 && r + 1 < d.R && qdst) {
         const uint32_t* S2 = S + words;
         long long acc = 0;
         for (int k = threadIdx.x; k < words; k += blockDim.x) acc += __popc(S[k] ^ S2[k]);
         const long long tot = block_sum(acc, red);
-        if (threadIdx.x == 0) qdst[(r >> 1) * q_stride_p] = tot;
+        if (threadIdx.x == 0) qdst[(r >> 1) * q_stride_p] += tot;
     }
     long long acc = 0;
     for (int i = threadIdx.x; i < d.N; i += blockDim.x) {
@@ -566,7 +566,7 @@ __global__ void k_sk_measure(SkDev d, int n_active, int64_t* cdst, int64_t c_str
         acc += (long long)s * d.H[(int64_t)r * d.Np + i];
     }
     const long long tot = block_sum(acc, red);
-    if (threadIdx.x == 0) edst[r * e_stride_r] = tot / 2;
+    if (threadIdx.x == 0) edst[r * e_stride_r] += tot / 2;
 }
 
 int sk_measure(const SkDev& d, int n_active, int64_t* cdst, int64_t c_stride_r,

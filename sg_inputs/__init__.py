@@ -30,6 +30,8 @@ __all__ = [
     "log_uniform_sizes",
     "csr_from_edges",
     "log_schedule",
+    "geometric_windows",
+    "tritone_windows",
 ]
 
 
@@ -188,3 +190,29 @@ def log_schedule(tw, t_max: int):
             tm.add(w + (1 << k))
             k += 1
     return np.array(tw, dtype=np.int64), np.array(sorted(tm), dtype=np.int64)
+
+
+def geometric_windows(t_min: int, t_max: int, ratio_log2: float = 0.25):
+    """Window bounds for averaging over geometric time windows [t_m, t_{m+1}) with
+    t_{m+1} / t_m = 2^ratio_log2 (2^(1/4): the "minor thirds" of the main text), from t_min
+    (>= 1) until t_max is covered; bounds are the distinct integer ceilings."""
+    if t_min < 1:
+        raise ValueError("t_min must be >= 1")
+    b, k = [], 0
+    while True:
+        v = int(np.ceil(t_min * 2.0 ** (k * ratio_log2) - 1e-9))
+        if not b or v > b[-1]:
+            b.append(v)
+        if v > t_max:
+            return np.array(b, dtype=np.int64)
+        k += 1
+
+
+def tritone_windows(t_max: int, t0: int = 4):
+    """Window bounds of the SK "tritone" lumps (SI section 1): the times T = t + t_w >= t0 with
+    the same floor(ln(T / t0) / (0.5 ln 2)) form one lump, so lump j = [t0 2^(j/2), t0 2^((j+1)/2)).
+    Evaluated on every integer T up to t_max exactly as written (double precision)."""
+    T = np.arange(t0, t_max + 2, dtype=np.int64)
+    j = np.floor(np.log(T / t0) / (0.5 * np.log(2.0))).astype(np.int64)
+    starts = np.flatnonzero(np.concatenate([[True], j[1:] != j[:-1]]))
+    return T[starts]

@@ -154,3 +154,19 @@ def test_edgeless_graph_is_accepted(lib):
         h = sg.sg_create_vb([g], 64, 2, kernel, [0], [0, 1, 2])
         assert sg.sg_workspace_bytes(h) > 0
         sg.sg_destroy(h)
+
+
+def test_windows_are_validated_and_grow_the_workspace(lib):
+    g = _graph()
+    h = sg.sg_create_vb([g], 64, 2, sg.SG_VB_PACKED, [0, 4], [0, 4, 8])
+    base = sg.sg_workspace_bytes(h)
+    for bad in ([5], [4, 4], [6, 3], [-1, 2]):
+        with pytest.raises(sg.SGError) as e:
+            sg.sg_set_windows(h, bad)
+        assert e.value.code == sg.SG_EINVAL
+    sg.sg_set_windows(h, sg_inputs.geometric_windows(2, 1000))
+    assert sg.sg_workspace_bytes(h) > base
+    with pytest.raises(sg.SGError) as e:  # nothing attached: no sums to read
+        sg.sg_read_windows(h, 3)
+    assert e.value.code == sg.SG_ESTATE
+    sg.sg_destroy(h)

@@ -53,3 +53,22 @@ def test_generator_is_seeded():
     b = sg_inputs.random_regular_graph(2000, 4, 9, bipartite=True)
     c = sg_inputs.random_regular_graph(2000, 4, 10, bipartite=True)
     assert np.array_equal(a[1], b[1]) and not np.array_equal(a[1], c[1])
+
+
+def test_tritone_windows_follow_the_lumping_formula():
+    """SI section 1: times T = t + t_w with equal floor(ln(T/4) / (0.5 ln 2)) form one lump;
+    {4, 5} is the first lump (its mean time is 4.5)."""
+    import math
+    b = sg_inputs.tritone_windows(5000)
+    assert list(b[:3]) == [4, 6, 8]
+    for m in range(len(b) - 1):
+        for T in range(int(b[m]), int(b[m + 1])):
+            assert math.floor(math.log(T / 4) / (0.5 * math.log(2.0))) == m
+
+
+def test_geometric_windows_have_ratio_two_to_the_quarter():
+    b = sg_inputs.geometric_windows(64, 10 ** 6)
+    assert b[0] == 64 and b[-1] > 10 ** 6
+    assert np.all(np.diff(b) > 0)
+    r = b[8:] / b[:-8]  # two octaves later: ratio 4 up to rounding
+    assert np.all(np.abs(r - 4.0) < 4.0 * 2.0 / b[:-8] + 1e-12)
