@@ -376,6 +376,51 @@ def run_rrbg(args):
     return 0
 
 
+def run_vb_windows(args):
+    """The headline VB workload with the main text's estimator (not the headline line): every
+    sweep from tau = 2^4 on is measured (C against every snapshot taken, q, E) and added into
+    geometric windows of ratio 2^(1/4), on top of the point schedule; one step = one sweep of
+    each temperature instance.  Shows what the per-sweep measurement costs."""
+    import torch
+
+    import paper_1906_11195_gb300 as sg
+    from paper_1906_11195_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    rp, col, jb = instance(0)
+    tw, tm = sg_inputs.log_schedule(TW, T_MAX)
+    bounds = sg_inputs.geometric_windows(16, args.warmup + args.steps + 1)
+    runs = [sg.VBRun([dict(row_ptr=rp, col=col, jbits=jb, seed=1, temps=[T] * REPLICAS)],
+                     n_lanes=LANES, n_replicas=REPLICAS, kernel=sg.SG_VB_PACKED, tw=tw, tm=tm,
+                     windows=bounds) for T in TEMPS]
+    stream = torch.cuda.current_stream()
+    for r in runs:
+        r.sweep(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = sum(r.launches for r in runs)
+    nvtx_push("timed_region")
+    e0.record(stream)
+    for r in runs:
+        r.sweep(args.steps)
+    e1.record(stream)
+    nvtx_pop()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = sum(r.launches for r in runs) - l0
+    for r in runs:
+        r.synchronize()
+        r.close()
+    updates = len(TEMPS) * N_VERTS * LANES * REPLICAS
+    print(json.dumps({"metric": "spin updates/ns", "unit": "spin updates/ns",
+                      "value": updates / (ms * 1e6), "ms_per_step": ms, "steps": args.steps,
+                      "warmup": args.warmup, "gpu_launches": launches,
+                      "config": {"workload": WORKLOAD + "_windowed",
+                                 "windows": f"{len(bounds) - 1} geometric windows, ratio 2^(1/4), "
+                                            f"from tau = 16, every sweep measured"}}), flush=True)
+    return 0
+
+
 def run_e6(args):
     """The paper's bipartite vs non-bipartite comparison (not a throughput line): C(t_w + t, t_w)
     at t_w = 4 on random regular graphs of degree 4, bipartite and plain, T = 0.8 T_c, for
@@ -725,11 +770,13 @@ def main():
     ap.add_argument("--profile-replicas", type=int, default=2, choices=[2, 4],
                     help="replicas of the profile case (4: two per temperature)")
     ap.add_argument("--workload", default="vb",
-                    choices=["vb", "sk", "vb_batch", "sk_batch", "rrbg", "e6"],
+                    choices=["vb", "sk", "vb_batch", "sk_batch", "rrbg", "e6", "vb_windows"],
                     help="vb: the headline bit-packed Viana-Bray line; sk: the SK blocked line; "
                          "vb_batch: the uneven batch of Viana-Bray graphs; sk_batch: the uneven "
                          "batch of SK samples; rrbg: the paper's bipartite regular graph; e6: "
-                         "bipartite vs plain regular graphs, C(t_w + t, t_w) at t_w = 4")
+                         "bipartite vs plain regular graphs, C(t_w + t, t_w) at t_w = 4; "
+                         "vb_windows: the headline workload measured every sweep into "
+                         "geometric windows")
     ap.add_argument("--e6-tmax", type=int, default=4 + 2 ** 16, help="last time of the e6 curves")
     ap.add_argument("--batch", type=int, default=512, help="graphs in the vb_batch workload")
     ap.add_argument("--sk-block", type=int, default=SK_B)
@@ -750,6 +797,8 @@ def main():
         return run_rrbg(args)
     if args.workload == "e6":
         return run_e6(args)
+    if args.workload == "vb_windows":
+        return run_vb_windows(args)
     return run_gpu(args)
 
 

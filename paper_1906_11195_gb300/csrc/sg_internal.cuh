@@ -187,11 +187,14 @@ struct VbPlainDev {
 //   kind 0: Hamming distance between the spins and snapshot w (all replicas)
 //   kind 1: Hamming distance between replicas 2p and 2p+1 (all pairs)
 //   kind 2: number of unsatisfied directed entries, J_ij s_i s_j = -1 (all replicas)
+// kind 0: C against snapshot w; 1: q; 2: E; 3 (packed only): C against snapshots 0 .. w-1 in
+// one pass (snapshot k adds at dst + k * stride_w), reading the current spins once
 struct VbCountJob {
     int kind;
     int w;
     int64_t* dst;
     int64_t stride_g, stride_r, stride_k;
+    int64_t stride_w;
 };
 
 // launch wrappers (vb_kernels.cu); each returns the number of kernel launches queued

@@ -281,11 +281,19 @@ public:
     void measure_into(int64_t* Cb, int64_t* Qb, int64_t* Eb, int64_t ncol, int64_t u, int64_t tau,
                       cudaStream_t st) {
         const int64_t ntw = (int64_t)tw.size();
-        for (int64_t w = 0; w < ntw; ++w) {
-            if (tw[w] > tau) break;
-            VbCountJob j{0, (int)w, Cb + w * ncol + u, (int64_t)R * Lc_ * ntw * ncol,
-                         (int64_t)Lc_ * ntw * ncol, ntw * ncol};
+        int64_t active = 0;
+        while (active < ntw && tw[active] <= tau) ++active;
+        if (kernel_ == SG_VB_PACKED && active > 1) {
+            // every active snapshot in one pass over the current spins
+            VbCountJob j{3, (int)active, Cb + u, (int64_t)R * Lc_ * ntw * ncol,
+                         (int64_t)Lc_ * ntw * ncol, ntw * ncol, ncol};
             run_job(j, st);
+        } else {
+            for (int64_t w = 0; w < active; ++w) {
+                VbCountJob j{0, (int)w, Cb + w * ncol + u, (int64_t)R * Lc_ * ntw * ncol,
+                             (int64_t)Lc_ * ntw * ncol, ntw * ncol, 0};
+                run_job(j, st);
+            }
         }
         if (R >= 2) {
             VbCountJob j{1, 0, Qb + u, (int64_t)(R / 2) * Lc_ * ncol, (int64_t)Lc_ * ncol, ncol};

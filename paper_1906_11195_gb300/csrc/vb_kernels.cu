@@ -816,46 +816,58 @@ __global__ void __launch_bounds__(256, R <= 2 ? 2 : 1) k_vb_packed_count(VbPacke
     const int64_t s_lo = (int64_t)warp * kCountSlicesPerWarp;
     int64_t s_hi = s_lo + kCountSlicesPerWarp;
     if (s_hi > d.n_slices) s_hi = d.n_slices;
-    const int nq = job.kind == 1 ? R / 2 : R;
-    uint64_t p[NQ][kCountWide];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q)
-#pragma unroll
-        for (int b = 0; b < kCountWide; ++b) p[q][b] = 0ull;
     const int64_t words = d.n_slots * R;
-    const uint64_t* snap = d.snap + (int64_t)(job.kind == 0 ? job.w : 0) * words;
-    int64_t cur_g = -1;
-    for (int64_t s = s_lo; s < s_hi; ++s) {
-        const uint32_t g = __ldg(d.slice_graph + s);  // warp-uniform
-        if ((int64_t)g != cur_g) {
-            if (cur_g >= 0) count_flush<NQ>(p, job, (uint32_t)cur_g, nq, lane);
-            cur_g = g;
+    // kind 3: one pass per snapshot over this warp's slices; the current spins of the slices
+    // (a few KB) stay in L1 after the first pass
+    const int passes = job.kind == 3 ? job.w : 1;
+    for (int pass = 0; pass < passes; ++pass) {
+        VbCountJob jb = job;
+        if (job.kind == 3) {
+            jb.kind = 0;
+            jb.w = pass;
+            jb.dst = job.dst + pass * job.stride_w;
         }
-        const int64_t slot = s * 32 + lane;
-        if (__ldg(d.vinfo + slot) == kInactive) continue;
-        const SpinWords<R> si = load_words<R>(d.S + slot * R);
-        if (job.kind == 0) {
-            const SpinWords<R> sw = load_words<R>(snap + slot * R);
+        const int kind = jb.kind;
+        const int nq = kind == 1 ? R / 2 : R;
+        uint64_t p[NQ][kCountWide];
 #pragma unroll
-            for (int r = 0; r < R; ++r) count_add<NQ>(p, r, si.v[r] ^ sw.v[r]);
-        } else if (job.kind == 1) {
+        for (int q = 0; q < NQ; ++q)
 #pragma unroll
-            for (int q = 0; q < R / 2; ++q) count_add<NQ>(p, q, si.v[2 * q] ^ si.v[2 * q + 1]);
-        } else {
-            const uint32_t base = __ldg(d.slice_base + s);
-            const uint32_t width = (__ldg(d.slice_base + s + 1) - base) >> 5;
-            uint32_t idx = base + lane;
+            for (int b = 0; b < kCountWide; ++b) p[q][b] = 0ull;
+        const uint64_t* snap = d.snap + (int64_t)(kind == 0 ? jb.w : 0) * words;
+        int64_t cur_g = -1;
+        for (int64_t s = s_lo; s < s_hi; ++s) {
+            const uint32_t g = __ldg(d.slice_graph + s);  // warp-uniform
+            if ((int64_t)g != cur_g) {
+                if (cur_g >= 0) count_flush<NQ>(p, jb, (uint32_t)cur_g, nq, lane);
+                cur_g = g;
+            }
+            const int64_t slot = s * 32 + lane;
+            if (__ldg(d.vinfo + slot) == kInactive) continue;
+            const SpinWords<R> si = load_words<R>(d.S + slot * R);
+            if (kind == 0) {
+                const SpinWords<R> sw = load_words<R>(snap + slot * R);
+#pragma unroll
+                for (int r = 0; r < R; ++r) count_add<NQ>(p, r, si.v[r] ^ sw.v[r]);
+            } else if (kind == 1) {
+#pragma unroll
+                for (int q = 0; q < R / 2; ++q) count_add<NQ>(p, q, si.v[2 * q] ^ si.v[2 * q + 1]);
+            } else {
+                const uint32_t base = __ldg(d.slice_base + s);
+                const uint32_t width = (__ldg(d.slice_base + s + 1) - base) >> 5;
+                uint32_t idx = base + lane;
 #pragma unroll 4
-            for (uint32_t e = 0; e < width; ++e, idx += 32) {
-                const uint32_t j = __ldg(d.col + idx);
-                const uint64_t J = __ldg(d.jb + idx);
-                const SpinWords<R> sj = gather_words<R>(d.S + (int64_t)j * R);
+                for (uint32_t e = 0; e < width; ++e, idx += 32) {
+                    const uint32_t j = __ldg(d.col + idx);
+                    const uint64_t J = __ldg(d.jb + idx);
+                    const SpinWords<R> sj = gather_words<R>(d.S + (int64_t)j * R);
 #pragma unroll
-                for (int r = 0; r < R; ++r) count_add<NQ>(p, r, si.v[r] ^ sj.v[r] ^ J);
+                    for (int r = 0; r < R; ++r) count_add<NQ>(p, r, si.v[r] ^ sj.v[r] ^ J);
+                }
             }
         }
+        if (cur_g >= 0) count_flush<NQ>(p, jb, (uint32_t)cur_g, nq, lane);
     }
-    if (cur_g >= 0) count_flush<NQ>(p, job, (uint32_t)cur_g, nq, lane);
 }
 
 int vb_packed_count(const VbPackedDev& d, const VbCountJob& job, cudaStream_t st) {
