@@ -836,6 +836,9 @@ __global__ void __launch_bounds__(256, R <= 2 ? 2 : 1) k_vb_packed_count(VbPacke
             for (int b = 0; b < kCountWide; ++b) p[q][b] = 0ull;
         const uint64_t* snap = d.snap + (int64_t)(kind == 0 ? jb.w : 0) * words;
         int64_t cur_g = -1;
+        // padding slots hold zero words and zero couplings, so they add nothing: no vinfo test,
+        // and the loads of several slices can be in flight together
+#pragma unroll 4
         for (int64_t s = s_lo; s < s_hi; ++s) {
             const uint32_t g = __ldg(d.slice_graph + s);  // warp-uniform
             if ((int64_t)g != cur_g) {
@@ -843,7 +846,6 @@ __global__ void __launch_bounds__(256, R <= 2 ? 2 : 1) k_vb_packed_count(VbPacke
                 cur_g = g;
             }
             const int64_t slot = s * 32 + lane;
-            if (__ldg(d.vinfo + slot) == kInactive) continue;
             const SpinWords<R> si = load_words<R>(d.S + slot * R);
             if (kind == 0) {
                 const SpinWords<R> sw = load_words<R>(snap + slot * R);
