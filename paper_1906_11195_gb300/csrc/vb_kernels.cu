@@ -757,16 +757,15 @@ int vb_packed_snapshot(const VbPackedDev& d, int w, cudaStream_t st) {
 // accumulates bit-sliced per-lane counters (16 planes) and flushes them to global memory when
 // the graph changes and at the end of its run.
 // ---------------------------------------------------------------------------------------------
-// A lane adds at most one word per slot (C, q) or one per entry (E: 16 slices x width <= 63 =
-// 1008 words), so 10 planes (up to 1023) cannot overflow before the flush at the end of a run.
-constexpr int kCountPlanes = 10;
-constexpr int kCountWide = kCountPlanes + 5;     // after the 32-lane butterfly
+// A lane adds at most one word per slot (C, q: 16 slices, so 5 planes hold up to 31) or one per
+// entry (E: 16 slices x width <= 63 = 1008 words: 10 planes, up to 1023), so PL planes cannot
+// overflow before the flush at the end of a run; the 32-lane butterfly needs PL + 5 planes.
 constexpr int kCountSlicesPerWarp = 16;
 
-template <int NQ>
-__device__ __forceinline__ void count_add(uint64_t (&p)[NQ][kCountWide], int q, uint64_t x) {
+template <int NQ, int PW>
+__device__ __forceinline__ void count_add(uint64_t (&p)[NQ][PW], int q, uint64_t x) {
 #pragma unroll
-    for (int b = 0; b < kCountPlanes; ++b) {
+    for (int b = 0; b < PW - 5; ++b) {
         const uint64_t c = p[q][b] & x;
         p[q][b] ^= x;
         x = c;
@@ -775,8 +774,8 @@ __device__ __forceinline__ void count_add(uint64_t (&p)[NQ][kCountWide], int q, 
 
 // Sum the bit-sliced counters of the 32 lanes with a butterfly of bit-sliced additions, then
 // lane l writes the totals of spin lanes l and l + 32.
-template <int NQ>
-__device__ __forceinline__ void count_flush(uint64_t (&p)[NQ][kCountWide], const VbCountJob& job,
+template <int NQ, int PW>
+__device__ __forceinline__ void count_flush(uint64_t (&p)[NQ][PW], const VbCountJob& job,
                                             uint32_t g, int nq, uint32_t lane) {
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
@@ -785,7 +784,7 @@ __device__ __forceinline__ void count_flush(uint64_t (&p)[NQ][kCountWide], const
         for (int off = 16; off > 0; off >>= 1) {
             uint64_t carry = 0ull;
 #pragma unroll
-            for (int b = 0; b < kCountWide; ++b) {
+            for (int b = 0; b < PW; ++b) {
                 const uint64_t o = __shfl_xor_sync(0xFFFFFFFFu, p[q][b], off);
                 const uint64_t x = p[q][b] ^ o;
                 const uint64_t sum = x ^ carry;
@@ -795,7 +794,7 @@ __device__ __forceinline__ void count_flush(uint64_t (&p)[NQ][kCountWide], const
         }
         uint32_t c0 = 0, c1 = 0;
 #pragma unroll
-        for (int b = 0; b < kCountWide; ++b) {
+        for (int b = 0; b < PW; ++b) {
             c0 |= (uint32_t)((p[q][b] >> lane) & 1ull) << b;
             c1 |= (uint32_t)((p[q][b] >> (lane + 32)) & 1ull) << b;
         }
@@ -804,13 +803,16 @@ __device__ __forceinline__ void count_flush(uint64_t (&p)[NQ][kCountWide], const
         if (c1)
             atomicAdd((unsigned long long*)(base + (lane + 32) * job.stride_k), (unsigned long long)c1);
 #pragma unroll
-        for (int b = 0; b < kCountWide; ++b) p[q][b] = 0ull;
+        for (int b = 0; b < PW; ++b) p[q][b] = 0ull;
     }
 }
 
-template <int R>
-__global__ void __launch_bounds__(256, R <= 2 ? 2 : 1) k_vb_packed_count(VbPackedDev d, VbCountJob job) {
+// EN: the energy job (kind 2, PW = 15); otherwise C and q jobs (kinds 0, 1, 3, PW = 10)
+template <int R, bool EN>
+__global__ void __launch_bounds__(256, EN ? (R <= 2 ? 2 : 1) : (R <= 2 ? 3 : 2))
+    k_vb_packed_count(VbPackedDev d, VbCountJob job) {
     constexpr int NQ = R;
+    constexpr int PW = EN ? 15 : 10;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t s_lo = (int64_t)warp * kCountSlicesPerWarp;
@@ -829,11 +831,11 @@ __global__ void __launch_bounds__(256, R <= 2 ? 2 : 1) k_vb_packed_count(VbPacke
         }
         const int kind = jb.kind;
         const int nq = kind == 1 ? R / 2 : R;
-        uint64_t p[NQ][kCountWide];
+        uint64_t p[NQ][PW];
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
 #pragma unroll
-            for (int b = 0; b < kCountWide; ++b) p[q][b] = 0ull;
+            for (int b = 0; b < PW; ++b) p[q][b] = 0ull;
         const uint64_t* snap = d.snap + (int64_t)(kind == 0 ? jb.w : 0) * words;
         int64_t cur_g = -1;
         // padding slots hold zero words and zero couplings, so they add nothing: no vinfo test,
@@ -842,18 +844,21 @@ __global__ void __launch_bounds__(256, R <= 2 ? 2 : 1) k_vb_packed_count(VbPacke
         for (int64_t s = s_lo; s < s_hi; ++s) {
             const uint32_t g = __ldg(d.slice_graph + s);  // warp-uniform
             if ((int64_t)g != cur_g) {
-                if (cur_g >= 0) count_flush<NQ>(p, jb, (uint32_t)cur_g, nq, lane);
+                if (cur_g >= 0) count_flush<NQ, PW>(p, jb, (uint32_t)cur_g, nq, lane);
                 cur_g = g;
             }
             const int64_t slot = s * 32 + lane;
             const SpinWords<R> si = load_words<R>(d.S + slot * R);
-            if (kind == 0) {
-                const SpinWords<R> sw = load_words<R>(snap + slot * R);
+            if constexpr (!EN) {
+                if (kind == 0) {
+                    const SpinWords<R> sw = load_words<R>(snap + slot * R);
 #pragma unroll
-                for (int r = 0; r < R; ++r) count_add<NQ>(p, r, si.v[r] ^ sw.v[r]);
-            } else if (kind == 1) {
+                    for (int r = 0; r < R; ++r) count_add<NQ, PW>(p, r, si.v[r] ^ sw.v[r]);
+                } else {
 #pragma unroll
-                for (int q = 0; q < R / 2; ++q) count_add<NQ>(p, q, si.v[2 * q] ^ si.v[2 * q + 1]);
+                    for (int q = 0; q < R / 2; ++q)
+                        count_add<NQ, PW>(p, q, si.v[2 * q] ^ si.v[2 * q + 1]);
+                }
             } else {
                 const uint32_t base = __ldg(d.slice_base + s);
                 const uint32_t width = (__ldg(d.slice_base + s + 1) - base) >> 5;
@@ -864,11 +869,11 @@ __global__ void __launch_bounds__(256, R <= 2 ? 2 : 1) k_vb_packed_count(VbPacke
                     const uint64_t J = __ldg(d.jb + idx);
                     const SpinWords<R> sj = gather_words<R>(d.S + (int64_t)j * R);
 #pragma unroll
-                    for (int r = 0; r < R; ++r) count_add<NQ>(p, r, si.v[r] ^ sj.v[r] ^ J);
+                    for (int r = 0; r < R; ++r) count_add<NQ, PW>(p, r, si.v[r] ^ sj.v[r] ^ J);
                 }
             }
         }
-        if (cur_g >= 0) count_flush<NQ>(p, jb, (uint32_t)cur_g, nq, lane);
+        if (cur_g >= 0) count_flush<NQ, PW>(p, jb, (uint32_t)cur_g, nq, lane);
     }
 }
 
@@ -876,10 +881,20 @@ int vb_packed_count(const VbPackedDev& d, const VbCountJob& job, cudaStream_t st
     const int bs = 256;
     const int64_t warps = (d.n_slices + kCountSlicesPerWarp - 1) / kCountSlicesPerWarp;
     const unsigned nb = (unsigned)((warps + (bs / 32) - 1) / (bs / 32));
+    const bool en = job.kind == 2;
     switch (d.R) {
-        case 1: k_vb_packed_count<1><<<nb, bs, 0, st>>>(d, job); break;
-        case 2: k_vb_packed_count<2><<<nb, bs, 0, st>>>(d, job); break;
-        case 4: k_vb_packed_count<4><<<nb, bs, 0, st>>>(d, job); break;
+        case 1:
+            if (en) k_vb_packed_count<1, true><<<nb, bs, 0, st>>>(d, job);
+            else k_vb_packed_count<1, false><<<nb, bs, 0, st>>>(d, job);
+            break;
+        case 2:
+            if (en) k_vb_packed_count<2, true><<<nb, bs, 0, st>>>(d, job);
+            else k_vb_packed_count<2, false><<<nb, bs, 0, st>>>(d, job);
+            break;
+        case 4:
+            if (en) k_vb_packed_count<4, true><<<nb, bs, 0, st>>>(d, job);
+            else k_vb_packed_count<4, false><<<nb, bs, 0, st>>>(d, job);
+            break;
         default: return -1;
     }
     return 1;
