@@ -421,6 +421,68 @@ def run_vb_windows(args):
     return 0
 
 
+def run_aging(args):
+    """The paper's analysis chain at small scale (not a throughput line): bipartite random
+    regular graphs of degree 4 at T = 0.8 T_c, N = 2^12 .. 2^18 (2^21 vertices per size in one
+    batch, 64 coupling sets x 2 replicas per graph), t_w = 4, C(t_w + t, t_w) averaged over
+    geometric windows of ratio 2^(1/4) up to t_w + t = --aging-tmax; then the extrapolation to
+    infinite size (quadratic in N^(-2/3)) per window and the inverse Frechet and M = 1..3
+    polynomial fits of C_inf(t) on the last window of 8 octaves."""
+    import math
+
+    import torch
+
+    import paper_1906_11195_gb300 as sg
+    from paper_1906_11195_gb300 import _build, analysis
+    _build.build()
+    torch.cuda.set_device(0)
+    tw0 = 4
+    bounds = sg_inputs.geometric_windows(8, args.aging_tmax)
+    sizes = [1 << k for k in (12, 14, 16, 18)]
+    curves = []
+    t0 = time.perf_counter()
+    for n in sizes:
+        ng = max(1, (1 << 21) // n)
+        graphs = []
+        for i in range(ng):
+            sd = (n << 8) + i
+            rp, col, eid = sg_inputs.random_regular_graph(n, 4, sd, bipartite=True)
+            jb = sg_inputs.vb_lane_couplings(eid, eid.max() + 1, sd)
+            graphs.append(dict(row_ptr=rp, col=col, jbits=jb, seed=sd, temps=[T_08_TC] * REPLICAS))
+        run = sg.VBRun(graphs, n_lanes=LANES, n_replicas=REPLICAS, kernel=sg.SG_VB_PACKED,
+                       tw=[tw0], tm=[], windows=bounds)
+        run.sweep(int(bounds[-1]))
+        run.synchronize()
+        C, _, _, cnt = run.windows()
+        run.close()
+        avg, t_mean = analysis.window_averages(bounds, C[:, :, :, 0, :].sum(axis=(0, 1, 2)),
+                                               cnt[0] * ng * LANES * REPLICAS)
+        curves.append(avg / n)
+        log(f"N = {n}: {ng} graphs, {time.perf_counter() - t0:.1f} s")
+    curves = np.array(curves)  # [size][window]
+    ok = ~np.isnan(curves).any(axis=0)
+    c_inf, coef, _ = analysis.finite_size_extrapolation(np.array(sizes), curves[:, ok],
+                                                        nu=2.0 / 3.0, order=2)
+    t = t_mean[ok] - tw0
+    keep = t >= 1
+    t, ci = t[keep], c_inf[keep]
+    n_last = int(math.floor(math.log2(t.max())))
+    win = (t >= 2.0 ** (n_last - 8)) & (t <= 2.0 ** n_last)
+    fits = {}
+    if win.sum() >= 4 and np.all(ci[win] > 0):
+        a, b, g, r = analysis.frechet_fit(t[win], ci[win])
+        fits["frechet"] = {"A": a, "B": b, "gamma": g, "ssr": r}
+        for M in (1, 2, 3):
+            a, b, g, r = analysis.polynomial_fit(t[win], ci[win], M)
+            fits[f"poly_M{M}"] = {"A": a, "B": b, "gamma": g, "ssr": r}
+    out = {"workload": "aging_rrbg_z4_T0.8Tc_tw4", "T": T_08_TC, "sizes": sizes,
+           "t": t.round(2).tolist(), "C_by_size": curves[:, ok][:, keep].round(6).tolist(),
+           "C_inf": ci.round(6).tolist(), "leading_coef_N^-2/3": coef[0][keep].round(4).tolist(),
+           "fit_window": [float(2.0 ** (n_last - 8)), float(2.0 ** n_last)], "fits": fits}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_e6(args):
     """The paper's bipartite vs non-bipartite comparison (not a throughput line): C(t_w + t, t_w)
     at t_w = 4 on random regular graphs of degree 4, bipartite and plain, T = 0.8 T_c, for
@@ -770,13 +832,15 @@ def main():
     ap.add_argument("--profile-replicas", type=int, default=2, choices=[2, 4],
                     help="replicas of the profile case (4: two per temperature)")
     ap.add_argument("--workload", default="vb",
-                    choices=["vb", "sk", "vb_batch", "sk_batch", "rrbg", "e6", "vb_windows"],
+                    choices=["vb", "sk", "vb_batch", "sk_batch", "rrbg", "e6", "vb_windows",
+                             "aging"],
                     help="vb: the headline bit-packed Viana-Bray line; sk: the SK blocked line; "
                          "vb_batch: the uneven batch of Viana-Bray graphs; sk_batch: the uneven "
                          "batch of SK samples; rrbg: the paper's bipartite regular graph; e6: "
                          "bipartite vs plain regular graphs, C(t_w + t, t_w) at t_w = 4; "
                          "vb_windows: the headline workload measured every sweep into "
-                         "geometric windows")
+                         "geometric windows; aging: the paper's extrapolations at small scale")
+    ap.add_argument("--aging-tmax", type=int, default=2 ** 14, help="last time of the aging run")
     ap.add_argument("--e6-tmax", type=int, default=4 + 2 ** 16, help="last time of the e6 curves")
     ap.add_argument("--batch", type=int, default=512, help="graphs in the vb_batch workload")
     ap.add_argument("--sk-block", type=int, default=SK_B)
@@ -799,6 +863,8 @@ def main():
         return run_e6(args)
     if args.workload == "vb_windows":
         return run_vb_windows(args)
+    if args.workload == "aging":
+        return run_aging(args)
     return run_gpu(args)
 
 

@@ -7,7 +7,7 @@ import bench
 
 
 def test_every_dispatch_target_exists():
-    for name in ("run_gpu", "run_sk", "run_vb_batch", "run_sk_batch", "run_rrbg", "run_e6", "run_vb_windows",
+    for name in ("run_gpu", "run_sk", "run_vb_batch", "run_sk_batch", "run_rrbg", "run_e6", "run_vb_windows", "run_aging",
                  "run_reference", "run_profile_case", "main"):
         assert callable(getattr(bench, name, None)), name
 
