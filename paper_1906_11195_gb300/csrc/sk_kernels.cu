@@ -282,11 +282,15 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, int kw) {
 // --------------------------------------------------------------------------------------------
 constexpr uint32_t kWaitPolls = 1u << 24;
 
+// NTC: the replica tile NT fixed at compile time (64 or 128: the epilogue is then straight-line
+// code), or 0 to take it from the argument nt
+template <int NTC>
 __global__ void __launch_bounds__(128, 1) k_sk_field_mma(const __grid_constant__ CUtensorMap mapJ,
                                                       const __grid_constant__ CUtensorMap mapD,
-                                                      SkDev d, int b0, int B, int kw, int NT,
+                                                      SkDev d, int b0, int B, int kw, int nt,
                                                       int scale, int skip0, int skip1,
                                                       int atomic_add) {
+    const int NT = NTC ? NTC : nt;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte aligned operand area
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -435,8 +439,15 @@ int sk_field_update_rows(const SkDev& d, const CUtensorMap& mapJ, const CUtensor
     if (n <= 0) return 0;
     const size_t smem = sk_field_smem_bytes(B, kw, NT);
     dim3 grid((unsigned)n, (unsigned)(d.R / NT));
-    k_sk_field_mma<<<grid, 128, smem, st>>>(mapJ, mapD, d, b0, B, kw, NT, scale, skip0, skip1,
-                                            atomic_add);
+    if (NT == 64)
+        k_sk_field_mma<64><<<grid, 128, smem, st>>>(mapJ, mapD, d, b0, B, kw, NT, scale, skip0,
+                                                    skip1, atomic_add);
+    else if (NT == 128)
+        k_sk_field_mma<128><<<grid, 128, smem, st>>>(mapJ, mapD, d, b0, B, kw, NT, scale, skip0,
+                                                     skip1, atomic_add);
+    else
+        k_sk_field_mma<0><<<grid, 128, smem, st>>>(mapJ, mapD, d, b0, B, kw, NT, scale, skip0,
+                                                   skip1, atomic_add);
     return 1;
 }
 
@@ -451,9 +462,10 @@ static int g_field_smem_limit = 0;
 int sk_field_prepare(int B, int kw, int NT) {
     const int need = (int)sk_field_smem_bytes(B, kw, NT);
     if (need <= g_field_smem_limit) return 0;
-    const cudaError_t e = cudaFuncSetAttribute(k_sk_field_mma,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, need);
-    if (e != cudaSuccess) return -1;
+    for (auto kern : {k_sk_field_mma<0>, k_sk_field_mma<64>, k_sk_field_mma<128>})
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, need) !=
+            cudaSuccess)
+            return -1;
     g_field_smem_limit = need;
     return 0;
 }
