@@ -296,10 +296,10 @@ public:
             }
         }
         if (R >= 2) {
-            VbCountJob j{1, 0, Qb + u, (int64_t)(R / 2) * Lc_ * ncol, (int64_t)Lc_ * ncol, ncol};
+            VbCountJob j{1, 0, Qb + u, (int64_t)(R / 2) * Lc_ * ncol, (int64_t)Lc_ * ncol, ncol, 0};
             run_job(j, st);
         }
-        VbCountJob j{2, 0, Eb + u, (int64_t)R * Lc_ * ncol, (int64_t)Lc_ * ncol, ncol};
+        VbCountJob j{2, 0, Eb + u, (int64_t)R * Lc_ * ncol, (int64_t)Lc_ * ncol, ncol, 0};
         run_job(j, st);
     }
 
@@ -355,14 +355,14 @@ public:
         check_cuda(cudaMemsetAsync(mE_, 0, nmE() * 8, st), "memset");
         for (int64_t w = 0; w < ntw; ++w) {
             if (tw[w] > tau) break;
-            VbCountJob j{0, (int)w, mC_ + w, (int64_t)R * Lc_ * ntw, (int64_t)Lc_ * ntw, ntw};
+            VbCountJob j{0, (int)w, mC_ + w, (int64_t)R * Lc_ * ntw, (int64_t)Lc_ * ntw, ntw, 0};
             run_job(j, st);
         }
         if (R >= 2) {
-            VbCountJob j{1, 0, mQ_, (int64_t)(R / 2) * Lc_, (int64_t)Lc_, 1};
+            VbCountJob j{1, 0, mQ_, (int64_t)(R / 2) * Lc_, (int64_t)Lc_, 1, 0};
             run_job(j, st);
         }
-        VbCountJob j{2, 0, mE_, (int64_t)R * Lc_, (int64_t)Lc_, 1};
+        VbCountJob j{2, 0, mE_, (int64_t)R * Lc_, (int64_t)Lc_, 1, 0};
         run_job(j, st);
     }
 
