@@ -91,12 +91,28 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t phas
     return ok != 0;
 }
 
-// wait bounded in time: false if the phase did not complete within budget_ns (global timer)
+// non-blocking test of a phase
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// wait bounded in time: false if the phase did not complete within budget_ns (global timer);
+// a zero budget only tests the phase once, without waiting
 __device__ __forceinline__ bool mbar_wait_timed(uint64_t* bar, uint32_t phase, uint64_t budget_ns) {
+    if (budget_ns == 0) return mbar_test_wait(bar, phase);
     if (mbar_try_wait(bar, phase)) return true;
     const uint64_t t0 = global_ns();
+    const uint32_t hint = budget_ns < 1000000ull ? (uint32_t)budget_ns : 1000000u;
     for (;;) {
-        if (mbar_try_wait_sleep(bar, phase, 1000000u)) return true;
+        if (mbar_try_wait_sleep(bar, phase, hint)) return true;
         if (global_ns() - t0 > budget_ns) return false;
     }
 }
@@ -165,6 +181,7 @@ struct VbPackedDev {
     int32_t n_slices;
     int32_t R;
     int32_t n_colours;
+    uint64_t stage_wait_ns;      // bound of one pipeline wait in the colour kernel
 };
 
 constexpr int kVbMaxColours = 64;  // greedy colouring with degree <= 63

@@ -533,6 +533,10 @@ private:
             pk_.n_slices = (int32_t)(n_slots_ / 32);
             pk_.R = R;
             pk_.n_colours = (int32_t)colour_group_.size() - 1;
+            // SG_TEST_STAGE_WAIT_NS shortens the colour kernel's pipeline waits: a test of the
+            // timeout path (the kernel gives up, flags SG_ETIMEOUT and exits cleanly)
+            pk_.stage_wait_ns = 2000000000ull;
+            if (const char* w = getenv("SG_TEST_STAGE_WAIT_NS")) pk_.stage_wait_ns = strtoull(w, nullptr, 10);
             if (pk_.n_colours > kVbMaxColours) fail(SG_EINVAL, "more colour classes than supported");
         } else {
             const Graph& g = graphs_[0];

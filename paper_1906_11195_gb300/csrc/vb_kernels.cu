@@ -276,7 +276,10 @@ __device__ __forceinline__ void count_and_flip_narrow(SpinWords<R>& si, const ui
     }
 }
 
-constexpr uint64_t kStageWaitNs = 2000000000ull;  // 2 s: a stage is late only if something broke
+// 2 s: a stage is late only if something broke.  The pipeline waits use the handle's
+// d.stage_wait_ns (this value unless a test shortens it); the drains before a CTA exits always
+// use this one, so no copy can still be landing when the CTA is gone.
+constexpr uint64_t kStageWaitNs = 2000000000ull;
 
 template <int R>
 __device__ __forceinline__ void gather_async(uint64_t* dst, const uint64_t* src, uint64_t pol) {
@@ -499,7 +502,7 @@ __global__ void __launch_bounds__(32 * (kGroupSlices + 1))
                 }
                 const int s = (int)(k % NSS);
                 if (k >= (uint32_t)NSS &&
-                    !mbar_wait_timed(&empty[s], ((k / NSS) - 1) & 1u, kStageWaitNs)) {
+                    !mbar_wait_timed(&empty[s], ((k / NSS) - 1) & 1u, d.stage_wait_ns)) {
                     atomicOr(d.err, 4);
                     break;
                 }
@@ -539,8 +542,8 @@ __global__ void __launch_bounds__(32 * (kGroupSlices + 1))
     auto gathers = [&](uint32_t k, uint32_t k_end) -> bool {
         if (k < k_end) {
             const int s = (int)(k % NSS), b = (int)(k % NG);
-            if (!mbar_wait_timed(&full[s], (k / NSS) & 1u, kStageWaitNs)) return false;
-            if (k >= (uint32_t)NG && !mbar_wait_timed(&gfree[b], ((k / NG) - 1) & 1u, kStageWaitNs))
+            if (!mbar_wait_timed(&full[s], (k / NSS) & 1u, d.stage_wait_ns)) return false;
+            if (k >= (uint32_t)NG && !mbar_wait_timed(&gfree[b], ((k / NG) - 1) & 1u, d.stage_wait_ns))
                 return false;
             const uint4 gi = stream[s].gi;
             const uint32_t nsl = gi.y & ~kWideGroup;
@@ -571,7 +574,7 @@ __global__ void __launch_bounds__(32 * (kGroupSlices + 1))
     bool ok = true;
     int kmin_next[R];
     if (n_mine) {
-        ok = __all_sync(0xFFFFFFFFu, mbar_wait_timed(&full[0], 0u, kStageWaitNs));
+        ok = __all_sync(0xFFFFFFFFu, mbar_wait_timed(&full[0], 0u, d.stage_wait_ns));
         if (ok) acceptance<R>(stream[0], warp, lane, t, kmin_next);
     }
     for (uint32_t j = 0; j < nc; ++j) {
@@ -595,7 +598,7 @@ __global__ void __launch_bounds__(32 * (kGroupSlices + 1))
                 const uint32_t kn = k + 1;
                 if (kn >= ke)
                     ok = __all_sync(0xFFFFFFFFu, mbar_wait_timed(&full[kn % NSS], (kn / NSS) & 1u,
-                                                           kStageWaitNs));
+                                                           d.stage_wait_ns));
                 if (ok) acceptance<R>(stream[kn % NSS], warp, lane, t, kmin_next);
             }
             asm volatile("cp.async.wait_group %0;" ::"n"(L) : "memory");
