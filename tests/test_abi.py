@@ -170,3 +170,15 @@ def test_windows_are_validated_and_grow_the_workspace(lib):
         sg.sg_read_windows(h, 3)
     assert e.value.code == sg.SG_ESTATE
     sg.sg_destroy(h)
+
+
+def test_undersized_workspace_is_rejected_before_use(lib):
+    """sg_attach checks the size first: a workspace one byte short is SG_ENOMEM, and the pointer
+    is never dereferenced (a dummy address suffices on a machine without a GPU)."""
+    g = _graph()
+    h = sg.sg_create_vb([g], 64, 2, sg.SG_VB_PACKED, [0], [0, 1])
+    need = sg.sg_workspace_bytes(h)
+    with pytest.raises(sg.SGError) as e:
+        sg.sg_attach(h, 1 << 20, need - 1, 0)
+    assert e.value.code == sg.SG_ENOMEM
+    sg.sg_destroy(h)
