@@ -559,8 +559,10 @@ def run_sk(args):
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
+    R = args.sk_replicas
+
     def timed(block):
-        run = sg.SKRun(J, [SK_T] * SK_R, 1, kernel=sg.SG_SK_BLOCKED, block=block)
+        run = sg.SKRun(J, [SK_T] * R, 1, kernel=sg.SG_SK_BLOCKED, block=block)
         run.sweep(args.warmup)
         torch.cuda.synchronize()
         l0 = run.launches
@@ -577,10 +579,10 @@ def run_sk(args):
         return ms, launches
 
     ms, launches = timed(args.sk_block)
-    flops = 2.0 * SK_N * SK_N * SK_R  # field update per sweep (all rows, all blocks)
+    flops = 2.0 * SK_N * SK_N * R  # field update per sweep (all rows, all blocks)
     out = {"metric": "spin updates/ns", "unit": "spin updates/ns",
-           "config": {"workload": f"sk_blocked_N{SK_N}_R{SK_R}_T{SK_T}_B{args.sk_block}"},
-           "value": SK_N * SK_R / (ms * 1e6), "ms_per_step": ms, "steps": args.steps,
+           "config": {"workload": f"sk_blocked_N{SK_N}_R{R}_T{SK_T}_B{args.sk_block}"},
+           "value": SK_N * R / (ms * 1e6), "ms_per_step": ms, "steps": args.steps,
            "warmup": args.warmup, "gpu_launches": launches,
            "field_gemm_tflops_over_sweep": flops / (ms * 1e-3) / 1e12}
     others = {}
@@ -589,10 +591,10 @@ def run_sk(args):
             continue
         bms, _ = timed(b)
         others["autotuned" if b == 0 else f"B{b}"] = {
-            "value": SK_N * SK_R / (bms * 1e6), "ms_per_step": bms}
+            "value": SK_N * R / (bms * 1e6), "ms_per_step": bms}
     out["other_blocks"] = others
     if not args.skip_plain:
-        pr = sg.SKRun(J, [SK_T] * SK_R, 1, kernel=sg.SG_SK_PLAIN)
+        pr = sg.SKRun(J, [SK_T] * R, 1, kernel=sg.SG_SK_PLAIN)
         pr.sweep(1)
         torch.cuda.synchronize()
         e0.record(stream)
@@ -601,7 +603,7 @@ def run_sk(args):
         torch.cuda.synchronize()
         pms = e0.elapsed_time(e1) / 2
         pr.close()
-        out["plain_kernel"] = {"value": SK_N * SK_R / (pms * 1e6), "ms_per_sweep": pms}
+        out["plain_kernel"] = {"value": SK_N * R / (pms * 1e6), "ms_per_sweep": pms}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -844,6 +846,8 @@ def main():
     ap.add_argument("--e6-tmax", type=int, default=4 + 2 ** 16, help="last time of the e6 curves")
     ap.add_argument("--batch", type=int, default=512, help="graphs in the vb_batch workload")
     ap.add_argument("--sk-block", type=int, default=SK_B)
+    ap.add_argument("--sk-replicas", type=int, default=SK_R,
+                    help="replicas sharing J in the sk workload (a multiple of 128 above 128)")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warning: fewer than 3 warm-up steps")
