@@ -93,6 +93,20 @@ def test_zero_and_infinite_temperature(T):
     check(J, temps, 3, 10, tw, tm, got)
 
 
+@pytest.mark.parametrize("R,block", [(1024, 512), (512, 128)])
+def test_many_replicas_sharing_couplings(R, block):
+    """Hundreds of replicas on one coupling matrix (several 128-replica tiles of the field GEMM
+    and many in-block CTAs); replicas are independent chains, so the oracle follows a few of
+    them, spread over the tiles."""
+    n = 1000
+    J = sg_inputs.sk_couplings(n, 91)
+    temps = [0.4 + 0.2 * (r % 3) for r in range(R)]
+    tw, tm = sg_inputs.log_schedule([0, 3], 12)
+    got = run_sk(J, temps, 8, sg.SG_SK_BLOCKED, block, 12, tw, tm)
+    for r0 in (0, 130, R // 2 + 4, R - 2):
+        check(J, temps, 8, 12, tw, tm, got, r_first=r0, r_count=2)
+
+
 def test_autotuned_block_with_512_padding():
     """n >= 2048 with block = 0: n is padded to a multiple of 512 and the autotuner may pick
     B = 512 (the ragged last block holds padding spins that never flip)."""
