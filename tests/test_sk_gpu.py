@@ -149,19 +149,20 @@ def test_checkpoint_resume_is_bit_exact():
 
 
 # --------------------------------------------------------------------------------------------
-# full-size workload: N = 8192, 256 replicas sharing J, T = 0.4, B = 128
+# full-size workload: N = 8192, 256 replicas sharing J, T = 0.4, B = 128 (configured) and 512
 # --------------------------------------------------------------------------------------------
 @pytest.fixture(scope="module")
 def sk_big():
     return sg_inputs.sk_couplings(8192, 3)
 
 
-def test_full_size_matches_oracle_on_sampled_replicas(sk_big):
+@pytest.mark.parametrize("block", [128, 512])
+def test_full_size_matches_oracle_on_sampled_replicas(sk_big, block):
     J = sk_big
     R, sweeps = 256, 12
     temps = [0.4] * R
     tw, tm = sg_inputs.log_schedule([0, 3, 8], sweeps)
-    got = run_sk(J, temps, 1, sg.SG_SK_BLOCKED, 128, sweeps, tw, tm)
+    got = run_sk(J, temps, 1, sg.SG_SK_BLOCKED, block, sweeps, tw, tm)
     # replicas are independent chains: the oracle follows a few of them one by one
     for r0 in (0, 2, 126, 254):
         check(J, temps, 1, sweeps, tw, tm, got, r_first=r0, r_count=2)
