@@ -8,18 +8,21 @@
 //
 // Blocked sweep (exact reformulation of the sequential order): the spins are cut into blocks
 // of B.  For block b:
-//   1. in-block kernel: every replica (one warp each) runs the B sequential decisions of the
-//      block on its fields h (exact as of the start of the block) and records the changes
-//      D_j = (s_j' - s_j)/2 in {-1, 0, +1}.  Inside a 32-spin chunk the warp finds the next flip
-//      with a ballot: lanes at or after the resolved prefix evaluate their decision given the
-//      flips found so far (bit-packed couplings, popcount corrections); the first tentative
-//      flip is final, is added, and the rest is re-evaluated.  The number of rounds is the
-//      number of flips in the chunk plus one.
-//   2. field kernel: H[:, R] += 2 J[:, block] D[block, R] for every row, as a tcgen05 tensor-core
+//   1. in-block kernel: every replica (one warp each) first adds the previous block's flips to
+//      the fields of its own rows (popcounts over the bit-packed couplings), then runs the B
+//      sequential decisions of the block and records the changes D_j = (s_j' - s_j)/2 in
+//      {-1, 0, +1}.  Inside a 32-spin chunk the warp finds the next flip with a ballot: lanes
+//      past the last accepted flip evaluate their decision with the fields as they stand; the
+//      lowest tentative flip is final, moves every later lane's k by +-2 (its coupling bit),
+//      and the rest is re-evaluated.  The number of rounds is the number of flips in the chunk
+//      plus one; after the chunk, popcounts update the fields of the block's later chunks.
+//   2. field kernel: H[rows, R] += 2 J[rows, block] D[block, R] for every row but those of the
+//      next block (which the next in-block kernel folds in itself), as a tcgen05 tensor-core
 //      GEMM with e4m3 operands (J = +-1, 0 on the diagonal and in padding; D in {-1,0,1}: all
 //      exact) and an FP32 accumulator in tensor memory that starts from zero for every block,
 //      so partial sums stay below B in magnitude and are exact; the epilogue adds 2*acc to the
-//      int32 fields.  Integer arithmetic makes the result identical to the sequential order.
+//      int32 fields.  It runs on a parallel branch and is needed only two blocks later.
+//      Integer arithmetic makes the result identical to the sequential order.
 #include <cuda.h>
 
 #include "sg_internal.cuh"
