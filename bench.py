@@ -112,10 +112,16 @@ def peaks():
 
 
 def kernel_source_hash():
+    """Hash of the colour kernel's code (comments and layout removed, so a comment edit does
+    not invalidate the recorded traffic, while any code change does)."""
+    import re
     h = hashlib.sha256()
     for f in ("vb_kernels.cu", "sg_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_1906_11195_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1906_11195_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -8,11 +8,12 @@
 //
 // Packed kernel (multispin coding, SI section 2): bit k of a uint64 spin word is lane k (an
 // independent disorder sample); one thread updates one vertex for all 64 lanes and all R
-// replicas.  Per neighbour, x = S_i ^ S_j ^ J marks the unsatisfied lanes; x is added into a
-// bit-sliced counter (6 planes, degree <= 63).  Because thr[m] is non-increasing in m and the
-// random number is shared by the 64 lanes, the accepted set {m <= m*} is a prefix: with
-// m* = #{m in 1..d : r32 < thr[m]}, a lane flips iff d - 2u <= m*, i.e. u >= ceil((d - m*)/2).
-// That is one bit-sliced compare against a per-thread constant.
+// replicas.  Per neighbour, x = S_i ^ S_j ^ J marks the unsatisfied lanes; the x words are
+// summed into a bit-sliced count (an unrolled carry-save adder tree for slices of width <= 8,
+// a ripple counter of up to 6 planes, degree <= 63, otherwise).  Because thr[m] is
+// non-increasing in m and the random number is shared by the 64 lanes, the accepted set
+// {m <= m*} is a prefix: with m* = #{m in 1..d : r32 < thr[m]}, a lane flips iff d - 2u <= m*,
+// i.e. u >= ceil((d - m*)/2): one bit-sliced compare against a per-thread constant.
 #include "sg_internal.cuh"
 
 namespace sg {
