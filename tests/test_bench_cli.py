@@ -24,3 +24,10 @@ def test_reference_arm_prints_one_line(monkeypatch, capsys):
     assert line["higher_is_better"] is True and line["unit"] == "spin updates/ns"
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_all_core_cpu_sample_runs_one_process_per_core():
+    # spawned processes re-import bench; a small graph keeps the sample to a fraction of a second
+    out = bench.cpu_baseline_all_cores(budget_lanes=2, n_verts=1 << 12)
+    assert out["kind"] == "oracle" and out["unit"] == "spin updates/ns"
+    assert out["cores"] >= 1 and out["value"] > 0
