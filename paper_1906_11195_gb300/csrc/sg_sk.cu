@@ -86,7 +86,7 @@ public:
         // couplings
         const int words = Np_ / 32;
         h_J8_.assign((size_t)Np_ * Np_, 0);
-        h_Jbits_.assign((size_t)Np_ * words, 0);
+        h_JbT_.assign((size_t)words * Np_, 0);
         for (int i = 0; i < n; ++i)
             for (int j = 0; j < n; ++j) {
                 const int8_t v = J[(size_t)i * n + j];
@@ -97,7 +97,7 @@ public:
                 if (v != 1 && v != -1) fail(SG_EINVAL, "off-diagonal J must be +-1");
                 if (v != J[(size_t)j * n + i]) fail(SG_EINVAL, "J must be symmetric");
                 h_J8_[(size_t)i * Np_ + j] = v > 0 ? 0x38 : 0xB8;
-                if (v < 0) h_Jbits_[(size_t)i * words + j / 32] |= 1u << (j & 31);
+                if (v < 0) h_JbT_[(size_t)(j / 32) * Np_ + i] |= 1u << (j & 31);
             }
         // threshold tables, one per distinct temperature
         std::map<double, int> idx;
@@ -136,7 +136,7 @@ public:
         auto up = [&](void* dst, const void* src, size_t bytes) {
             if (bytes) check_cuda(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), "H2D copy");
         };
-        up((void*)d_.Jbits, h_Jbits_.data(), h_Jbits_.size() * 4);
+        up((void*)d_.JbT, h_JbT_.data(), h_JbT_.size() * 4);
         up((void*)d_.J8, h_J8_.data(), h_J8_.size());
         up((void*)d_.thr, h_thr_.data(), h_thr_.size() * 4);
         up((void*)d_.temp_index, h_tidx_.data(), h_tidx_.size() * 4);
@@ -432,7 +432,7 @@ private:
     void carve(Carver& c) {
         const int words = Np_ / 32;
         clock_dev = c.take<uint32_t>(1);
-        d_.Jbits = c.take<uint32_t>(h_Jbits_.size());
+        d_.JbT = c.take<uint32_t>(h_JbT_.size());
         d_.J8 = c.take<uint8_t>(h_J8_.size());
         d_.thr = c.take<uint32_t>(h_thr_.size());
         d_.temp_index = c.take<int32_t>(h_tidx_.size());
@@ -467,7 +467,7 @@ private:
     int n_ = 0, Np_ = 0, B_ = 128, kw_ = 128, NT_ = 128;
     uint64_t seed_ = 0;
     std::vector<uint8_t> h_J8_;
-    std::vector<uint32_t> h_Jbits_, h_thr_;
+    std::vector<uint32_t> h_JbT_, h_thr_;
     std::vector<int32_t> h_tidx_;
     std::vector<float> h_coef_;
     SkDev d_{};

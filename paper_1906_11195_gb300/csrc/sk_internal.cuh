@@ -9,7 +9,7 @@ namespace sg {
 
 // One SK sample, spins padded to Np (a multiple of 128 and of the block size).
 struct SkDev {
-    const uint32_t* Jbits;    // [Np][Np/32] bit j%32 of word j/32 of row i: J_ij = -1
+    const uint32_t* JbT;      // [Np/32][Np] bit j%32 of word j/32 of row i, at (j/32)*Np + i: J_ij = -1
     const uint8_t* J8;        // [Np][Np] e4m3: +1 = 0x38, -1 = 0xB8, 0 on the diagonal/padding
     const uint32_t* thr;      // [n_temps][N] thresholds (entry k)
     const int32_t* temp_index;// [R] row of thr used by replica r

@@ -106,23 +106,30 @@ int sk_kstar_sweep(const SkDev& d, const uint32_t* clock, uint32_t t_off, cudaSt
 // --------------------------------------------------------------------------------------------
 // in-block sequential update, one warp per replica.  The CTA stages the couplings of the
 // block's rows with the block's own columns (and, when prev_b0 >= 0, with the previous block's
-// columns) in shared memory; its 8 replicas share them.
+// columns) in shared memory; its 8 replicas share them.  The couplings are stored column-word
+// major (JbT[w][i] = word w of row i), so the block's rows of one column word are one
+// contiguous run: a single thread stages them with one bulk copy per word, and in shared memory
+// ([word][row]) the 32 lanes of a warp (32 consecutive rows) read 32 consecutive words, one
+// per bank.
 // When prev_b0 >= 0 the kernel first adds the previous block's flips to the fields of its own
 // rows (popcounts over bit-packed couplings, written back to H): that update is on the
 // sequential critical path, while the tensor-core update of every other row runs elsewhere.
 // --------------------------------------------------------------------------------------------
+// 2 s: the coupling copies of a launch are late only if something broke
+constexpr uint64_t kSkStageWaitNs = 2000000000ull;
+
 template <int NC>
 __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0, int prev_b0) {
     static_assert(NC == 2 || NC == 4 || NC == 8 || NC == 16, "B = 64, 128, 256 or 512");
-    // [32 * NC rows][2 * NC words + 1]: own cols, previous cols; the odd row stride keeps the
-    // 32 lanes (32 consecutive rows) on 32 different banks
-    extern __shared__ uint32_t jblk[];
-    constexpr int W = 2 * NC + 1;
+    // [2 * NC words][B rows]: own column words 0..NC-1, then the previous block's
+    extern __shared__ __align__(128) uint32_t jblk[];
+    __shared__ __align__(8) uint64_t jbar;
+    constexpr int B = 32 * NC;
     const int lane = threadIdx.x & 31;
     const int words = d.Np / 32;
     const int wb = b0 / 32;
     const int pwb = prev_b0 >= 0 ? prev_b0 / 32 : 0;
-    const int nw = prev_b0 >= 0 ? 2 * NC : NC;  // words staged per row
+    const int nw = prev_b0 >= 0 ? 2 * NC : NC;  // column words staged
     // A programmatic launch after the previous block's in-block kernel: let the next block's
     // kernel start its own prologue now (it reads nothing of ours before its dependency wait).
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -130,21 +137,18 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0, int prev_b0
     const bool active = r < d.R;
     // Prologue on data no in-block kernel writes (couplings, the sweep's K* table): may run
     // while the previous block is still being updated.
+    if (threadIdx.x == 0) {
+        mbar_init(&jbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_expect_tx(&jbar, (uint32_t)(nw * B * 4));
+        for (int w = 0; w < nw; ++w) {
+            const int cw = w < NC ? wb + w : pwb + (w - NC);
+            bulk_copy_g2s(jblk + w * B, d.JbT + (int64_t)cw * d.Np + b0, B * 4, &jbar);
+        }
+    }
     int kst[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) kst[c] = active ? d.kst[(int64_t)r * d.Np + b0 + 32 * c + lane] : 0;
-    // the block's coupling bits (own columns, previous block's columns) land in shared memory
-    // through asynchronous copies, all in flight together
-    // nw is NC or 2 NC, a power of two: row and word by shift and mask
-    const int nw_log = (prev_b0 >= 0 ? 1 : 0) + (NC == 2 ? 1 : NC == 4 ? 2 : NC == 8 ? 3 : 4);
-    for (int k = threadIdx.x; k < 32 * NC * nw; k += blockDim.x) {
-        const int row = k >> nw_log, w = k & (nw - 1);
-        const int col_word = w < NC ? wb + w : pwb + (w - NC);
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(&jblk[row * W + w])),
-                     "l"(d.Jbits + (int64_t)(b0 + row) * words + col_word)
-                     : "memory");
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
     // Everything below depends on the previous block (spins, flips, fields): wait until that
     // kernel has completed and its writes are visible (immediate for a plain launch).
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -159,8 +163,13 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0, int prev_b0
         pF[c] = pv ? d.flips[(int64_t)r * words + pwb + c] : 0u;
         psn[c] = pv ? d.S[(int64_t)r * words + pwb + c] : 0u;
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncthreads();
+    __syncthreads();  // the barrier's initialisation is visible to every thread
+    if (!mbar_wait_timed(&jbar, 0u, kSkStageWaitNs)) {
+        // no thread leaves while a copy may still be landing in shared memory
+        mbar_wait_timed(&jbar, 0u, kSkStageWaitNs);
+        atomicOr(d.err, 4);
+        return;
+    }
     if (!active) return;
     if (prev_b0 >= 0) {
         // fields += 2 sum_{j flipped in the previous block} J_ij s_j'
@@ -175,7 +184,7 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0, int prev_b0
             const int pf = __popc(F);
 #pragma unroll
             for (int c = 0; c < NC; ++c)
-                dh[c] += 2 * (pf - 2 * __popc(F & (jblk[(32 * c + lane) * W + NC + cp] ^ sn)));
+                dh[c] += 2 * (pf - 2 * __popc(F & (jblk[(NC + cp) * B + 32 * c + lane] ^ sn)));
         }
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
@@ -188,7 +197,7 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0, int prev_b0
         const int i = b0 + 32 * c + lane;
         const uint32_t sbit = (sw[c] >> lane) & 1u;
         const int x = sbit ? -h[c] : h[c];
-        const uint32_t neg = jblk[(32 * c + lane) * W + c] ^ sw[c] ^ (sbit ? 0xFFFFFFFFu : 0u);
+        const uint32_t neg = jblk[c * B + 32 * c + lane] ^ sw[c] ^ (sbit ? 0xFFFFFFFFu : 0u);
         // Resolve the chunk's 32 sequential decisions: every lane past the last accepted flip
         // decides with the fields as they stand; the lowest lane that flips is accepted (the
         // lanes below it keep their decision), its flip moves every later lane's k by +2 or -2 (by
@@ -217,7 +226,7 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0, int prev_b0
             const int pf = __popc(F);
 #pragma unroll
             for (int c2 = c + 1; c2 < NC; ++c2) {
-                const uint32_t m = jblk[(32 * c2 + lane) * W + c] ^ nsw;
+                const uint32_t m = jblk[c * B + 32 * c2 + lane] ^ nsw;
                 h[c2] += 2 * (pf - 2 * __popc(F & m));
             }
         }
@@ -239,7 +248,7 @@ int sk_inblock(const SkDev& d, int b0, int prev_b0, int B, bool after_inblock, c
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nb);
     cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = (size_t)32 * nc * (2 * nc + 1) * 4;
+    cfg.dynamicSmemBytes = (size_t)32 * nc * (2 * nc) * 4;
     cfg.stream = st;
     // directly after the previous block's in-block kernel: programmatic dependent launch, so
     // the launch and the prologue overlap that kernel
@@ -254,7 +263,7 @@ int sk_inblock(const SkDev& d, int b0, int prev_b0, int B, bool after_inblock, c
 int sk_inblock_prepare() {
     const cudaError_t e = cudaFuncSetAttribute(k_sk_inblock<16>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               32 * 16 * 33 * 4);
+                                               32 * 16 * 32 * 4);
     return e == cudaSuccess ? 0 : -1;
 }
 
