@@ -6,6 +6,7 @@
 // (SI section 1); the blocked kernel reproduces that order exactly (see sk_kernels.cu).
 #include <cudaTypedefs.h>
 #include <math.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <map>
@@ -448,6 +449,14 @@ private:
         d_.N = n_;
         d_.Np = Np_;
         d_.R = R;
+        // replica warps per in-block CTA: 4 spreads the replicas over twice the SMs of 8 and
+        // measured faster (the per-replica decision chain has fewer warps beside it on each
+        // scheduler); SG_SK_INBLOCK_WARPS = 2, 4 or 8 pins a split (results never change)
+        {
+            const char* e = getenv("SG_SK_INBLOCK_WARPS");
+            const int v = e ? atoi(e) : 4;
+            d_.inblock_warps = (v == 2 || v == 4 || v == 8) ? v : 4;
+        }
         dC_ = c.take<int64_t>(nC());
         dQ_ = c.take<int64_t>(nQ());
         dE_ = c.take<int64_t>(nE());

@@ -23,6 +23,7 @@ struct SkDev {
     int* err;                 // device status word
     uint64_t seed;
     int32_t N, Np, R;
+    int32_t inblock_warps;    // replica warps per in-block CTA (2, 4 or 8)
 };
 
 int sk_init(const SkDev& d, cudaStream_t st);

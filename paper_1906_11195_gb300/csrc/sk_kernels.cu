@@ -106,11 +106,11 @@ int sk_kstar_sweep(const SkDev& d, const uint32_t* clock, uint32_t t_off, cudaSt
 // --------------------------------------------------------------------------------------------
 // in-block sequential update, one warp per replica.  The CTA stages the couplings of the
 // block's rows with the block's own columns (and, when prev_b0 >= 0, with the previous block's
-// columns) in shared memory; its 8 replicas share them.  The couplings are stored column-word
-// major (JbT[w][i] = word w of row i), so the block's rows of one column word are one
-// contiguous run: a single thread stages them with one bulk copy per word, and in shared memory
-// ([word][row]) the 32 lanes of a warp (32 consecutive rows) read 32 consecutive words, one
-// per bank.
+// columns) in shared memory; its replicas (2, 4 or 8 warps) share them.  The couplings are
+// stored column-word major (JbT[w][i] = word w of row i), so the block's rows of one column
+// word are one contiguous run: a single thread stages them with one bulk copy per word, and in
+// shared memory ([word][row]) the 32 lanes of a warp (32 consecutive rows) read 32 consecutive
+// words, one per bank.
 // When prev_b0 >= 0 the kernel first adds the previous block's flips to the fields of its own
 // rows (popcounts over bit-packed couplings, written back to H): that update is on the
 // sequential critical path, while the tensor-core update of every other row runs elsewhere.
@@ -235,7 +235,8 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0, int prev_b0
 }
 
 int sk_inblock(const SkDev& d, int b0, int prev_b0, int B, bool after_inblock, cudaStream_t st) {
-    const unsigned nb = (unsigned)((d.R + 7) / 8);
+    const int wpc = d.inblock_warps > 0 ? d.inblock_warps : 4;
+    const unsigned nb = (unsigned)((d.R + wpc - 1) / wpc);
     const int nc = B / 32;
     void (*kern)(SkDev, int, int) = nullptr;
     switch (nc) {
@@ -247,7 +248,7 @@ int sk_inblock(const SkDev& d, int b0, int prev_b0, int B, bool after_inblock, c
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nb);
-    cfg.blockDim = dim3(256);
+    cfg.blockDim = dim3(32 * wpc);
     cfg.dynamicSmemBytes = (size_t)32 * nc * (2 * nc) * 4;
     cfg.stream = st;
     // directly after the previous block's in-block kernel: programmatic dependent launch, so

@@ -62,6 +62,18 @@ def test_blocked_matches_oracle(n, R, block):
     check(J, temps, 5 + n, 24, tw, tm, got)
 
 
+@pytest.mark.parametrize("warps", [2, 4, 8])
+@pytest.mark.parametrize("n,R,block", [(700, 16, 512), (300, 48, 128)])
+def test_inblock_replica_split_matches_oracle(monkeypatch, warps, n, R, block):
+    # replicas per in-block CTA (the blocked kernel takes R in multiples of 16)
+    monkeypatch.setenv("SG_SK_INBLOCK_WARPS", str(warps))
+    J = sg_inputs.sk_couplings(n, 70 + n)
+    temps = [0.4 + 0.05 * r for r in range(R)]
+    tw, tm = sg_inputs.log_schedule([0, 3], 16)
+    got = run_sk(J, temps, 11 + warps, sg.SG_SK_BLOCKED, block, 16, tw, tm)
+    check(J, temps, 11 + warps, 16, tw, tm, got)
+
+
 @pytest.mark.parametrize("n,R", [(200, 8), (333, 5), (64, 2)])
 def test_plain_matches_oracle(n, R):
     J = sg_inputs.sk_couplings(n, 60 + n)
