@@ -686,17 +686,20 @@ static int colour_launch_v(const VbPackedDev& d, uint32_t c_begin, uint32_t c_en
 
 // pipeline shapes (the handle's autotuner picks one; none changes the results), as
 // (stream stages, gather buffers, gather lookahead, CTAs per SM):
-//   R = 1, 2: variant 0 (3, 2, 1, 2), variant 1 (4, 2, 1, 2), variant 2 (2, 2, 1, 3)
-//   R = 4:    variant 0 (4, 2, 1, 1), variant 1 (2, 2, 1, 2), variant 2 (3, 2, 1, 1)
+//   R = 1, 2: variant 0 (3, 3, 1, 2), variant 1 (4, 2, 1, 2), variant 2 (2, 2, 1, 3)
+//   R = 4:    variant 0 (4, 2, 1, 1), variant 1 (2, 2, 1, 2), variant 2 (3, 3, 1, 1)
+// With three gather buffers and gathers one group ahead, the buffer a warp fills for group
+// k + 1 was last read for group k - 2, which every warp finished an iteration earlier: no warp
+// waits for the slowest warp of the previous group before starting its gathers.
 template <int R>
 static int colour_launch(const VbPackedDev& d, uint32_t c_begin, uint32_t c_end, uint32_t ng,
                          const uint32_t* clock, uint32_t t_off, int variant, cudaStream_t st) {
     if constexpr (R == 4) {
         if (variant == 0) return colour_launch_v<R, 4, 2, 1>(d, c_begin, c_end, ng, clock, t_off, 1, st);
         if (variant == 1) return colour_launch_v<R, 2, 2, 1>(d, c_begin, c_end, ng, clock, t_off, 2, st);
-        return colour_launch_v<R, 3, 2, 1>(d, c_begin, c_end, ng, clock, t_off, 1, st);
+        return colour_launch_v<R, 3, 3, 1>(d, c_begin, c_end, ng, clock, t_off, 1, st);
     } else {
-        if (variant == 0) return colour_launch_v<R, 3, 2, 1>(d, c_begin, c_end, ng, clock, t_off, 2, st);
+        if (variant == 0) return colour_launch_v<R, 3, 3, 1>(d, c_begin, c_end, ng, clock, t_off, 2, st);
         if (variant == 1) return colour_launch_v<R, 4, 2, 1>(d, c_begin, c_end, ng, clock, t_off, 2, st);
         return colour_launch_v<R, 2, 2, 1>(d, c_begin, c_end, ng, clock, t_off, 3, st);
     }
