@@ -17,10 +17,11 @@ later step.  Each run must finish (no deadlock), and every step must respect:
     has been written (all CTAs) and completes before any update of a class > c is written.
 
 Planted protocol mistakes in the model (no gather-buffer wait, no grid barrier) must be caught.
-Two forms of a launch running several sweeps (which the kernel does not do) show why that needs
-more than the ring waits: holding the next sweep's first stage until the previous sweep's last
-group is released deadlocks against the consumers' look at that stage, and the ring waits alone
-can stage a group's own words before the previous sweep wrote them.  The model checks the design
+Forms of a launch running several sweeps (which the kernel does not do) show what that needs
+beyond the ring waits: holding the next sweep's first stage until the previous sweep's last
+group is released deadlocks against the consumers' look at that stage; the ring waits alone can
+stage a group's own words before the previous sweep wrote them; waiting for the release of the
+same group in the previous sweep keeps every order when each CTA owns at least two groups.  The model checks the design
 of the waits, not the CUDA code itself.
 """
 import random
@@ -116,6 +117,11 @@ class Sim:
                 yield lambda k=k, s=s: c["empty"][s].done(k // NSS - 1)
             if self.mutant == "hold_next_sweep" and k > 0 and k % c["n_mine"] == 0:
                 kp = k - 1
+                yield lambda kp=kp: c["empty"][kp % NSS].done(kp // NSS)
+            if self.mutant == "own_word_wait" and k >= c["n_mine"] and c["n_mine"] < NSS:
+                # wait for the release of the same group in the previous sweep, which is more
+                # recent than the ring's own k - NSS
+                kp = k - c["n_mine"]
                 yield lambda kp=kp: c["empty"][kp % NSS].done(kp // NSS)
             # refill stage s with group k: every consumer must have released group k - NSS
             if k >= NSS and c["released"].get(k - NSS, 0) != self.W:
@@ -283,6 +289,22 @@ def test_multi_sweep_launch_with_held_first_stage_deadlocks():
     # stage to compute its acceptance: the waits form a cycle
     with pytest.raises(ProtocolError, match="deadlock"):
         Sim(1, 2, 3, 3, 1, [4, 3], 0, sweeps=2, mutant="hold_next_sweep").run()
+
+
+def test_multi_sweep_launch_with_own_word_wait_is_consistent():
+    # the form to use: the producer also waits for the release of the same group in the previous
+    # sweep; with at least two groups per CTA it keeps every order and finishes (the memory
+    # fences the own-word copies need on the GPU are outside the model)
+    for layout, grid in (([2, 2, 1], 2), ([5, 3, 1], 2), ([3, 3], 3), ([9, 1, 1], 4)):
+        for seed in range(25):
+            Sim(grid, 2, 3, 3, 1, layout, seed, sweeps=3, mutant="own_word_wait").run()
+
+
+def test_multi_sweep_launch_with_one_group_per_cta_deadlocks():
+    # one group per CTA: the group's own previous-sweep release is the one its consumers hold
+    # while they look at the next sweep's first stage
+    with pytest.raises(ProtocolError, match="deadlock"):
+        Sim(2, 2, 3, 3, 1, [2, 1], 0, sweeps=2, mutant="own_word_wait").run()  # CTA 1: one group
 
 
 def test_multi_sweep_launch_with_ring_waits_only_stages_stale_own_words():
