@@ -255,7 +255,8 @@ class Sim:
                     raise ProtocolError(f"gather of class {cls} landed after an update of class {c_w} was written")
 
 
-SHAPES = [(3, 3, 1), (4, 2, 1), (2, 2, 1), (3, 2, 1)]  # (stream stages, gather buffers, lookahead)
+# (stream stages, gather buffers, lookahead): the kernel's shapes, then two it could take
+SHAPES = [(3, 3, 1), (4, 2, 1), (2, 2, 1), (4, 3, 1), (4, 3, 2)]
 LAYOUTS = [
     [7, 5, 3, 1],        # classes shrinking to a one-group tail
     [2, 9, 0, 4],        # an empty class
