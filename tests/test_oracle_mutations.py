@@ -20,6 +20,10 @@ VB_MUTATIONS = {
     "sweep_not_in_counter": ("draw_word(seed, (uint32_t)i, t,", "draw_word(seed, (uint32_t)i, 0,"),
     "colour_order_reversed": ("for (int32_t c = 0; c < ncol; ++c)", "for (int32_t c = ncol - 1; c >= 0; --c)"),
     "lane_init_high_word_dropped": ("| ((uint64_t)draw_word(seed, (uint32_t)i, 0, (uint32_t)r, 1, 1) << 32);", ";"),
+    # the greedy colouring sets the update order
+    "colour_flags_never_cleared": ("if (cj >= 0 && cj <= maxdeg + 1) used[cj] = 0;", ";"),
+    "colour_skips_last_neighbour": ("for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {\n            int32_t c = colour[col[e]];",
+                                    "for (int32_t e = row_ptr[i]; e + 1 < row_ptr[i + 1]; ++e) {\n            int32_t c = colour[col[e]];"),
 }
 
 SK_MUTATIONS = {
