@@ -84,11 +84,15 @@ typedef struct {
     const double *temps;
 } sg_vb_graph;
 
-/* Message of the last failed call on this thread ("" if none).  Owned by the library. */
+/* Message of the last failed call on this thread ("" if none).  Owned by the library.
+ * Library service; the paper has no counterpart. */
 const char *sg_last_error(void);
 
 /* Create a batch of Viana-Bray instances that evolve in lock-step (one sweep of the batch =
  * one sweep of every graph; the batched persistent form of the uneven workloads).
+ * Defines: the VB model of Eq. 3 on its graph with 64 coupling sets per word (SI section 2,
+ * Table 1), quenched from a random configuration (Methods); the many sizes of Table 1 run as
+ * one batch.
  *   graphs[n_graphs]  the instances (host)
  *   n_lanes           lanes reported in the results, 1..64 (the packed kernel always simulates
  *                     all 64; the plain kernel simulates only these)
@@ -103,7 +107,8 @@ int sg_create_vb(const sg_vb_graph *graphs, int32_t n_graphs, int32_t n_lanes,
                  int32_t n_replicas, int32_t kernel, const int64_t *tw, int32_t n_tw,
                  const int64_t *tm, int32_t n_tm, sg_handle *out);
 
-/* Create an SK instance (Eq. 1; SI section 1).
+/* Create an SK instance (Eq. 1 with binary couplings; SI section 1: fixed-order Metropolis,
+ * R replicas sharing J, the "two clones" of the overlap).
  *   n          spins, 2 <= n <= 32768
  *   J          int8[n*n] row-major couplings (host): +-1 off the diagonal, 0 on it, symmetric
  *   n_replicas R >= 1 replicas sharing J (a multiple of 16 for SG_SK_BLOCKED)
@@ -137,28 +142,47 @@ int sg_create_sk_batch(const sg_sk_sample *samples, int32_t n_samples, int32_t n
                        int32_t kernel, int32_t block, const int64_t *tw, int32_t n_tw,
                        const int64_t *tm, int32_t n_tm, sg_handle *out);
 
-/* Device workspace size the handle needs (bytes). */
+/* Replace the measurement schedule: tw[n_tw] snapshot times and tm[n_tm] measurement times,
+ * each strictly increasing, >= 0 and < 2^32 (as for sg_create_vb).  Before sg_attach any sizes
+ * are allowed (the workspace size follows them).  After sg_attach the schedule can still be
+ * replaced while no scheduled time has been reached yet (no snapshot or measurement taken,
+ * including those at tau = 0) if n_tw and n_tm stay the same (the workspace layout is fixed at
+ * attach) and every new time is later than the current tau; otherwise SG_ESTATE.  Bad arrays:
+ * SG_EINVAL.  Defines: the waiting times t_w and the log-spaced measurement times t_w + t of
+ * the aging protocol (main text, Fig. 1; SI section 3). */
+int sg_set_schedule(sg_handle h, const int64_t *tw, int32_t n_tw, const int64_t *tm,
+                    int32_t n_tm);
+
+/* Device workspace size the handle needs (bytes).  Library service; no counterpart in the
+ * paper. */
 int sg_workspace_bytes(sg_handle h, size_t *bytes);
 
 /* Bind the caller's device workspace and CUDA stream (cudaStream_t, may be NULL for the legacy
  * default stream), copy the instance to the device, draw the initial spins (tau = 0) and take the
- * tau = 0 snapshot/measurement if scheduled.  Returns after the copies have completed. */
+ * tau = 0 snapshot/measurement if scheduled.  Returns after the copies have completed.
+ * Defines: the quench, a random initial configuration at t = 0 (Methods). */
 int sg_attach(sg_handle h, void *dev_workspace, size_t bytes, void *cuda_stream);
 
 /* Advance by n >= 0 sweeps, asynchronously on the handle's stream.  Snapshots and measurements
- * due at the times passed are taken on the device on the way. */
+ * due at the times passed are taken on the device on the way.
+ * Defines: one sweep = one Metropolis visit of every spin, the time unit of every figure
+ * (Methods; SI sections 1-3: colour classes for VB, the fixed order for SK). */
 int sg_sweep(sg_handle h, int64_t n);
 
-/* Current time tau (completed sweeps), as queued. */
+/* Current time tau (completed sweeps), as queued.  The paper's t, in sweeps (Methods). */
 int sg_time(sg_handle h, int64_t *tau);
 
-/* Wait for the handle's queued work; reports device-side errors (SG_ECUDA, SG_ETIMEOUT). */
+/* Wait for the handle's queued work; reports device-side errors (SG_ECUDA, SG_ETIMEOUT).
+ * Library service; no counterpart in the paper. */
 int sg_synchronize(sg_handle h);
 
-/* Shapes of the result arrays: n_inst, n_replicas, n_lanes, n_tw, n_tm (5 int32). */
+/* Shapes of the result arrays: n_inst, n_replicas, n_lanes, n_tw, n_tm (5 int32).
+ * Library service; no counterpart in the paper. */
 int sg_result_shape(sg_handle h, int32_t *shape5);
 
-/* Copy the scheduled measurements to the host (synchronises).  Layouts (int64):
+/* Copy the scheduled measurements to the host (synchronises).  Defines: C(t_w + t, t_w) as in
+ * Eq. formula1 (the sum after Eq. 1), the overlap of the two clones (SI section 1), and the energy
+ * of Eq. 3 / Eq. 1 (SI section 3 measures them at log-spaced times).  Layouts (int64):
  *   C[n_inst][R][L][n_tw][n_tm]  sum_i s_i(tm) s_i(tw) for tw <= tm <= tau, else 0
  *   q[n_inst][R/2][L][n_tm]      sum_i s_i^(2p)(tm) s_i^(2p+1)(tm)
  *   E[n_inst][R][L][n_tm]        VB: sum_{(ij) in E} J_ij s_i s_j;  SK: sum_{i<j} J_ij s_i s_j
@@ -186,49 +210,54 @@ int sg_set_windows(sg_handle h, const int64_t *bounds, int32_t n_bounds);
 int sg_read_windows(sg_handle h, int64_t *C, int64_t *q, int64_t *E, int64_t *n_meas);
 
 /* Measure now, at the current tau, against every snapshot taken so far (synchronises).
+ * Defines: the same observables as sg_read_results (Eq. formula1, SI section 1), at one time.
  * C[n_inst][R][L][n_tw] (0 for snapshots not yet taken), q[n_inst][R/2][L], E[n_inst][R][L]. */
 int sg_measure(sg_handle h, int64_t *C, size_t C_len, int64_t *q, size_t q_len, int64_t *E,
                size_t E_len);
 
-/* Current spins in the caller's vertex order (synchronises).
+/* Current spins in the caller's vertex order (synchronises).  The configuration {s_i} of
+ * Eq. 1 / Eq. 3; the multispin word layout of SI section 2 for VB.
  *   VB: uint64[n_inst][R][n_g] concatenated over graphs, bit k = 1 iff s = -1 in lane k (bits
  *       >= n_lanes are 0 for SG_VB_PLAIN);  SK: int8[R][n] of +-1.
  * bytes must equal the exact size. */
 int sg_get_spins(sg_handle h, void *host_dst, size_t bytes);
 
 /* The acceptance threshold tables in use: VB uint32[n_inst][R][SG_VB_MAX_DEGREE+1] (entry m),
- * SK uint32[R][n] (entry k).  Entry 0 is 2^32-1. */
+ * SK uint32[R][n] (entry k).  Entry 0 is 2^32-1.  Defines: the Metropolis acceptance
+ * min(1, exp(-dE/T)) (Methods) as integer thresholds on a 32-bit random number. */
 int sg_get_thresholds(sg_handle h, uint32_t *dst, size_t len);
 
 /* Checkpoint: the full dynamic state (tau, spins, snapshots, counts) as an opaque host blob.
  * sg_state_bytes gives its size; sg_load_state restores it into an attached handle created
- * from the same instance. */
+ * from the same instance.  Library service (long runs in pieces, as the paper's campaign of
+ * Table 1 needed); the paper describes no checkpoint format. */
 int sg_state_bytes(sg_handle h, size_t *bytes);
 int sg_save_state(sg_handle h, void *host_dst, size_t bytes);
 int sg_load_state(sg_handle h, const void *host_src, size_t bytes);
 
-/* Release the handle (the workspace and stream stay the caller's). */
+/* Release the handle (the workspace and stream stay the caller's).  Library service. */
 int sg_destroy(sg_handle h);
 
-/* Number of kernel launches the handle has queued since creation (for launch accounting). */
+/* Number of kernel launches the handle has queued since creation (for launch accounting).
+ * Library service; no counterpart in the paper. */
 int sg_launch_count(sg_handle h, int64_t *count);
 
 /* SK local fields h[r][i] = sum_j J_ij s[r][j] computed on the tensor cores without allocating
  * any device memory.  The paper has no counterpart: this is a service for callers that cannot
  * allocate device memory where they need the fields -- a host application that fixes the
- * library's memory budget, a plugin whose process owns every device allocation, or code running
- * inside a stream capture, where allocation is not allowed.
+ * library's memory budget, or a plugin whose process owns every device allocation.
  *   J  device int8[n*n], row-major, +-1 off the diagonal, 0 on it, symmetric (not checked here)
  *   s  device int8[n_replicas*n], spins +-1, replica-major
  *   h  device int32[n_replicas*n], output, replica-major
  *   n  2..2048;  n_replicas a multiple of 16 in 16..128;  cuda_stream a cudaStream_t (or NULL)
  * The tensor-core operand images live in one static device array of about 5.3 MiB inside the
  * library (held by every GPU that loads it until the process exits); larger sizes return
- * SG_EINVAL.  The first call on a device looks up that array's device address (make that first
- * call before any stream capture).  Every call reuses the array and clears what must start at
- * zero, so calls that overlap on the GPU (different streams or host threads) race with each
- * other: serialise them.  The call is queued on cuda_stream and returns after it completed;
- * errors are reported like every other call (status code, sg_last_error). */
+ * SG_EINVAL.  J, s and h must be device memory of the current device.  The first call on a
+ * device looks up that array's device address.  Every call reuses the array and clears what must
+ * start at zero, so calls that overlap on the GPU (different streams or host threads) race with
+ * each other: serialise them.  The call is queued on cuda_stream, synchronises that stream and
+ * returns after its work completed; errors are reported like every other call (status code,
+ * sg_last_error). */
 int sg_sk_fields_noalloc(const int8_t *J, const int8_t *s, int32_t n, int32_t n_replicas,
                          int32_t *h, void *cuda_stream);
 

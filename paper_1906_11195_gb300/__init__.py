@@ -37,6 +37,7 @@ EXPORTED = [
     "sg_sweep", "sg_time", "sg_synchronize", "sg_result_shape", "sg_read_results", "sg_measure",
     "sg_get_spins", "sg_get_thresholds", "sg_state_bytes", "sg_save_state", "sg_load_state",
     "sg_destroy", "sg_launch_count", "sg_sk_fields_noalloc", "sg_set_windows", "sg_read_windows",
+    "sg_set_schedule",
 ]
 
 
@@ -98,6 +99,7 @@ def _load():
                 "sg_sk_fields_noalloc": (ctypes.c_int, [P, P, i32, i32, P, P]),
                 "sg_set_windows": (ctypes.c_int, [H, P, i32]),
                 "sg_read_windows": (ctypes.c_int, [H, P, P, P, P]),
+                "sg_set_schedule": (ctypes.c_int, [H, P, i32, P, i32]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -227,6 +229,12 @@ def sg_measure(h):
     return C, q, E
 
 
+def sg_set_schedule(h, tw, tm):
+    """Replace the snapshot times tw and measurement times tm (see sg.h for when this is allowed)."""
+    tw_a, tm_a = _i64(tw), _i64(tm)
+    _check(_load().sg_set_schedule(h, _p(tw_a), int(tw_a.size), _p(tm_a), int(tm_a.size)))
+
+
 def sg_set_windows(h, bounds):
     b = _i64(bounds)
     _check(_load().sg_set_windows(h, _p(b), int(b.size)))
@@ -329,6 +337,10 @@ class _Run:
 
     def measure(self):
         return sg_measure(self.h)
+
+    def set_schedule(self, tw, tm):
+        """Replace the schedule after attach (same sizes, no scheduled time reached yet)."""
+        sg_set_schedule(self.h, tw, tm)
 
     def windows(self):
         """Window sums C, q, E and the measurement counts n_meas (see sg_read_windows)."""

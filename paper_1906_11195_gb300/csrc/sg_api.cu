@@ -228,6 +228,26 @@ int sg_create_sk_batch(const sg_sk_sample* samples, int32_t n_samples, int32_t n
     });
 }
 
+int sg_set_schedule(sg_handle h, const int64_t* tw, int32_t n_tw, const int64_t* tm,
+                    int32_t n_tm) {
+    return guarded([&] {
+        if (!h) sg::fail(SG_EINVAL, "null handle");
+        std::vector<int64_t> a = read_schedule(tw, n_tw, "tw");
+        std::vector<int64_t> b = read_schedule(tm, n_tm, "tm");
+        if (h->attached) {
+            if (h->next_tw > 0 || h->next_tm > 0)
+                sg::fail(SG_ESTATE, "a scheduled time has already been reached");
+            if (a.size() != h->tw.size() || b.size() != h->tm.size())
+                sg::fail(SG_ESTATE, "after sg_attach the schedule must keep n_tw and n_tm");
+            if ((!a.empty() && a.front() <= h->tau) || (!b.empty() && b.front() <= h->tau))
+                sg::fail(SG_ESTATE, "after sg_attach every new time must be later than tau");
+        }
+        h->model->set_schedule(a, b, h->attached);
+        h->tw = std::move(a);
+        h->tm = std::move(b);
+    });
+}
+
 int sg_workspace_bytes(sg_handle h, size_t* bytes) {
     return guarded([&] {
         if (!h || !bytes) sg::fail(SG_EINVAL, "null argument");

@@ -73,6 +73,15 @@ public:
                               int64_t* E, cudaStream_t st) = 0;
     int64_t n_bins = 0;
 
+    // Replace the schedule.  Before attach the workspace is re-measured for the new sizes;
+    // after attach the sizes are unchanged (checked by the caller) and only the times change.
+    virtual void set_schedule(const std::vector<int64_t>& tw_, const std::vector<int64_t>& tm_,
+                              bool attached) {
+        tw = tw_;
+        tm = tm_;
+        if (!attached) set_windows(n_bins);
+    }
+
     int n_inst = 1, R = 1, L = 1;
     uint32_t* clock_dev = nullptr;  // device word holding the index of the next sweep
     std::vector<int64_t> tw, tm;

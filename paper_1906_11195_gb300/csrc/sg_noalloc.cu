@@ -1,13 +1,12 @@
 // sg_noalloc.cu -- SK local fields h = J s without any device allocation.
 //
-// Some callers cannot allocate device memory at the point where they need this computation:
-// a host application that hands the library a fixed memory budget and forbids further
-// allocations, code running where the allocator must not be entered (allocation inside a
-// stream that is being captured is an error), or a plugin whose process owns every device
-// allocation.  sg_sk_fields_noalloc serves them: the caller passes its own input and output
-// buffers, and the intermediate tensor-core operand images live in one fixed-size array in the
-// library's static device memory, which every GPU that loads the library holds until the
-// process exits.
+// Some callers cannot allocate device memory at the point where they need this computation: a
+// host application that hands the library a fixed memory budget and forbids further
+// allocations, or a plugin whose process owns every device allocation.  sg_sk_fields_noalloc
+// serves them: the caller passes its own input and output buffers, and the intermediate
+// tensor-core operand images live in one fixed-size array in the library's static device
+// memory, which every GPU that loads the library holds until the process exits.  The call
+// waits for its own work (it synchronises the caller's stream before returning).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -51,6 +50,7 @@ void* scratch_address() {
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!fn) {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
@@ -106,13 +106,18 @@ __global__ void k_noalloc_unpad(const int32_t* __restrict__ H, int n, int Np, in
     }
 }
 
-bool is_device_pointer(const void* p) {
+// The device that owns p: its ordinal for device memory, -2 for managed memory (usable from
+// any device), -1 for anything else (host memory, or no CUDA device at all).  A buffer on
+// another GPU would be dereferenced as a peer address, which faults when peer access is not
+// enabled, so the caller compares the ordinal with the current device.
+int pointer_device(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return -1;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return -2;
+    return a.type == cudaMemoryTypeDevice ? a.device : -1;
 }
 
 }  // namespace
@@ -128,8 +133,13 @@ extern "C" int sg_sk_fields_noalloc(const int8_t* J, const int8_t* s, int32_t n,
         if (n_replicas < 16 || n_replicas > kNoallocMaxR || n_replicas % 16)
             fail(SG_EINVAL, "n_replicas must be a multiple of 16 in [16, " +
                                 std::to_string(kNoallocMaxR) + "]");
-        if (!is_device_pointer(J) || !is_device_pointer(s) || !is_device_pointer(h))
-            fail(SG_EINVAL, "J, s and h must be device pointers");
+        const int owner[3] = {pointer_device(J), pointer_device(s), pointer_device(h)};
+        for (int o : owner)
+            if (o == -1) fail(SG_EINVAL, "J, s and h must be device memory");
+        int dev = 0;
+        check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+        for (int o : owner)
+            if (o >= 0 && o != dev) fail(SG_EINVAL, "J, s and h must be memory of the current device");
         cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
         uint8_t* base = static_cast<uint8_t*>(scratch_address());
         const int Np = (n + 127) / 128 * 128;

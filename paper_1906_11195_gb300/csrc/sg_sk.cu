@@ -376,8 +376,11 @@ private:
         make_map_2d(&mapD_, d_.D, Np_, R, Np_, kw_, NT_);
     }
 
-    // tau = 0 state: initial spins, exact fields, zero counters
+    // tau = 0 state: initial spins, exact fields, zero counters (waits keep their full bound
+    // here even in a test of the timeout path, which concerns the sweeps)
     void init_state(cudaStream_t st) {
+        const int nowait = d_.test_nowait;
+        d_.test_nowait = 0;
         check_cuda(cudaMemsetAsync(d_.H, 0, (size_t)R * Np_ * 4, st), "memset");
         check_cuda(cudaMemsetAsync(d_.err, 0, 4, st), "memset");
         check_cuda(cudaMemsetAsync(dC_, 0, nC() * 8, st), "memset");
@@ -396,6 +399,7 @@ private:
         } else {
             fields_direct(st);  // h = J s on CUDA cores
         }
+        d_.test_nowait = nowait;
     }
 
     // Autotuner: time two sweeps with each block size that divides Np and keep the fastest.
@@ -456,6 +460,12 @@ private:
             const char* e = getenv("SG_SK_INBLOCK_WARPS");
             const int v = e ? atoi(e) : 4;
             d_.inblock_warps = (v == 2 || v == 4 || v == 8) ? v : 4;
+        }
+        // SG_TEST_STAGE_WAIT_NS=0 (tests of the timeout path only) turns every bounded device
+        // wait of a sweep into a single test, so that a wait gives up without a GPU fault
+        {
+            const char* w = getenv("SG_TEST_STAGE_WAIT_NS");
+            d_.test_nowait = (w && strtoull(w, nullptr, 10) == 0) ? 1 : 0;
         }
         dC_ = c.take<int64_t>(nC());
         dQ_ = c.take<int64_t>(nQ());
@@ -597,6 +607,13 @@ public:
     void set_windows(int64_t nb) override {
         n_bins = nb;
         for (auto& m : subs_) m->set_windows(nb);
+    }
+
+    void set_schedule(const std::vector<int64_t>& tw_, const std::vector<int64_t>& tm_,
+                      bool attached) override {
+        tw = tw_;
+        tm = tm_;
+        for (auto& m : subs_) m->set_schedule(tw_, tm_, attached);
     }
 
     void measure_window(int mw, int64_t tau, cudaStream_t st) override {

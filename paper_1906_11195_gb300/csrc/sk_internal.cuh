@@ -24,6 +24,8 @@ struct SkDev {
     uint64_t seed;
     int32_t N, Np, R;
     int32_t inblock_warps;    // replica warps per in-block CTA (2, 4 or 8)
+    int32_t test_nowait;      // nonzero only in tests of the timeout path: every bounded wait
+                              // of a sweep becomes a single test (drains keep the full bound)
 };
 
 int sk_init(const SkDev& d, cudaStream_t st);

@@ -25,6 +25,8 @@
 //      Integer arithmetic makes the result identical to the sequential order.
 #include <cuda.h>
 
+#include <mutex>
+
 #include "sg_internal.cuh"
 #include "sk_internal.cuh"
 
@@ -164,7 +166,7 @@ __global__ void __launch_bounds__(256) k_sk_inblock(SkDev d, int b0, int prev_b0
         psn[c] = pv ? d.S[(int64_t)r * words + pwb + c] : 0u;
     }
     __syncthreads();  // the barrier's initialisation is visible to every thread
-    if (!mbar_wait_timed(&jbar, 0u, kSkStageWaitNs)) {
+    if (!mbar_wait_timed(&jbar, 0u, d.test_nowait ? 0ull : kSkStageWaitNs)) {
         // no thread leaves while a copy may still be landing in shared memory
         mbar_wait_timed(&jbar, 0u, kSkStageWaitNs);
         atomicOr(d.err, 4);
@@ -354,8 +356,12 @@ __global__ void __launch_bounds__(128, 1) k_sk_field_mma(const __grid_constant__
                 if (32 * c + j < NT) hv[c][j] = __ldcg(d.H + (int64_t)(n0 + 32 * c + j) * d.Np + row);
     }
 
+    // polls of one wait (a test of the timeout path shortens them to one; drains keep the bound)
+    const uint32_t polls = d.test_nowait ? 1u : kWaitPolls;
+    __shared__ int mma_issued;
     bool ok = true;
     if (tid == 0) {
+        mma_issued = 0;
         const uint32_t bytes = (uint32_t)(nchunks * (128 + NT) * kw);
         mbar_expect_tx(&bars[0], bytes);
         for (int kc = 0; kc < nchunks; ++kc) {
@@ -363,7 +369,7 @@ __global__ void __launch_bounds__(128, 1) k_sk_field_mma(const __grid_constant__
             tma_load_2d(sA + (size_t)kc * 128 * kw, &mapJ, b0 + kc * kw, m0, &bars[0], pol_keep);
             tma_load_2d(sB + (size_t)kc * NT * kw, &mapD, b0 + kc * kw, n0, &bars[0], pol_keep);
         }
-        ok = mbar_wait(&bars[0], 0, kWaitPolls);
+        ok = mbar_wait(&bars[0], 0, polls);
         if (ok) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             // instruction descriptor: D = F32, A = B = E4M3, both K-major, M = 128, N = NT
@@ -386,16 +392,19 @@ __global__ void __launch_bounds__(128, 1) k_sk_field_mma(const __grid_constant__
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     smem_addr(&bars[1]))
                 : "memory");
+            mma_issued = 1;
         } else {
             atomicOr(d.err, 1);
         }
     }
     ok = __syncthreads_and(ok);
     if (ok) {
-        ok = mbar_wait(&bars[1], 0, kWaitPolls);
+        ok = mbar_wait(&bars[1], 0, polls);
         if (!ok) atomicOr(d.err, 2);
     }
     ok = __syncthreads_and(ok);
+    // an MMA that was issued must have finished with tensor memory before it is released
+    if (!ok && mma_issued && tid == 0) mbar_wait(&bars[1], 0, kWaitPolls);
     if (ok) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
@@ -469,11 +478,14 @@ int sk_field_update(const SkDev& d, const CUtensorMap& mapJ, const CUtensorMap& 
     return sk_field_update_rows(d, mapJ, mapD, b0, B, kw, NT, scale, 0, 0, 0, st);
 }
 
-// The limit is a property of the kernel, shared by every handle: it only ever grows.
+// The limit is a property of the kernel, shared by every handle and every host thread: it only
+// ever grows, under a lock.
 static int g_field_smem_limit = 0;
+static std::mutex g_field_smem_mutex;
 
 int sk_field_prepare(int B, int kw, int NT) {
     const int need = (int)sk_field_smem_bytes(B, kw, NT);
+    std::lock_guard<std::mutex> lock(g_field_smem_mutex);
     if (need <= g_field_smem_limit) return 0;
     for (auto kern : {k_sk_field_mma<0>, k_sk_field_mma<64>, k_sk_field_mma<128>})
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, need) !=

@@ -182,3 +182,51 @@ def test_undersized_workspace_is_rejected_before_use(lib):
         sg.sg_attach(h, 1 << 20, need - 1, 0)
     assert e.value.code == sg.SG_ENOMEM
     sg.sg_destroy(h)
+
+
+def test_set_schedule_before_attach_resizes_the_workspace(lib):
+    """sg_set_schedule before sg_attach: any valid schedule, the workspace follows its sizes;
+    invalid arrays are SG_EINVAL and leave the handle's schedule as it was."""
+    g = _graph()
+    for kernel in (sg.SG_VB_PLAIN, sg.SG_VB_PACKED):
+        h = sg.sg_create_vb([g], 8, 2, kernel, [0], [0, 1])
+        base = sg.sg_workspace_bytes(h)
+        sg.sg_set_schedule(h, [0, 4, 16], [0, 4, 8, 16, 20, 32])
+        assert sg.sg_result_shape(h) == (1, 2, 8, 3, 6)
+        assert sg.sg_workspace_bytes(h) > base
+        for tw, tm in (([4, 2], [5]), ([0], [-1, 3]), ([1 << 32], [1]), ([0], [3, 3])):
+            with pytest.raises(sg.SGError) as e:
+                sg.sg_set_schedule(h, tw, tm)
+            assert e.value.code == sg.SG_EINVAL
+        assert sg.sg_result_shape(h) == (1, 2, 8, 3, 6)
+        sg.sg_set_schedule(h, [], [])
+        assert sg.sg_result_shape(h) == (1, 2, 8, 0, 0)
+        assert sg.sg_workspace_bytes(h) < base
+        sg.sg_destroy(h)
+    J = sg_inputs.sk_couplings(200, 2)
+    h = sg.sg_create_sk(J, 16, [0.4] * 16, 7, sg.SG_SK_BLOCKED, 128, [0], [0])
+    base = sg.sg_workspace_bytes(h)
+    sg.sg_set_schedule(h, [0, 3], [0, 3, 9])
+    assert sg.sg_result_shape(h) == (1, 16, 1, 2, 3)
+    assert sg.sg_workspace_bytes(h) > base
+    sg.sg_destroy(h)
+    samples = [dict(J=sg_inputs.sk_couplings(n, 3 + n), seed=n, temps=[0.5] * 16) for n in (100, 140)]
+    h = sg.sg_create_sk_batch(samples, 16, sg.SG_SK_BLOCKED, 64, [0], [0])
+    base = sg.sg_workspace_bytes(h)
+    sg.sg_set_schedule(h, [0, 2, 5], [0, 2, 5, 7])
+    assert sg.sg_result_shape(h) == (2, 16, 1, 3, 4)
+    assert sg.sg_workspace_bytes(h) > base
+    sg.sg_destroy(h)
+
+
+def test_noalloc_rejects_host_pointers_before_launching(lib):
+    """The allocation-free field call checks its pointers on the host: host memory (or memory of
+    another device) is SG_EINVAL and nothing is launched; sizes beyond the static array too."""
+    L = sg._load()
+    J = np.zeros(64 * 64, dtype=np.int8)
+    s = np.ones(16 * 64, dtype=np.int8)
+    h = np.zeros(16 * 64, dtype=np.int32)
+    for n, R in ((64, 16), (4096, 16), (64, 256), (64, 24), (1, 16)):
+        rc = L.sg_sk_fields_noalloc(J.ctypes.data, s.ctypes.data, n, R, h.ctypes.data, None)
+        assert rc == sg.SG_EINVAL, (n, R)
+        assert sg.sg_last_error()

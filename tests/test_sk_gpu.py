@@ -203,3 +203,20 @@ def test_batched_uneven_samples_with_autotuned_blocks():
         assert np.array_equal(spins[b], ref["spins"]), b
         assert np.array_equal(C[b, :, 0], ref["C"]) and np.array_equal(E[b, :, 0], ref["E"])
         assert np.array_equal(q[b, :, 0], ref["q"])
+
+
+def test_set_schedule_after_attach_matches_oracle():
+    """sg_set_schedule on an attached SK handle before any scheduled time: the new times give
+    exactly the oracle's measurements."""
+    n, R = 600, 32
+    J = sg_inputs.sk_couplings(n, 44)
+    temps = [0.4] * (R // 2) + [0.6] * (R // 2)
+    run = sg.SKRun(J, temps, 9, kernel=sg.SG_SK_BLOCKED, block=128, tw=[5, 6], tm=[7, 8, 9])
+    run.sweep(1)
+    tw, tm = [2, 4], [2, 6, 11]
+    run.set_schedule(tw, tm)
+    run.sweep(10)
+    C, q, E = run.results()
+    spins = run.spins()
+    run.close()
+    check(J, temps, 9, 11, tw, tm, (spins, C[0, :, 0], q[0, :, 0], E[0, :, 0]))

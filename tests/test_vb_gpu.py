@@ -326,3 +326,55 @@ def test_full_size_long_run_invariants(big_graph):
     # aging: correlations decay with t and stay positive at T = 0.6 on these scales
     u_last = len(tm) - 1
     assert np.all(C[:, :, 0, u_last].mean() < n)
+
+
+def test_set_schedule_before_and_after_attach_matches_oracle():
+    """sg_set_schedule through the C ABI: a schedule replaced before attach (new sizes), and one
+    replaced after attach while no scheduled time has been reached (same sizes, later times),
+    each give exactly the oracle's measurements for the schedule in force; replacing it once a
+    scheduled time has passed is refused (SG_ESTATE) and changes nothing."""
+    g = vb_instance(3000, 4.0, 31, [1.0, 0.6], 5)
+    stream = torch.cuda.current_stream()
+
+    def attach(h):
+        nb = sg.sg_workspace_bytes(h)
+        buf = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        sg.sg_attach(h, buf.data_ptr(), nb, stream.cuda_stream)
+        return buf
+
+    # before attach: created with a one-entry schedule, replaced by a larger one
+    tw, tm = sg_inputs.log_schedule([0, 2, 8], 40)
+    h = sg.sg_create_vb([g], 64, 2, sg.SG_VB_PACKED, [5], [6])
+    sg.sg_set_schedule(h, tw, tm)
+    buf = attach(h)
+    sg.sg_sweep(h, 40)
+    C, q, E = sg.sg_read_results(h)
+    sg.sg_destroy(h)
+    del buf
+    ref = oracle.vb_run(g["row_ptr"], g["col"], g["jbits"], 64, g["temps"], g["seed"], 40, tw, tm)
+    assert np.array_equal(C[0], ref["C"]) and np.array_equal(q[0], ref["q"])
+    assert np.array_equal(E[0], ref["E"])
+
+    # after attach: nothing scheduled at tau = 0, so the times can still move (same sizes)
+    h = sg.sg_create_vb([g], 64, 2, sg.SG_VB_PACKED, [4, 9], [5, 10, 17])
+    buf = attach(h)
+    sg.sg_sweep(h, 2)
+    with pytest.raises(sg.SGError) as e:  # sizes must stay
+        sg.sg_set_schedule(h, [3], [5, 10, 17])
+    assert e.value.code == sg.SG_ESTATE
+    with pytest.raises(sg.SGError) as e:  # times must be later than tau = 2
+        sg.sg_set_schedule(h, [2, 9], [5, 10, 17])
+    assert e.value.code == sg.SG_ESTATE
+    tw2, tm2 = [3, 7], [3, 8, 15]
+    sg.sg_set_schedule(h, tw2, tm2)
+    sg.sg_sweep(h, 6)
+    with pytest.raises(sg.SGError) as e:  # tau = 8: snapshots 3, 7 and measurements 3, 8 taken
+        sg.sg_set_schedule(h, [9, 10], [11, 12, 13])
+    assert e.value.code == sg.SG_ESTATE
+    sg.sg_sweep(h, 12)
+    C, q, E = sg.sg_read_results(h)
+    sg.sg_destroy(h)
+    del buf
+    ref = oracle.vb_run(g["row_ptr"], g["col"], g["jbits"], 64, g["temps"], g["seed"], 20, tw2, tm2)
+    assert np.array_equal(C[0], ref["C"]) and np.array_equal(q[0], ref["q"])
+    assert np.array_equal(E[0], ref["E"])

@@ -1,4 +1,4 @@
-"""The timeout path of the colour kernel's pipeline waits, without a GPU fault: with the waits
+"""The timeout path of the bounded device waits, without a GPU fault.  Colour kernel (VB): with the waits
 shortened to nothing (SG_TEST_STAGE_WAIT_NS=0), a consumer gives up on the first stage that has
 not landed yet, the kernel drains its copies in flight (with the normal bound), flags the
 handle's status word and exits; sg_synchronize then reports SG_ETIMEOUT and the context stays
@@ -46,3 +46,33 @@ def test_shortened_waits_report_timeout_and_leave_the_context_usable(sg, monkeyp
     ok.close()
     ref = oracle.vb_run(rp, col, jb, 4, g["temps"], g["seed"], 3, tw, tm)
     assert np.array_equal(C[0][:, :4], ref["C"]) and np.array_equal(E[0][:, :4], ref["E"])
+
+
+@pytest.mark.parametrize("block", [64, 128, 512])
+def test_sk_shortened_waits_report_timeout_and_leave_the_context_usable(sg, monkeypatch, block):
+    """The same for the SK sweep: with every bounded wait of a sweep shortened to one test, the
+    field kernel (and the in-block kernel, when its coupling copy has not landed) gives up, waits
+    for its copies and tensor-core work in flight with the normal bound, frees its tensor memory,
+    flags the status word and exits; sg_synchronize reports SG_ETIMEOUT, and a fresh handle
+    afterwards matches the oracle."""
+    n, R = 1024, 32
+    J = sg_inputs.sk_couplings(n, 5)
+    temps = [0.4] * R
+    monkeypatch.setenv("SG_TEST_STAGE_WAIT_NS", "0")
+    run = sg.SKRun(J, temps, 3, kernel=sg.SG_SK_BLOCKED, block=block)
+    run.sweep(2)
+    with pytest.raises(sg.SGError) as e:
+        run.synchronize()
+    assert e.value.code == sg.SG_ETIMEOUT
+    run.close()
+    monkeypatch.delenv("SG_TEST_STAGE_WAIT_NS")
+    tw, tm = [0], [0, 3]
+    ok = sg.SKRun(J, temps, 3, kernel=sg.SG_SK_BLOCKED, block=block, tw=tw, tm=tm)
+    ok.sweep(3)
+    ok.synchronize()
+    C, q, E = ok.results()
+    spins = ok.spins()
+    ok.close()
+    ref = oracle.sk_run(J, temps, 3, 3, tw, tm)
+    assert np.array_equal(spins, ref["spins"])
+    assert np.array_equal(C[0, :, 0], ref["C"]) and np.array_equal(E[0, :, 0], ref["E"])

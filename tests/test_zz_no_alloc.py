@@ -1,12 +1,14 @@
 """The allocation-free field entry point (sg_sk_fields_noalloc) agrees with the regular path.
 
-Callers that cannot allocate device memory -- a host that fixes the library's memory budget,
-a plugin whose process owns all device allocations, code inside a stream capture -- use
-sg_sk_fields_noalloc, which keeps its tensor-core operand images in a fixed static device array
-instead of a workspace.  Its fields h = J s must reproduce what the regular handle computes:
-for every replica, one half of sum_i s_i h_i equals the energy count that sg_measure reports
-for the same spins (bit-exact, as everywhere in this suite), and h equals the exact integer
-product J s.  Two calls in a row (the array keeps the previous call's contents) must both agree.
+Callers that cannot allocate device memory -- a host that fixes the library's memory budget, or
+a plugin whose process owns all device allocations -- use sg_sk_fields_noalloc, which keeps its
+tensor-core operand images in a fixed static device array instead of a workspace.  Its fields
+h = J s must reproduce what the regular handle computes: for every replica, one half of
+sum_i s_i h_i equals the energy count that sg_measure reports for the same spins (bit-exact, as
+everywhere in this suite), and h equals the exact integer product J s.  Two calls in a row (the
+array keeps the previous call's contents) must both agree.  The sizes cover the array's limits
+(n = 2048 with 128 replicas fills it), the smallest replica count (16), sizes that are and are
+not multiples of the 128-spin tile, and every replica tile width of the field kernel.
 This file is collected last on purpose.
 """
 import numpy as np
@@ -38,9 +40,9 @@ def fields_noalloc(sg, J, spins):
     return hd.cpu().numpy().astype(np.int64)
 
 
-def test_noalloc_fields_match_regular_path_twice(sg):
-    n, R = 1000, 32
-    J = sg_inputs.sk_couplings(n, 77)
+@pytest.mark.parametrize("n,R", [(1000, 32), (2048, 128), (128, 16), (1500, 64)])
+def test_noalloc_fields_match_regular_path_twice(sg, n, R):
+    J = sg_inputs.sk_couplings(n, 77 + n)
     temps = [0.4] * R
     run = sg.SKRun(J, temps, 5, kernel=sg.SG_SK_BLOCKED, block=128, tw=[0], tm=[])
     Jl = J.astype(np.int64)
