@@ -11,6 +11,12 @@ schedule falls inside the timed window):
 Under torchrun (N > 1 GPUs) every rank runs its own independent instance (its own graph seed):
 weak scaling with no collective on the data path; rank 0 prints the one JSON line.
 
+Beside the headline, the same line carries one object per other configuration of the metric
+(one GPU only): "sk" (SK, N = 8192, 256 replicas sharing J, T = 0.4, B = 128), "vb_batch" (512
+uneven Poissonian graphs, N in [2^10, 2^20]) and "sk_batch" (32 uneven SK samples, N in
+[2^9, 2^14], 128 replicas), each with its own value, ms_per_step, roofline, e2e, clocks and CPU
+baseline.  --skip-extra leaves them out.
+
 --impl reference times the plain CPU oracle (single thread) on a bounded sample of the same
 workload instead (the test oracle as it stands).
 """
@@ -310,55 +316,298 @@ def run_profile_case(args):
 
 
 SK_N, SK_R, SK_T, SK_B = 8192, 256, 0.4, 128
+SK_WORKLOAD = f"sk_blocked_N{SK_N}_R{SK_R}_T{SK_T}_B{SK_B}"
+VB_BATCH_WORKLOAD = "vb_batch_512_graphs_N2^10..2^20_c4_lanes64_R2_T1.0"
+SK_BATCH_WORKLOAD = "sk_batch_32_samples_N2^9..2^14_R128_T0.4+0.6_autotuned_B"
+L2_FLUSH_BYTES = 256 << 20  # twice the 129 MB L2
 
 
-def run_vb_batch(args):
-    """Batched uneven VB workload (not the headline line): args.batch graphs (512 in the full
-    workload) of Poissonian c = 4 graphs with N = round(2^U), U ~ Uniform[10, 20], 64 lanes,
-    R = 2, T = 1.0, all advancing in lock-step (one launch per colour index per sweep, replayed
-    from CUDA graphs).  One step = one sweep of the whole batch."""
+def e4m3_peak():
+    """e4m3 dense tensor peak: the measured bf16 burst rate x 2 (the nominal e4m3/bf16 ratio)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return 2.0 * float(json.load(f)["bf16_tflops"]), "measured bf16 burst x 2 (nominal e4m3/bf16 ratio)"
+    return 2.0 * 1900.0, "fallback bf16 1.9 PFLOP/s x 2 (nominal e4m3/bf16 ratio)"
+
+
+def _timed_region(run, steps, stream, flush=None):
+    """CUDA-event time (ms) of `steps` sweeps of `run` on `stream`.  With a flush buffer, every
+    sweep is timed on its own and the buffer (larger than L2) is rewritten between sweeps,
+    outside the timed intervals; otherwise one interval covers all sweeps."""
+    import torch
+    if flush is None:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nvtx_push("timed_region")
+        e0.record(stream)
+        run.sweep(steps)
+        e1.record(stream)
+        nvtx_pop()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    nvtx_push("timed_region")
+    for k, (a, b) in enumerate(evs):
+        a.record(stream)
+        run.sweep(1)
+        b.record(stream)
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0x7F)
+    nvtx_pop()
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs)
+
+
+def _e2e(create, steps, updates_per_step, dev, stream, sg):
+    """The same metric end to end through the C ABI from host buffers: attach (H2D of the
+    handle's device image) + `steps` sweeps + D2H of every count, around one host clock; the
+    host-side instance preparation (validation, layout) precedes the timed region."""
+    import torch
+    h = create()
+    nb = sg.sg_workspace_bytes(h)
+    buf = torch.empty(nb, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sg.sg_attach(h, buf.data_ptr(), nb, stream.cuda_stream)
+    sg.sg_sweep(h, steps)
+    C, q, E = sg.sg_read_results(h)
+    dt = time.perf_counter() - t0
+    sg.sg_destroy(h)
+    del buf
+    return {"value": updates_per_step * steps / (dt * 1e9), "unit": "spin updates/ns",
+            "h2d_bytes_per_step": nb // steps, "d2h_bytes_per_step": (C.nbytes + q.nbytes + E.nbytes) // steps,
+            "note": f"attach (H2D of the {nb} B device image) + {steps} sweeps + D2H of all counts"}
+
+
+def measure_sk(args, dev, stream, steps, warmup, cpu=True):
+    """SK, N = 8192, +-1 couplings, 256 replicas sharing J, T = 0.4, block B = 128 as configured
+    (one step = one sweep of all replicas).  The working set (about 90 MB) fits in L2, so every
+    timed sweep runs on its own with L2 flushed before it.  Beside it: the autotuner's choice."""
     import torch
 
     import paper_1906_11195_gb300 as sg
+    J = sg_inputs.sk_couplings(SK_N, 3)
+    R = SK_R
+    tw, tm = sg_inputs.log_schedule([1 << k for k in range(0, 12)], 1 << 12)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def timed(block):
+        run = sg.SKRun(J, [SK_T] * R, 1, kernel=sg.SG_SK_BLOCKED, block=block, tw=tw, tm=tm,
+                       device=dev, stream=stream)
+        run.sweep(warmup)
+        torch.cuda.synchronize()
+        l0 = run.launches
+        sampler = ClockSampler(torch.cuda.current_device())
+        sampler.start()
+        ms = _timed_region(run, steps, stream, flush)
+        clocks = sampler.stop()
+        run.synchronize()
+        launches = run.launches - l0
+        run.close()
+        return ms / steps, launches, clocks
+
+    ms, launches, clocks = timed(SK_B)
+    a_ms, _, _ = timed(0)
+    flops = 2.0 * SK_N * (SK_N - SK_B) * R  # off-block field update of one sweep
+    peak, peak_src = e4m3_peak()
+    achieved = flops / (ms * 1e-3) / 1e12
+    out = {"metric": "spin updates/ns", "unit": "spin updates/ns", "value": SK_N * R / (ms * 1e6),
+           "ms_per_step": ms, "steps": steps, "warmup": warmup, "gpu_launches": launches,
+           "config": {"workload": SK_WORKLOAD, "N": SK_N, "replicas": R, "T": SK_T, "block": SK_B,
+                      "schedule": "tw = 2^0..2^11, log-spaced measurements",
+                      "l2": "working set ~90 MB < L2: each timed sweep follows a 256 MB L2 flush"},
+           "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                        "kernel": "field update on the tensor cores (e4m3 tcgen05), one unit = one sweep",
+                        "algorithmic_flops_per_sweep": flops,
+                        "note": "achieved = 2 N (N - B) R flops per sweep over the whole sweep's "
+                                "event time (every kernel of the sweep): a lower bound of the "
+                                "field kernel's own rate"},
+           "autotuned": {"value": SK_N * R / (a_ms * 1e6), "ms_per_step": a_ms},
+           "clocks": clocks}
+    out["e2e"] = _e2e(lambda: sg.sg_create_sk(J, R, [SK_T] * R, 1, sg.SG_SK_BLOCKED, SK_B, tw, tm),
+                      warmup + steps, SK_N * R, dev, stream, sg)
+    if cpu:
+        import oracle
+        oracle.build()
+        rs, sw = 4, 3
+        t0 = time.perf_counter()
+        oracle.sk_run(J, [SK_T] * rs, 1, sw)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": SK_N * rs * sw / (dt * 1e9), "unit": "spin updates/ns",
+                               "cores": 1, "kind": "oracle",
+                               "sample": f"{sw} sweeps of N={SK_N} from the quench, {rs} replicas, "
+                                         f"T={SK_T} ({dt:.1f} s, initial fields included)"}
+    del flush
+    return out
+
+
+def _gen_vb_graph(args):
+    k, n = args
+    rp, col, eid = sg_inputs.poisson_graph(int(n), MEAN_DEGREE, (4 << 20) + k)
+    jb = sg_inputs.vb_lane_couplings(eid, eid.max() + 1, (4 << 20) + k)
+    return rp, col, jb
+
+
+def vb_batch_graphs(count=512):
+    """The uneven batch: count Poissonian c = 4 graphs, N = round(2^U), U ~ Uniform[10, 20],
+    drawn in parallel host processes (spawned, so safe after CUDA initialisation)."""
+    import multiprocessing as mp
+    sizes = sg_inputs.log_uniform_sizes(count, 10, 20, 4)
+    jobs = list(enumerate(int(n) for n in sizes))
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        res = pool.map(_gen_vb_graph, jobs, chunksize=4)
+    graphs = [dict(row_ptr=rp, col=col, jbits=jb, seed=(4 << 20) + k, temps=[1.0] * REPLICAS)
+              for k, (rp, col, jb) in enumerate(res)]
+    return sizes, graphs
+
+
+def measure_vb_batch(args, dev, stream, steps, warmup, cpu=True, count=512):
+    """Batched uneven VB: 512 Poissonian c = 4 graphs, N log-uniform in [2^10, 2^20], 64 lanes,
+    R = 2, T = 1.0, all graphs in lock-step (one fused launch per sweep for the whole batch,
+    replayed from CUDA graphs).  One step = one sweep of the whole batch."""
+    import torch
+
+    import paper_1906_11195_gb300 as sg
+    t0 = time.perf_counter()
+    sizes, graphs = vb_batch_graphs(count)
+    log(f"vb_batch: generated {len(graphs)} graphs, sum N = {int(sizes.sum())} in {time.perf_counter() - t0:.1f} s")
+    tw, tm = sg_inputs.log_schedule([1 << k for k in range(4, 14)], 1 << 14)
+    t0 = time.perf_counter()
+    run = sg.VBRun(graphs, n_lanes=LANES, n_replicas=REPLICAS, kernel=sg.SG_VB_PACKED, tw=tw, tm=tm,
+                   device=dev, stream=stream)
+    log(f"vb_batch: created and attached in {time.perf_counter() - t0:.1f} s")
+    run.sweep(warmup)
+    torch.cuda.synchronize()
+    l0 = run.launches
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    ms = _timed_region(run, steps, stream) / steps
+    clocks = sampler.stop()
+    run.synchronize()
+    launches = run.launches - l0
+    run.close()
+    n_sum = int(sizes.sum())
+    updates = n_sum * LANES * REPLICAS
+    n_entries = sum(int(g["row_ptr"][-1]) for g in graphs)
+    bytes_sweep = algorithmic_bytes_per_sweep(n_sum, n_entries, REPLICAS)
+    peak, peak_kind = peaks()
+    achieved = bytes_sweep / (ms * 1e-3) / 1e9
+    out = {"metric": "spin updates/ns", "unit": "spin updates/ns", "value": updates / (ms * 1e6),
+           "ms_per_step": ms, "steps": steps, "warmup": warmup, "gpu_launches": launches,
+           "config": {"workload": VB_BATCH_WORKLOAD, "graphs": len(graphs), "sum_N": n_sum,
+                      "schedule": "tw = 2^4..2^13, log-spaced measurements",
+                      "l2": f"inputs larger than L2: {bytes_sweep / 1e9:.2f} GB streamed per sweep"},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                        "kernel": "k_vb_packed_colour over the whole batch, one unit = one sweep",
+                        "algorithmic_bytes_per_sweep": bytes_sweep,
+                        "note": "achieved over the timed region (measurements included)"},
+           "clocks": clocks}
+    out["e2e"] = _e2e(lambda: sg.sg_create_vb(graphs, LANES, REPLICAS, sg.SG_VB_PACKED, tw, tm),
+                      warmup + steps, updates, dev, stream, sg)
+    if cpu:
+        import oracle
+        oracle.build()
+        k = int(np.argmin(np.abs(sizes - (1 << 16))))
+        g = graphs[k]
+        lanes = 16
+        t0 = time.perf_counter()
+        oracle.vb_run(g["row_ptr"], g["col"], g["jbits"], lanes, g["temps"], g["seed"], 4)
+        dt = time.perf_counter() - t0
+        n = int(sizes[k])
+        out["cpu_baseline"] = {"value": n * lanes * REPLICAS * 4 / (dt * 1e9), "unit": "spin updates/ns",
+                               "cores": 1, "kind": "oracle",
+                               "sample": f"4 sweeps of batch graph {k} (N={n}), {lanes} lanes x "
+                                         f"{REPLICAS} replicas ({dt:.2f} s, initial draw included)"}
+    return out
+
+
+def sk_batch_samples():
+    sizes = [int(x) for x in sg_inputs.log_uniform_sizes(32, 9, 14, 5)]
+    R = 128
+    samples = [dict(J=sg_inputs.sk_couplings(n, (5 << 20) + k), seed=(5 << 20) + k,
+                    temps=[0.4] * (R // 2) + [0.6] * (R // 2)) for k, n in enumerate(sizes)]
+    return sizes, R, samples
+
+
+def measure_sk_batch(args, dev, stream, steps, warmup, cpu=True):
+    """Batched uneven SK: 32 samples, N = round(2^U), U ~ Uniform[9, 14], +-1 couplings,
+    R = 128 replicas (64 at T = 0.4, 64 at T = 0.6), block chosen per sample by the autotuner;
+    all samples advance in lock-step, one CUDA graph branch per sample.  One step = one sweep of
+    every sample."""
+    import torch
+
+    import paper_1906_11195_gb300 as sg
+    t0 = time.perf_counter()
+    sizes, R, samples = sk_batch_samples()
+    log(f"sk_batch: generated {len(samples)} samples, sum N = {sum(sizes)} in {time.perf_counter() - t0:.1f} s")
+    tw, tm = sg_inputs.log_schedule([3, 12, 48], 1 << 14)
+    t0 = time.perf_counter()
+    run = sg.SKBatchRun(samples, R, kernel=sg.SG_SK_BLOCKED, block=0, tw=tw, tm=tm, device=dev,
+                        stream=stream)
+    log(f"sk_batch: created, attached and tuned in {time.perf_counter() - t0:.1f} s")
+    run.sweep(warmup)
+    torch.cuda.synchronize()
+    l0 = run.launches
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    ms = _timed_region(run, steps, stream) / steps
+    clocks = sampler.stop()
+    run.synchronize()
+    launches = run.launches - l0
+    run.close()
+    updates = sum(sizes) * R
+    flops = sum(2.0 * n * n * R for n in sizes)
+    peak, peak_src = e4m3_peak()
+    achieved = flops / (ms * 1e-3) / 1e12
+    j_bytes = sum(n * n for n in sizes)
+    out = {"metric": "spin updates/ns", "unit": "spin updates/ns", "value": updates / (ms * 1e6),
+           "ms_per_step": ms, "steps": steps, "warmup": warmup, "gpu_launches": launches,
+           "config": {"workload": SK_BATCH_WORKLOAD, "sizes": sizes, "replicas": R,
+                      "schedule": "tw = 3, 12, 48, log-spaced measurements",
+                      "l2": f"inputs larger than L2: {j_bytes / 1e9:.2f} GB of e4m3 couplings"},
+           "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                        "kernel": "field update on the tensor cores (e4m3 tcgen05), one unit = one sweep of every sample",
+                        "algorithmic_flops_per_sweep": flops,
+                        "note": "2 N^2 R flops per sample per sweep over the whole sweep's event time"},
+           "clocks": clocks}
+    out["e2e"] = _e2e(lambda: sg.sg_create_sk_batch(samples, R, sg.SG_SK_BLOCKED, 0, tw, tm),
+                      warmup + steps, updates, dev, stream, sg)
+    if cpu:
+        import oracle
+        oracle.build()
+        k = int(np.argmin(np.abs(np.array(sizes) - 2048)))
+        x = samples[k]
+        rs, sw = 4, 3
+        t0 = time.perf_counter()
+        oracle.sk_run(x["J"], x["temps"][:rs], x["seed"], sw)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": sizes[k] * rs * sw / (dt * 1e9), "unit": "spin updates/ns",
+                               "cores": 1, "kind": "oracle",
+                               "sample": f"{sw} sweeps of batch sample {k} (N={sizes[k]}), {rs} "
+                                         f"replicas at T=0.4 ({dt:.2f} s)"}
+    return out
+
+
+def _single_gpu():
+    import torch
+
     from paper_1906_11195_gb300 import _build
     _build.build()
     torch.cuda.set_device(0)
-    sizes = sg_inputs.log_uniform_sizes(args.batch, 10, 20, 4)
-    graphs = []
-    t0 = time.perf_counter()
-    for k, n in enumerate(sizes):
-        rp, col, eid = sg_inputs.poisson_graph(int(n), MEAN_DEGREE, (4 << 20) + k)
-        jb = sg_inputs.vb_lane_couplings(eid, eid.max() + 1, (4 << 20) + k)
-        graphs.append(dict(row_ptr=rp, col=col, jbits=jb, seed=(4 << 20) + k, temps=[1.0] * REPLICAS))
-    log(f"generated {len(graphs)} graphs, sum N = {int(sizes.sum())} in {time.perf_counter() - t0:.1f} s")
-    t0 = time.perf_counter()
-    run = sg.VBRun(graphs, n_lanes=LANES, n_replicas=REPLICAS, kernel=sg.SG_VB_PACKED)
-    log(f"created and attached in {time.perf_counter() - t0:.1f} s")
-    stream = torch.cuda.current_stream()
-    run.sweep(args.warmup)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0 = run.launches
-    nvtx_push("timed_region")
-    e0.record(stream)
-    run.sweep(args.steps)
-    e1.record(stream)
-    nvtx_pop()
-    torch.cuda.synchronize()
-    run.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    updates = int(sizes.sum()) * LANES * REPLICAS
-    n_entries = sum(int(g["row_ptr"][-1]) for g in graphs)
-    bytes_sweep = algorithmic_bytes_per_sweep(int(sizes.sum()), n_entries, REPLICAS)
-    peak, _ = peaks()
-    out = {"metric": "spin updates/ns", "unit": "spin updates/ns",
-           "value": updates / (ms * 1e6), "ms_per_step": ms, "steps": args.steps,
-           "warmup": args.warmup, "gpu_launches": run.launches - l0,
-           "config": {"workload": f"vb_batch_{args.batch}_graphs_N2^10..2^20_c4_lanes64_R2_T1.0",
-                      "sum_N": int(sizes.sum())},
-           "roofline": {"bound": "hbm", "achieved": bytes_sweep / (ms * 1e-3) / 1e9, "peak": peak,
-                        "unit": "GB/s", "frac": bytes_sweep / (ms * 1e-3) / 1e9 / peak}}
-    run.close()
+    dev = torch.device("cuda", 0)
+    return dev, torch.cuda.current_stream(dev)
+
+
+def run_vb_batch(args):
+    """The batched uneven VB workload on its own (the same object as the default run's vb_batch
+    key); --batch sets the number of graphs."""
+    dev, stream = _single_gpu()
+    out = measure_vb_batch(args, dev, stream, args.steps, args.warmup, cpu=not args.skip_cpu,
+                           count=args.batch)
     print(json.dumps(out), flush=True)
     return 0
 
@@ -403,11 +652,12 @@ def run_rrbg(args):
     out = {"metric": "spin updates/ns", "unit": "spin updates/ns",
            "value": value, "ms_per_step": ms, "steps": args.steps,
            "warmup": args.warmup, "gpu_launches": run.launches - l0,
-           # the paper's own figure for this ensemble: about 15 ps per spin update on one P100
-           # (another machine: context, not the target)
-           "vs_baseline": value / PAPER_P100_UPDATES_PER_NS,
-           "vs_baseline_note": "paper: ~15 ps per spin update (~66.7 spin updates/ns), one P100, "
-                               "bipartite random regular graph z = 4, T = 0.8 T_c",
+           "vs_baseline": None,
+           # the paper's own figure for this ensemble, another machine: context, not a baseline
+           "context": {"paper_p100_updates_per_ns": PAPER_P100_UPDATES_PER_NS,
+                       "ratio_to_paper_p100": value / PAPER_P100_UPDATES_PER_NS,
+                       "note": "paper: ~15 ps per spin update on one P100, bipartite random "
+                               "regular graph z = 4, T = 0.8 T_c"},
            "config": {"workload": f"vb_packed_rrbg_z4_N{n}_lanes64_R2_T{T_08_TC:.5f}",
                       "colour_classes": 2},
            "roofline": {"bound": "hbm", "achieved": bytes_sweep / (ms * 1e-3) / 1e9,
@@ -587,56 +837,32 @@ def run_e6(args):
 
 
 def run_sk(args):
-    """SK workload (not the headline line): N = 8192, +-1 couplings, 256 replicas sharing J,
-    T = 0.4; one step = one sweep.  The line's value is the configured block B (--sk-block,
-    default 128); the same sweep with the other block sizes and with the autotuner's choice
-    (block = 0) is reported beside it (B never changes the trajectory), with the plain kernel."""
+    """The SK workload on its own (the default run's sk key), plus every other block size on
+    fresh handles (B never changes the trajectory) and the plain kernel; --sk-replicas and
+    --sk-block vary the replicas sharing J and the block of the extra comparison."""
     import torch
 
     import paper_1906_11195_gb300 as sg
-    from paper_1906_11195_gb300 import _build
-    _build.build()
-    torch.cuda.set_device(0)
+    dev, stream = _single_gpu()
+    out = measure_sk(args, dev, stream, args.steps, args.warmup, cpu=not args.skip_cpu)
     J = sg_inputs.sk_couplings(SK_N, 3)
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-
     R = args.sk_replicas
-
-    def timed(block):
-        run = sg.SKRun(J, [SK_T] * R, 1, kernel=sg.SG_SK_BLOCKED, block=block)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    others = {}
+    for b in (64, 128, 256, 512):
+        run = sg.SKRun(J, [SK_T] * R, 1, kernel=sg.SG_SK_BLOCKED, block=b)
         run.sweep(args.warmup)
         torch.cuda.synchronize()
-        l0 = run.launches
-        nvtx_push("timed_region")
         e0.record(stream)
         run.sweep(args.steps)
         e1.record(stream)
-        nvtx_pop()
         torch.cuda.synchronize()
-        run.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
-        launches = run.launches - l0
+        bms = e0.elapsed_time(e1) / args.steps
         run.close()
-        return ms, launches
-
-    ms, launches = timed(args.sk_block)
-    flops = 2.0 * SK_N * SK_N * R  # field update per sweep (all rows, all blocks)
-    out = {"metric": "spin updates/ns", "unit": "spin updates/ns",
-           "config": {"workload": f"sk_blocked_N{SK_N}_R{R}_T{SK_T}_B{args.sk_block}"},
-           "value": SK_N * R / (ms * 1e6), "ms_per_step": ms, "steps": args.steps,
-           "warmup": args.warmup, "gpu_launches": launches,
-           "field_gemm_tflops_over_sweep": flops / (ms * 1e-3) / 1e12}
-    others = {}
-    for b in (64, 128, 256, 512, 0):
-        if b == args.sk_block:
-            continue
-        bms, _ = timed(b)
-        others["autotuned" if b == 0 else f"B{b}"] = {
-            "value": SK_N * R / (bms * 1e6), "ms_per_step": bms}
+        others[f"B{b}_R{R}"] = {"value": SK_N * R / (bms * 1e6), "ms_per_step": bms}
     out["other_blocks"] = others
     if not args.skip_plain:
-        pr = sg.SKRun(J, [SK_T] * R, 1, kernel=sg.SG_SK_PLAIN)
+        pr = sg.SKRun(J, [SK_T] * SK_R, 1, kernel=sg.SG_SK_PLAIN)
         pr.sweep(1)
         torch.cuda.synchronize()
         e0.record(stream)
@@ -645,53 +871,15 @@ def run_sk(args):
         torch.cuda.synchronize()
         pms = e0.elapsed_time(e1) / 2
         pr.close()
-        out["plain_kernel"] = {"value": SK_N * R / (pms * 1e6), "ms_per_sweep": pms}
+        out["plain_kernel"] = {"value": SK_N * SK_R / (pms * 1e6), "ms_per_sweep": pms}
     print(json.dumps(out), flush=True)
     return 0
 
 
 def run_sk_batch(args):
-    """Batched uneven SK workload (not the headline line): 32 samples, N = round(2^U),
-    U ~ Uniform[9, 14], +-1 couplings, R = 128 replicas (64 at T = 0.4, 64 at T = 0.6), block
-    chosen per sample by the autotuner; all samples advance in lock-step, one CUDA graph
-    branch per sample.  One step = one sweep of every sample."""
-    import torch
-
-    import paper_1906_11195_gb300 as sg
-    from paper_1906_11195_gb300 import _build
-    _build.build()
-    torch.cuda.set_device(0)
-    sizes = [int(x) for x in sg_inputs.log_uniform_sizes(32, 9, 14, 5)]
-    R = 128
-    t0 = time.perf_counter()
-    samples = [dict(J=sg_inputs.sk_couplings(n, (5 << 20) + k), seed=(5 << 20) + k,
-                    temps=[0.4] * (R // 2) + [0.6] * (R // 2)) for k, n in enumerate(sizes)]
-    log(f"generated {len(samples)} SK samples, sum N = {sum(sizes)} in {time.perf_counter() - t0:.1f} s")
-    t0 = time.perf_counter()
-    run = sg.SKBatchRun(samples, R, kernel=sg.SG_SK_BLOCKED, block=0)
-    log(f"created, attached and tuned in {time.perf_counter() - t0:.1f} s")
-    stream = torch.cuda.current_stream()
-    run.sweep(args.warmup)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0 = run.launches
-    nvtx_push("timed_region")
-    e0.record(stream)
-    run.sweep(args.steps)
-    e1.record(stream)
-    nvtx_pop()
-    torch.cuda.synchronize()
-    run.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    updates = sum(sizes) * R
-    flops = sum(2.0 * n * n * R for n in sizes)
-    out = {"metric": "spin updates/ns", "unit": "spin updates/ns",
-           "value": updates / (ms * 1e6), "ms_per_step": ms, "steps": args.steps,
-           "warmup": args.warmup, "gpu_launches": run.launches - l0,
-           "config": {"workload": "sk_batch_32_samples_N2^9..2^14_R128_T0.4+0.6_autotuned_B",
-                      "sizes": sizes},
-           "field_gemm_tflops_over_sweep": flops / (ms * 1e-3) / 1e12}
-    run.close()
+    """The batched uneven SK workload on its own (the default run's sk_batch key)."""
+    dev, stream = _single_gpu()
+    out = measure_sk_batch(args, dev, stream, args.steps, args.warmup, cpu=not args.skip_cpu)
     print(json.dumps(out), flush=True)
     return 0
 
@@ -780,7 +968,13 @@ def run_gpu(args):
                 "kernel": "k_vb_packed_colour<2>, one unit = one sweep (all colour classes)",
                 "algorithmic_bytes_per_sweep": bytes_sweep, "ms_per_sweep": sweep_ms_timed,
                 "achieved_isolated": bytes_sweep / (sweep_ms * 1e-3) / 1e9,
-                "ms_per_sweep_isolated": sweep_ms}
+                "ms_per_sweep_isolated": sweep_ms,
+                "frac_kernel": bytes_sweep / (sweep_ms * 1e-3) / 1e9 / peak,
+                "note": "frac: the colour kernel's algorithmic bytes over the whole timed step "
+                        "(snapshot and measurement launches included); frac_kernel: the same "
+                        "over sweeps timed alone (no schedule), the kernel's own fraction; "
+                        "traffic: DRAM bytes per sweep from the committed ncu summary of this "
+                        "kernel source (not measured in this run), null if the source changed"}
 
     # the plain one-thread-per-(vertex, lane, replica) kernel on the same graph, T = 1.0
     plain = None
@@ -828,6 +1022,22 @@ def run_gpu(args):
            "note": "H2D of the device image of both instances + sweeps + D2H of all counts, "
                    "bytes spread over the steps"}
 
+    # the other configurations of the metric, each with its own value, roofline, e2e, clocks
+    # and CPU baseline (one GPU only; each is a separate JSON object inside the line)
+    extra = {}
+    if ws == 1 and not args.skip_extra:
+        es = max(1, min(args.steps, args.extra_steps))
+        ew = max(3, min(args.warmup, 8))
+        for key, fn in (("sk", measure_sk), ("vb_batch", measure_vb_batch),
+                        ("sk_batch", measure_sk_batch)):
+            t0 = time.perf_counter()
+            try:
+                extra[key] = fn(args, dev, stream, es, ew, cpu=not args.skip_cpu)
+            except Exception as e:  # a failing extra leaves the headline line intact
+                extra[key] = {"error": f"{type(e).__name__}: {e}"}
+            log(f"{key}: {time.perf_counter() - t0:.1f} s")
+            torch.cuda.empty_cache()
+
     cpu = cpu_all = None
     if rank == 0 and ws == 1 and not args.skip_cpu:
         cpu = cpu_baseline_sample(rp, col, jb)
@@ -861,6 +1071,7 @@ def run_gpu(args):
         "plain_kernel": plain,
         "speedup_vs_plain": (value / ws) / plain["value"] if plain else None,
     }
+    line.update(extra)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -875,6 +1086,10 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-extra", action="store_true",
+                    help="headline VB line only (no sk, vb_batch, sk_batch keys)")
+    ap.add_argument("--extra-steps", type=int, default=256,
+                    help="timed steps of each extra configuration (at most --steps)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run only the single-instance sweep case used for ncu captures")
     ap.add_argument("--profile-log2n", type=int, default=22, help="log2 N of the profile case")

@@ -12,8 +12,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/sg.h"
@@ -108,6 +110,54 @@ void load_graph(const sg_vb_graph& in, int R, int idx, Graph& g) {
     g.n_colours = nc;
 }
 
+// Validate and colour every graph of a batch, one graph per task on the host's cores (the
+// graphs are independent; a batch of hundreds of uneven graphs is mostly this work).  The first
+// failing graph's error, in graph order, is raised after all tasks have ended.
+void load_graphs(const sg_vb_graph* in, int n_graphs, int R, std::vector<Graph>& out) {
+    out.resize(n_graphs);
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nt = (int)std::min<unsigned>(hw, (unsigned)n_graphs);
+    std::vector<std::unique_ptr<Error>> errs(n_graphs);
+    std::atomic<int> next{0};
+    auto work = [&] {
+        for (;;) {
+            const int b = next.fetch_add(1);
+            if (b >= n_graphs) return;
+            try {
+                load_graph(in[b], R, b, out[b]);
+            } catch (const Error& e) {
+                errs[b].reset(new Error(e));
+            } catch (const std::bad_alloc&) {
+                errs[b].reset(new Error{SG_ENOMEM, "host allocation failed"});
+            }
+        }
+    };
+    if (nt <= 1) {
+        work();
+    } else {
+        std::vector<std::thread> pool;
+        for (int t = 0; t < nt; ++t) pool.emplace_back(work);
+        for (auto& th : pool) th.join();
+    }
+    for (auto& e : errs)
+        if (e) throw *e;
+}
+
+// Run f(lo, hi) over [0, n) cut into contiguous ranges, one per host thread (f must only write
+// what its own range owns).
+template <class F>
+void parallel_ranges(int64_t n, F&& f) {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int64_t nt = std::min<int64_t>((int64_t)hw, std::max<int64_t>(1, n / 4096));
+    if (nt <= 1) {
+        f((int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (int64_t t = 0; t < nt; ++t) pool.emplace_back([&, t] { f(n * t / nt, n * (t + 1) / nt); });
+    for (auto& th : pool) th.join();
+}
+
 std::vector<uint32_t> vb_table(double T) {
     std::vector<uint32_t> t(kVbThrStride);
     const double beta = 1.0 / T;
@@ -133,8 +183,7 @@ public:
         Lc_ = kernel == SG_VB_PACKED ? 64 : L;
         tw = tw_;
         tm = tm_;
-        graphs_.resize(n_graphs);
-        for (int b = 0; b < n_graphs; ++b) load_graph(graphs[b], R, b, graphs_[b]);
+        load_graphs(graphs, n_graphs, R, graphs_);
         for (const Graph& g : graphs_)
             for (int r = 0; r < R; ++r) {
                 auto t = vb_table(g.temps[r]);
@@ -642,46 +691,55 @@ private:
         h_vinfo_.assign(n_slots_, kInactive);
         h_slice_graph_.assign(n_slices, 0);
         h_slice_base_.assign(n_slices + 1, 0);
+        std::vector<int32_t> width_of(n_slices, 0);
+        parallel_ranges(n_slices, [&](int64_t s0, int64_t s1) {
+            for (int64_t s = s0; s < s1; ++s) {
+                const int b = slot_graph[s * 32];
+                h_slice_graph_[s] = (uint32_t)b;
+                const Graph& g = graphs_[b];
+                int width = 0;
+                for (int l = 0; l < 32; ++l) {
+                    const int32_t i = slot_graph_vertex[s * 32 + l];
+                    if (i < 0) continue;
+                    const int d = g.row_ptr[i + 1] - g.row_ptr[i];
+                    width = std::max(width, d);
+                    h_vinfo_[s * 32 + l] = (uint32_t)i | ((uint32_t)d << kDegShift);
+                }
+                width_of[s] = width;
+            }
+        });
         int64_t entries = 0;
         for (int64_t s = 0; s < n_slices; ++s) {
-            const int b = slot_graph[s * 32];
-            h_slice_graph_[s] = (uint32_t)b;
-            const Graph& g = graphs_[b];
-            int width = 0;
-            for (int l = 0; l < 32; ++l) {
-                const int32_t i = slot_graph_vertex[s * 32 + l];
-                if (i < 0) continue;
-                const int d = g.row_ptr[i + 1] - g.row_ptr[i];
-                width = std::max(width, d);
-                h_vinfo_[s * 32 + l] = (uint32_t)i | ((uint32_t)d << kDegShift);
-            }
             h_slice_base_[s] = (uint32_t)entries;
-            entries += 32 * (int64_t)width;
+            entries += 32 * (int64_t)width_of[s];
             if (entries >= (int64_t(1) << 32)) fail(SG_EINVAL, "too many graph entries for one batch");
         }
         h_slice_base_[n_slices] = (uint32_t)entries;
         h_col_.assign(entries, 0);
         h_jb_.assign(entries, 0);
-        for (int64_t s = 0; s < n_slices; ++s) {
-            const int b = (int)h_slice_graph_[s];
-            const Graph& g = graphs_[b];
-            const int64_t base = h_slice_base_[s];
-            const int width = (int)((h_slice_base_[s + 1] - base) / 32);
-            for (int l = 0; l < 32; ++l) {
-                const int64_t slot = s * 32 + l;
-                const int32_t i = slot_graph_vertex[slot];
-                int e = 0;
-                if (i >= 0)
-                    for (int32_t k = g.row_ptr[i]; k < g.row_ptr[i + 1]; ++k, ++e) {
-                        h_col_[base + (int64_t)e * 32 + l] = (uint32_t)slot_of_[b][g.col[k]];
-                        h_jb_[base + (int64_t)e * 32 + l] = g.jb[k];
+        // every slice writes only its own entries
+        parallel_ranges(n_slices, [&](int64_t s0, int64_t s1) {
+            for (int64_t s = s0; s < s1; ++s) {
+                const int b = (int)h_slice_graph_[s];
+                const Graph& g = graphs_[b];
+                const int64_t base = h_slice_base_[s];
+                const int width = (int)((h_slice_base_[s + 1] - base) / 32);
+                for (int l = 0; l < 32; ++l) {
+                    const int64_t slot = s * 32 + l;
+                    const int32_t i = slot_graph_vertex[slot];
+                    int e = 0;
+                    if (i >= 0)
+                        for (int32_t k = g.row_ptr[i]; k < g.row_ptr[i + 1]; ++k, ++e) {
+                            h_col_[base + (int64_t)e * 32 + l] = (uint32_t)slot_of_[b][g.col[k]];
+                            h_jb_[base + (int64_t)e * 32 + l] = g.jb[k];
+                        }
+                    for (; e < width; ++e) {
+                        h_col_[base + (int64_t)e * 32 + l] = (uint32_t)slot;
+                        h_jb_[base + (int64_t)e * 32 + l] = 0;
                     }
-                for (; e < width; ++e) {
-                    h_col_[base + (int64_t)e * 32 + l] = (uint32_t)slot;
-                    h_jb_[base + (int64_t)e * 32 + l] = 0;
                 }
             }
-        }
+        });
         h_slice_meta_.resize(n_slices);
         for (int64_t s = 0; s < n_slices; ++s) {
             uint4 m;

@@ -220,3 +220,34 @@ def test_set_schedule_after_attach_matches_oracle():
     spins = run.spins()
     run.close()
     check(J, temps, 9, 11, tw, tm, (spins, C[0, :, 0], q[0, :, 0], E[0, :, 0]))
+
+
+def test_batch_with_large_samples_and_autotuned_blocks_matches_oracle():
+    """The uneven SK batch at its large end: samples with n >= 2048 (padded to a multiple of 512,
+    where the autotuner may pick B = 512 and the last block is ragged) up to the batch's largest
+    size n = 16384, next to small ones, R = 128 (64 at T = 0.4, 64 at T = 0.6), block = 0; the
+    oracle follows sampled replica pairs of every sample (both temperatures)."""
+    from oracle_pool import run_parallel
+    sizes = [600, 2100, 3000, 5000, 16384]
+    R = 128
+    samples = [dict(J=sg_inputs.sk_couplings(n, 1300 + n), seed=70 + k,
+                    temps=[0.4] * (R // 2) + [0.6] * (R // 2)) for k, n in enumerate(sizes)]
+    sweeps = 8
+    tw, tm = sg_inputs.log_schedule([0, 3], sweeps)
+    run = sg.SKBatchRun(samples, R, kernel=sg.SG_SK_BLOCKED, block=0, tw=tw, tm=tm)
+    run.sweep(sweeps)
+    run.synchronize()
+    C, q, E = run.results()
+    spins = run.spins()
+    run.close()
+    pairs = (0, 62, 64, 126)
+    jobs = [("sk_run", (x["J"], x["temps"], x["seed"], sweeps, tw, tm),
+             dict(r_first=r0, r_count=2)) for x in samples for r0 in pairs]
+    refs = run_parallel(jobs)
+    for b in range(len(samples)):
+        for j, r0 in enumerate(pairs):
+            ref = refs[b * len(pairs) + j]
+            sl = slice(r0, r0 + 2)
+            assert np.array_equal(spins[b][sl], ref["spins"]), (b, r0)
+            assert np.array_equal(C[b, sl, 0], ref["C"]) and np.array_equal(E[b, sl, 0], ref["E"])
+            assert np.array_equal(q[b, r0 // 2:r0 // 2 + 1, 0], ref["q"])

@@ -289,14 +289,52 @@ def big_graph():
     return vb_instance(1 << 22, 4.0, 2, [1.0, 1.0], 1)
 
 
-@pytest.mark.parametrize("T", [1.0, 0.6])
-def test_full_size_prefix_matches_oracle(big_graph, T):
-    """The bench's launch configuration (64 lanes, R = 2) on the full graph; the oracle follows
-    lanes 0..7 (lanes are independent samples), 2 sweeps."""
-    g = dict(big_graph, temps=[T, T])
-    sweeps = 2
-    spins, C, q, E, _ = run_gpu([g], 64, 2, sg.SG_VB_PACKED, sweeps, [0, 1], [0, 1, 2])
-    assert_matches_oracle(g, 8, 2, sg.SG_VB_PACKED, sweeps, [0, 1], [0, 1, 2], spins, C, q, E)
+def test_full_size_schedule_prefix_matches_oracle(big_graph):
+    """The bench's workload and launch configuration at full size: N = 2^22, 64 lanes, R = 2
+    per temperature, T = 1.0 and 0.6 as two handles on the same graph and couplings, the bench's
+    schedule (snapshots at t_w = 2^4..2^15, measurements at t_w + 2^k) run to tau = 24, which
+    takes the t_w = 16 snapshot and the measurements at 16, 17, 18, 20 and 24.  The oracle
+    follows lanes 0..7 of both replicas (lanes are independent samples), one host process per
+    temperature; spins, C, q and E are compared element by element."""
+    from oracle_pool import run_parallel
+    sweeps = 24
+    tw, tm = sg_inputs.log_schedule([1 << k for k in range(4, 16)], sweeps)
+    assert list(tw) == [16] and list(tm) == [16, 17, 18, 20, 24]
+    gs = [dict(big_graph, temps=[T, T]) for T in (1.0, 0.6)]
+    got = [run_gpu([g], 64, 2, sg.SG_VB_PACKED, sweeps, tw, tm) for g in gs]
+    refs = run_parallel([("vb_run", (g["row_ptr"], g["col"], g["jbits"], 8, g["temps"], g["seed"],
+                                     sweeps, tw, tm), {}) for g in gs])
+    mask = lane_mask(8)
+    for (spins, C, q, E, _), ref in zip(got, refs):
+        assert np.array_equal(spins[0] & mask, ref["spins"] & mask)
+        assert np.array_equal(C[0][:, :8], ref["C"]) and np.array_equal(q[0][:, :8], ref["q"])
+        assert np.array_equal(E[0][:, :8], ref["E"])
+        assert np.all(C[0][:, :, 0, 0] == 1 << 22)  # C(t_w, t_w) = N for every lane
+
+
+def test_batch_at_uneven_workload_shape_matches_per_graph_oracle():
+    """The uneven batch's shape: the first 64 graphs of the 512-graph workload (Poisson c = 4,
+    N = round(2^U), U ~ Uniform[10, 20], seeded as in the bench; several above 2^18 vertices) in
+    one handle, 64 lanes, R = 2, T = 1.0, 10 sweeps with snapshots and measurements on the way;
+    every graph's lanes 0..3 are compared with its own oracle run (host processes in parallel)."""
+    from oracle_pool import run_parallel
+    sizes = sg_inputs.log_uniform_sizes(512, 10, 20, 4)[:64]
+    assert (sizes > 1 << 18).sum() >= 5 and sizes.max() > 1 << 19
+    graphs = []
+    for k, n in enumerate(sizes):
+        rp, col, eid = sg_inputs.poisson_graph(int(n), 4.0, (4 << 20) + k)
+        jb = sg_inputs.vb_lane_couplings(eid, eid.max() + 1, (4 << 20) + k)
+        graphs.append(dict(row_ptr=rp, col=col, jbits=jb, seed=(4 << 20) + k, temps=[1.0, 1.0]))
+    sweeps = 10
+    tw, tm = sg_inputs.log_schedule([0, 4], sweeps)
+    spins, C, q, E, _ = run_gpu(graphs, 64, 2, sg.SG_VB_PACKED, sweeps, tw, tm, chunks=[3, 4])
+    refs = run_parallel([("vb_run", (g["row_ptr"], g["col"], g["jbits"], 4, g["temps"], g["seed"],
+                                     sweeps, tw, tm), {}) for g in graphs])
+    mask = lane_mask(4)
+    for b, ref in enumerate(refs):
+        assert np.array_equal(spins[b] & mask, ref["spins"] & mask), b
+        assert np.array_equal(C[b][:, :4], ref["C"]) and np.array_equal(q[b][:, :4], ref["q"]), b
+        assert np.array_equal(E[b][:, :4], ref["E"]), b
 
 
 def test_full_size_long_run_invariants(big_graph):
