@@ -51,6 +51,20 @@ void make_map_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t ou
     if (r != CUDA_SUCCESS) fail(SG_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
 }
 
+// 2-D map of 32-bit words [outer][inner] (row stride inner * 4 bytes), no swizzle
+void make_map_2d_u32(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer,
+                     uint32_t box_inner, uint32_t box_outer) {
+    const cuuint64_t dims[2] = {inner, outer};
+    const cuuint64_t strides[1] = {inner * 4};
+    const cuuint32_t box[2] = {box_inner, box_outer};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = get_encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void*>(base),
+                                       dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) fail(SG_ECUDA, "cuTensorMapEncodeTiled (32-bit) failed (" + std::to_string((int)r) + ")");
+}
+
 class SkModel : public Model {
 public:
     SkModel(int n, const int8_t* J, int n_replicas, const double* temps, uint64_t seed, int kernel,
@@ -176,6 +190,13 @@ public:
             return;
         }
         launches += sk_kstar_sweep(d_, clock_dev, t_off, st);
+        if (persist_) {
+            // one cooperative launch: fields resident in tensor memory, chains on their own CTAs
+            if (sk_persist_sweep(d_, pa_, mapJ_, mapDr_, pmaps_, st) < 0)
+                fail(SG_ECUDA, "persistent sweep launch failed");
+            ++launches;
+            return;
+        }
         const int ntiles = Np_ / 128;
         const int nblocks = (n_ + B_ - 1) / B_;
         if (B_ < 128) {
@@ -364,8 +385,51 @@ private:
 
     void fields_direct(cudaStream_t st);
 
+    // Persistent sweep (B = 128): field CTAs with TPC row tiles each in tensor memory, chain CTAs
+    // of W replica warps; the smallest TPC and then W for which every CTA is resident.
+    // SG_SK_PERSISTENT=0 keeps the launch-per-block sequence (results are the same);
+    // SG_SK_LOOKAHEAD=<L> sets the blocks of flips a chain warp folds in itself (default 6).
+    bool plan_persist() {
+        const char* e = getenv("SG_SK_PERSISTENT");
+        if (e && e[0] == '0' && !e[1]) return false;
+        if (R < 32 || R > 256 || R % 32 || Np_ % 128) return false;
+        int dev = 0, sms = 0;
+        check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+        check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+        int L = 6;
+        if (const char* l = getenv("SG_SK_LOOKAHEAD")) L = std::max(0, atoi(l));
+        SkPersistArgs a = pa_;
+        a.nb = Np_ / 128;
+        a.L = a.nb > 1 ? std::max(1, std::min(L, a.nb - 1)) : 0;
+        a.Q = kPersistSlots;
+        for (int W : {4, 8}) {
+            if (R % W) continue;
+            for (int TPC : {1, 2, 4}) {
+                if (TPC * R > 512) break;
+                a.W = W;
+                a.nC = R / W;
+                a.TPC = TPC;
+                a.nG = (a.nb + TPC - 1) / TPC;
+                for (int nst : {3, 2}) {
+                    a.nst = nst;
+                    if (sk_persist_fits(d_, a, sms)) {
+                        pa_ = a;
+                        make_map_2d(&mapDr_, pa_.Dring, 128, (uint64_t)kPersistSlots * R, 128, 128, R);
+                        make_map_2d_u32(&pmaps_.jb, d_.JbT, Np_, Np_ / 32, 128, (a.L + 1) * 4);
+                        make_map_2d_u32(&pmaps_.kst, d_.kst, Np_, R, 128, W);
+                        make_map_2d_u32(&pmaps_.h, d_.H, Np_, R, 128, W);
+                        make_map_2d_u32(&pmaps_.hpub, pa_.Hpub, Np_, R, 128, W);
+                        return true;
+                    }
+                }
+            }
+        }
+        return false;
+    }
+
     void set_block(int B) {
         B_ = B;
+        persist_ = false;
         kw_ = B >= 128 ? 128 : 64;
         // replica tile of the field GEMM: 64 columns for the short (K <= 128) updates, which
         // doubles the CTAs sharing each row tile's epilogue; 128 for the longer ones
@@ -374,6 +438,7 @@ private:
             fail(SG_ECUDA, "cannot raise the field kernel's shared memory limit");
         make_map_2d(&mapJ_, d_.J8, Np_, Np_, Np_, kw_, 128);
         make_map_2d(&mapD_, d_.D, Np_, R, Np_, kw_, NT_);
+        if (B == 128) persist_ = plan_persist();
     }
 
     // tau = 0 state: initial spins, exact fields, zero counters (waits keep their full bound
@@ -449,6 +514,11 @@ private:
         d_.flips = c.take<uint32_t>(kernel_ == SG_SK_BLOCKED ? (size_t)R * words : 0);
         d_.snap = c.take<uint32_t>((size_t)R * words * tw.size());
         d_.err = c.take<int>(1);
+        // persistent sweep: spin-change ring, published fields, counters
+        const bool blk = kernel_ == SG_SK_BLOCKED;
+        pa_.Dring = c.take<uint8_t>(blk ? (size_t)kPersistSlots * R * 128 : 0);
+        pa_.Hpub = c.take<int32_t>(blk ? (size_t)R * Np_ : 0);
+        pa_.sync = c.take<uint32_t>(blk ? (size_t)(2 * kPersistSlots + Np_ / 128) : 0);
         d_.seed = seed_;
         d_.N = n_;
         d_.Np = Np_;
@@ -478,8 +548,13 @@ private:
         wE_ = c.take<int64_t>(nwE());
     }
 
+    static constexpr int kPersistSlots = 8;  // spin-change ring slots of the persistent sweep
     int kernel_ = SG_SK_BLOCKED;
     bool autotune_ = false;
+    bool persist_ = false;   // B = 128 sweeps run as one persistent launch
+    SkPersistArgs pa_{};
+    CUtensorMap mapDr_{};
+    SkPersistMaps pmaps_{};
     size_t ws_bytes_ = 0;
     cudaStream_t side_ = nullptr;                      // branch for the off-critical-path update
     cudaEvent_t side_done_[2] = {}, inblock_done_[2] = {};

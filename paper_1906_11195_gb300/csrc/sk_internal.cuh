@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "sg_internal.cuh"
+
 namespace sg {
 
 // One SK sample, spins padded to Np (a multiple of 128 and of the block size).
@@ -27,6 +29,56 @@ struct SkDev {
     int32_t test_nowait;      // nonzero only in tests of the timeout path: every bounded wait
                               // of a sweep becomes a single test (drains keep the full bound)
 };
+
+// --------------------------------------------------------------------------------------------
+// TMA tile load and tcgen05 descriptors (inline PTX); mbarrier helpers are in sg_internal.cuh
+// --------------------------------------------------------------------------------------------
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar)), "l"(policy)
+        : "memory");
+}
+
+// shared-memory matrix descriptor, K-major operand in the 128B (kw = 128) or 64B (kw = 64)
+// swizzled layout written by TMA: 8-row groups are kw*8 bytes apart
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, int kw) {
+    const uint64_t sbo = (uint64_t)(kw * 8) >> 4;
+    const uint64_t layout = kw == 128 ? 2ull : 4ull;
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | (sbo << 32) | (1ull << 46) |
+           (layout << 61);
+}
+
+// Persistent sweep (sk_persist.cu): one cooperative launch per sweep, field CTAs holding row
+// tiles of H in tensor memory, chain CTAs running the sequential decisions (block = 128 spins).
+// Blocks of 32 * (W + 1) threads: a field CTA uses warps 0..3 and W, a chain CTA all.
+struct SkPersistArgs {
+    uint8_t* Dring;   // [Q][R][128] e4m3 spin changes 2 D = s' - s of the last Q blocks
+    int32_t* Hpub;    // [R][Np] fields of a tile's rows, published for its chain block
+    uint32_t* sync;   // [2Q + nb] D_count[Q], D_free[Q], H_ready[nb]; zeroed before each launch
+    int nb;           // blocks = row tiles, Np / 128
+    int nG;           // field CTAs; CTA j owns tiles j, j + nG, ...
+    int TPC;          // tiles per field CTA (TPC * R <= 512 tensor-memory columns)
+    int nC;           // chain CTAs, R / W
+    int W;            // replica warps per chain CTA (4 or 8)
+    int L;            // blocks of flips a chain warp folds in itself (lookahead)
+    int Q;            // spin-change ring slots
+    int nst;          // shared-memory stages of a field CTA (2..4)
+};
+// 2-D tensor maps (32-bit elements, no swizzle) of the chain CTAs' staging, boxes of 128 rows:
+// jb: JbT as [Np/32 column words][Np rows], box 128 x (L+1)*4; kst, h, hpub: [R][Np], box 128 x W
+struct SkPersistMaps {
+    CUtensorMap jb, kst, h, hpub;
+};
+size_t sk_persist_smem_bytes(const SkDev& d, const SkPersistArgs& a);
+// 1 if the configuration can be launched with every CTA resident on num_sms SMs
+int sk_persist_fits(const SkDev& d, const SkPersistArgs& a, int num_sms);
+// queue one sweep (counter reset + one cooperative launch); mapJ: J8 boxes of 128 x 128,
+// mapD: Dring as [Q R rows][128] with boxes of 128 x R
+int sk_persist_sweep(const SkDev& d, const SkPersistArgs& a, const CUtensorMap& mapJ,
+                     const CUtensorMap& mapD, const SkPersistMaps& maps, cudaStream_t st);
 
 int sk_init(const SkDev& d, cudaStream_t st);
 int sk_kstar_sweep(const SkDev& d, const uint32_t* clock, uint32_t t_off, cudaStream_t st);

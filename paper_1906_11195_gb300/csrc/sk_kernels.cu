@@ -271,27 +271,6 @@ int sk_inblock_prepare() {
 }
 
 // --------------------------------------------------------------------------------------------
-// TMA tile load and tcgen05 descriptors (inline PTX); mbarrier helpers are in sg_internal.cuh
-// --------------------------------------------------------------------------------------------
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                            uint64_t* bar, uint64_t policy) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar)), "l"(policy)
-        : "memory");
-}
-
-// shared-memory matrix descriptor, K-major operand in the 128B (kw = 128) or 64B (kw = 64)
-// swizzled layout written by TMA: 8-row groups are kw*8 bytes apart
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, int kw) {
-    const uint64_t sbo = (uint64_t)(kw * 8) >> 4;
-    const uint64_t layout = kw == 128 ? 2ull : 4ull;
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | (sbo << 32) | (1ull << 46) |
-           (layout << 61);
-}
-
-// --------------------------------------------------------------------------------------------
 // field update GEMM: H[n0.., m0..m0+127] += scale * (J[m0.., b0..b0+B) . D[n0.., b0..b0+B)^T)
 // One CTA (4 warps) per 128-row x NT-replica tile; one elected thread issues TMA and MMA.
 // --------------------------------------------------------------------------------------------

@@ -251,3 +251,52 @@ def test_batch_with_large_samples_and_autotuned_blocks_matches_oracle():
             assert np.array_equal(spins[b][sl], ref["spins"]), (b, r0)
             assert np.array_equal(C[b, sl, 0], ref["C"]) and np.array_equal(E[b, sl, 0], ref["E"])
             assert np.array_equal(q[b, r0 // 2:r0 // 2 + 1, 0], ref["q"])
+
+
+# --------------------------------------------------------------------------------------------
+# persistent sweep (B = 128, replicas a multiple of 32): one cooperative launch per sweep
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n,R,temps", [
+    (1000, 32, None), (2000, 64, None), (4100, 128, None), (700, 96, None),
+    (384, 32, 0.0), (1024, 32, math.inf), (129, 32, None)])
+def test_persistent_sweep_matches_oracle(n, R, temps):
+    J = sg_inputs.sk_couplings(n, 500 + n)
+    if temps is None:
+        temps = [0.4] * (R // 2) + [0.6] * (R // 2)
+    else:
+        temps = [temps] * R
+    tw, tm = sg_inputs.log_schedule([0, 2, 5], 14)
+    got = run_sk(J, temps, 31 + n, sg.SG_SK_BLOCKED, 128, 14, tw, tm)
+    r_count = None if R <= 64 else 4
+    for r0 in ((0,) if R <= 64 else (0, R // 2, R - 4)):
+        check(J, temps, 31 + n, 14, tw, tm, got, r_first=r0, r_count=r_count)
+
+
+@pytest.mark.parametrize("lookahead", ["1", "2", "5", "40"])
+def test_persistent_lookahead_and_fallback_give_the_same_results(monkeypatch, lookahead):
+    """The lookahead L (blocks of flips a chain warp folds in itself before the tensor cores
+    catch up) and the launch-per-block sequence (SG_SK_PERSISTENT=0) never change a result."""
+    n, R = 1800, 64
+    J = sg_inputs.sk_couplings(n, 17)
+    temps = [0.5] * R
+    tw, tm = sg_inputs.log_schedule([0, 3], 12)
+    monkeypatch.setenv("SG_SK_LOOKAHEAD", lookahead)
+    a = run_sk(J, temps, 4, sg.SG_SK_BLOCKED, 128, 12, tw, tm)
+    monkeypatch.setenv("SG_SK_PERSISTENT", "0")
+    b = run_sk(J, temps, 4, sg.SG_SK_BLOCKED, 128, 12, tw, tm)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("T", [math.inf, 0.4])
+def test_persistent_full_size_matches_oracle(sk_big, T):
+    """N = 8192 with 256 replicas (the configured workload's shape).  At T = inf every spin
+    flips every sweep, so a sweep moves each field by up to 2N: the tensor-memory accumulators
+    must stay exact far from zero."""
+    J = sk_big
+    R, sweeps = 256, 6
+    temps = [T] * R
+    tw, tm = sg_inputs.log_schedule([0, 2], sweeps)
+    got = run_sk(J, temps, 2, sg.SG_SK_BLOCKED, 128, sweeps, tw, tm)
+    for r0 in (0, 100, 254):
+        check(J, temps, 2, sweeps, tw, tm, got, r_first=r0, r_count=2)
