@@ -109,7 +109,7 @@ static cudaGraphExec_t sweep_graph(sg_handle h, int k) {
                    "cudaStreamBeginCapture");
     cudaGraph_t g = nullptr;
     try {
-        for (uint32_t s = 0; s < n; ++s) m.sweep(s, h->cap_stream);
+        m.sweep_many(0, (int)n, h->cap_stream);
         sg::k_clock_add<<<1, 1, 0, h->cap_stream>>>(m.clock_dev, n);
     } catch (...) {
         cudaStreamEndCapture(h->cap_stream, &g);

@@ -177,6 +177,11 @@ struct VbPackedDev {
     uint32_t* gbar;              // [2] grid-barrier arrivals and exits of a fused sweep (zeroed)
     uint64_t* S;                 // [n_slots][R]
     uint64_t* snap;              // [n_tw][n_slots][R]
+    // upper entries for the energy: per slice, each lane's neighbours in later colour classes
+    // (higher slots), sliced-ELL like col/jb; every edge appears once
+    const uint32_t* up_slice_base;  // [n_slices+1] (null: count over every directed entry)
+    const uint32_t* up_col;
+    const uint64_t* up_jb;
     int64_t n_slots;
     int32_t n_slices;
     int32_t R;
@@ -212,6 +217,8 @@ struct VbCountJob {
     int64_t* dst;
     int64_t stride_g, stride_r, stride_k;
     int64_t stride_w;
+    int shift;  // counts are added times 2^shift (the energy over upper entries counts each
+                // edge once and reports the number of unsatisfied directed entries, twice that)
 };
 
 // launch wrappers (vb_kernels.cu); each returns the number of kernel launches queued

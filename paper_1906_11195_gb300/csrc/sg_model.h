@@ -44,6 +44,11 @@ public:
     virtual void attach(char* ws, cudaStream_t st) = 0;
     // one sweep with sweep index *clock_dev + t_off (queued; also used under stream capture)
     virtual void sweep(uint32_t t_off, cudaStream_t st) = 0;
+    // n consecutive sweeps with indices *clock_dev + t_off + 0 .. n - 1 (a model may run them in
+    // fewer launches than n)
+    virtual void sweep_many(uint32_t t_off, int n, cudaStream_t st) {
+        for (int s = 0; s < n; ++s) sweep(t_off + (uint32_t)s, st);
+    }
     // snapshot w <- current spins
     virtual void snapshot(int w, cudaStream_t st) = 0;
     // scheduled measurement column u at time tau (snapshots with tw <= tau exist)

@@ -65,6 +65,20 @@ void make_map_2d_u32(CUtensorMap* map, const void* base, uint64_t inner, uint64_
     if (r != CUDA_SUCCESS) fail(SG_ECUDA, "cuTensorMapEncodeTiled (32-bit) failed (" + std::to_string((int)r) + ")");
 }
 
+// 2-D map of 16-bit words [outer][inner] (row stride inner * 2 bytes), no swizzle
+void make_map_2d_u16(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer,
+                     uint32_t box_inner, uint32_t box_outer) {
+    const cuuint64_t dims[2] = {inner, outer};
+    const cuuint64_t strides[1] = {inner * 2};
+    const cuuint32_t box[2] = {box_inner, box_outer};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = get_encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(base),
+                                       dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) fail(SG_ECUDA, "cuTensorMapEncodeTiled (16-bit) failed (" + std::to_string((int)r) + ")");
+}
+
 class SkModel : public Model {
 public:
     SkModel(int n, const int8_t* J, int n_replicas, const double* temps, uint64_t seed, int kernel,
@@ -189,14 +203,11 @@ public:
             launches += sk_plain_sweep(d_, clock_dev, t_off, st);
             return;
         }
-        launches += sk_kstar_sweep(d_, clock_dev, t_off, st);
         if (persist_) {
-            // one cooperative launch: fields resident in tensor memory, chains on their own CTAs
-            if (sk_persist_sweep(d_, pa_, mapJ_, mapDr_, pmaps_, st) < 0)
-                fail(SG_ECUDA, "persistent sweep launch failed");
-            ++launches;
+            sweep_many(t_off, 1, st);
             return;
         }
+        launches += sk_kstar_sweep(d_, clock_dev, t_off, st);
         const int ntiles = Np_ / 128;
         const int nblocks = (n_ + B_ - 1) / B_;
         if (B_ < 128) {
@@ -239,6 +250,25 @@ public:
         }
         for (int k = 0; k < 2; ++k)
             if (pending[k]) check_cuda(cudaStreamWaitEvent(st, side_done_[k], 0), "cudaStreamWaitEvent");
+    }
+
+    // persistent sweeps: one cooperative launch for all n (fields resident in tensor memory,
+    // chains on their own CTAs, K* of each next sweep computed inside the launch)
+    void sweep_many(uint32_t t_off, int n, cudaStream_t st) override {
+        if (!persist_) {
+            Model::sweep_many(t_off, n, st);
+            return;
+        }
+        for (int done = 0; done < n;) {
+            SkPersistArgs a = pa_;
+            a.clock = clock_dev;
+            a.t_off = t_off + (uint32_t)done;
+            a.n_sweeps = std::min(n - done, kSkPersistMaxSweeps);
+            const int k = sk_persist_sweeps(d_, a, mapJ_, mapDr_, pmaps_, st);
+            if (k < 0) fail(SG_ECUDA, "persistent sweep launch failed");
+            launches += k;
+            done += a.n_sweeps;
+        }
     }
 
     void snapshot(int w, cudaStream_t st) override { launches += sk_snapshot(d_, w, st); }
@@ -388,7 +418,8 @@ private:
     // Persistent sweep (B = 128): field CTAs with TPC row tiles each in tensor memory, chain CTAs
     // of W replica warps; the smallest TPC and then W for which every CTA is resident.
     // SG_SK_PERSISTENT=0 keeps the launch-per-block sequence (results are the same);
-    // SG_SK_LOOKAHEAD=<L> sets the blocks of flips a chain warp folds in itself (default 6).
+    // SG_SK_LOOKAHEAD=<L> (2, 4, 6 or 8; default 4, lowered below the number of blocks) sets the
+    // blocks of flips a chain warp folds in itself.
     bool plan_persist() {
         const char* e = getenv("SG_SK_PERSISTENT");
         if (e && e[0] == '0' && !e[1]) return false;
@@ -396,11 +427,16 @@ private:
         int dev = 0, sms = 0;
         check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
         check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
-        int L = 6;
-        if (const char* l = getenv("SG_SK_LOOKAHEAD")) L = std::max(0, atoi(l));
+        int L = 4;
+        if (const char* l = getenv("SG_SK_LOOKAHEAD")) L = atoi(l);
+        if (!sk_persist_lookahead_supported(L)) return false;
         SkPersistArgs a = pa_;
         a.nb = Np_ / 128;
-        a.L = a.nb > 1 ? std::max(1, std::min(L, a.nb - 1)) : 0;
+        // a fold window never holds a block twice: the largest compiled L below nb
+        while (L >= a.nb && L > 0) L -= 2;
+        if (L < 2) return false;
+        a.L = L;
+        a.n_sweeps = 1;
         a.Q = kPersistSlots;
         for (int W : {4, 8}) {
             if (R % W) continue;
@@ -415,8 +451,8 @@ private:
                     if (sk_persist_fits(d_, a, sms)) {
                         pa_ = a;
                         make_map_2d(&mapDr_, pa_.Dring, 128, (uint64_t)kPersistSlots * R, 128, 128, R);
-                        make_map_2d_u32(&pmaps_.jb, d_.JbT, Np_, Np_ / 32, 128, (a.L + 1) * 4);
-                        make_map_2d_u32(&pmaps_.kst, d_.kst, Np_, R, 128, W);
+                        make_map_2d_u32(&pmaps_.jb, d_.JbT, Np_, Np_ / 32, 128, 4);
+                        make_map_2d_u16(&pmaps_.kst, pa_.kst16, Np_, (uint64_t)kSkPersistMaxSweeps * R, 128, W);
                         make_map_2d_u32(&pmaps_.h, d_.H, Np_, R, 128, W);
                         make_map_2d_u32(&pmaps_.hpub, pa_.Hpub, Np_, R, 128, W);
                         return true;
@@ -483,8 +519,7 @@ private:
             check_cuda(cudaMemsetAsync(clock_dev, 0, 4, st), "memset");
             sweep(0, st);  // warm-up
             check_cuda(cudaEventRecord(e0, st), "cudaEventRecord");
-            sweep(1, st);
-            sweep(2, st);
+            sweep_many(1, 2, st);  // as the replayed graphs run them
             check_cuda(cudaEventRecord(e1, st), "cudaEventRecord");
             check_cuda(cudaEventSynchronize(e1), "cudaEventSynchronize");
             float ms = 0.f;
@@ -519,6 +554,7 @@ private:
         pa_.Dring = c.take<uint8_t>(blk ? (size_t)kPersistSlots * R * 128 : 0);
         pa_.Hpub = c.take<int32_t>(blk ? (size_t)R * Np_ : 0);
         pa_.sync = c.take<uint32_t>(blk ? (size_t)(2 * kPersistSlots + Np_ / 128) : 0);
+        pa_.kst16 = c.take<int16_t>(blk ? (size_t)kSkPersistMaxSweeps * R * Np_ : 0);
         d_.seed = seed_;
         d_.N = n_;
         d_.Np = Np_;
@@ -548,7 +584,7 @@ private:
         wE_ = c.take<int64_t>(nwE());
     }
 
-    static constexpr int kPersistSlots = 8;  // spin-change ring slots of the persistent sweep
+    static constexpr int kPersistSlots = kSkPersistSlots;  // spin-change ring slots
     int kernel_ = SG_SK_BLOCKED;
     bool autotune_ = false;
     bool persist_ = false;   // B = 128 sweeps run as one persistent launch
@@ -652,11 +688,14 @@ public:
         }
     }
 
-    void sweep(uint32_t t_off, cudaStream_t st) override {
+    void sweep(uint32_t t_off, cudaStream_t st) override { sweep_many(t_off, 1, st); }
+
+    // every sample's n sweeps on its own branch, joined once
+    void sweep_many(uint32_t t_off, int n, cudaStream_t st) override {
         check_cuda(cudaEventRecord(fork_, st), "cudaEventRecord");
         for (size_t b = 0; b < subs_.size(); ++b) {
             check_cuda(cudaStreamWaitEvent(streams_[b], fork_, 0), "cudaStreamWaitEvent");
-            subs_[b]->sweep(t_off, streams_[b]);
+            subs_[b]->sweep_many(t_off, n, streams_[b]);
             check_cuda(cudaEventRecord(events_[b], streams_[b]), "cudaEventRecord");
         }
         for (size_t b = 0; b < subs_.size(); ++b)

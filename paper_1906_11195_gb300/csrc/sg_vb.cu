@@ -225,6 +225,9 @@ public:
             std::vector<uint64_t> seeds(n_inst);
             for (int b = 0; b < n_inst; ++b) seeds[b] = graphs_[b].seed;
             up((void*)pk_.seeds, seeds.data(), seeds.size() * 8);
+            up((void*)pk_.up_slice_base, h_up_base_.data(), h_up_base_.size() * 4);
+            up((void*)pk_.up_col, h_up_col_.data(), h_up_col_.size() * 4);
+            up((void*)pk_.up_jb, h_up_jb_.data(), h_up_jb_.size() * 8);
             launches += vb_packed_init(pk_, st);
             // SG_VB_COLOUR_VARIANT=<k> and SG_VB_FUSED=<0|1> pin the pipeline shape and the
             // launch form (reproducible timings of one choice); otherwise the autotuner picks
@@ -575,6 +578,9 @@ private:
             pk_.gbar = c.take<uint32_t>(2);
             pk_.jb = c.take<uint64_t>(h_jb_.size());
             pk_.seeds = c.take<uint64_t>(n_inst);
+            pk_.up_slice_base = c.take<uint32_t>(h_up_base_.size());
+            pk_.up_col = c.take<uint32_t>(h_up_col_.size());
+            pk_.up_jb = c.take<uint64_t>(h_up_jb_.size());
             pk_.S = c.take<uint64_t>((size_t)n_slots_ * R);
             pk_.snap = c.take<uint64_t>((size_t)n_slots_ * R * tw.size());
             pk_.thr = d_thr_;
@@ -740,6 +746,59 @@ private:
                 }
             }
         });
+        // upper entries (energy measurement): neighbours in later colour classes only
+        h_up_base_.assign(n_slices + 1, 0);
+        std::vector<int32_t> up_width(n_slices, 0);
+        parallel_ranges(n_slices, [&](int64_t s0, int64_t s1) {
+            for (int64_t s = s0; s < s1; ++s) {
+                const int b = (int)h_slice_graph_[s];
+                const Graph& g = graphs_[b];
+                int w = 0;
+                for (int l = 0; l < 32; ++l) {
+                    const int64_t slot = s * 32 + l;
+                    const int32_t i = slot_graph_vertex[slot];
+                    if (i < 0) continue;
+                    int n_up = 0;
+                    for (int32_t k = g.row_ptr[i]; k < g.row_ptr[i + 1]; ++k)
+                        n_up += slot_of_[b][g.col[k]] > slot;
+                    w = std::max(w, n_up);
+                }
+                up_width[s] = w;
+            }
+        });
+        int64_t up_entries = 0;
+        for (int64_t s = 0; s < n_slices; ++s) {
+            h_up_base_[s] = (uint32_t)up_entries;
+            up_entries += 32 * (int64_t)up_width[s];
+        }
+        h_up_base_[n_slices] = (uint32_t)up_entries;
+        h_up_col_.assign(up_entries, 0);
+        h_up_jb_.assign(up_entries, 0);
+        parallel_ranges(n_slices, [&](int64_t s0, int64_t s1) {
+            for (int64_t s = s0; s < s1; ++s) {
+                const int b = (int)h_slice_graph_[s];
+                const Graph& g = graphs_[b];
+                const int64_t base = h_up_base_[s];
+                const int width = up_width[s];
+                for (int l = 0; l < 32; ++l) {
+                    const int64_t slot = s * 32 + l;
+                    const int32_t i = slot_graph_vertex[slot];
+                    int e = 0;
+                    if (i >= 0)
+                        for (int32_t k = g.row_ptr[i]; k < g.row_ptr[i + 1]; ++k) {
+                            const int64_t sj = slot_of_[b][g.col[k]];
+                            if (sj <= slot) continue;
+                            h_up_col_[base + (int64_t)e * 32 + l] = (uint32_t)sj;
+                            h_up_jb_[base + (int64_t)e * 32 + l] = g.jb[k];
+                            ++e;
+                        }
+                    for (; e < width; ++e) {  // padding: the vertex itself, no coupling
+                        h_up_col_[base + (int64_t)e * 32 + l] = (uint32_t)slot;
+                        h_up_jb_[base + (int64_t)e * 32 + l] = 0;
+                    }
+                }
+            }
+        });
         h_slice_meta_.resize(n_slices);
         for (int64_t s = 0; s < n_slices; ++s) {
             uint4 m;
@@ -802,6 +861,8 @@ private:
     int64_t n_slots_ = 0;
     std::vector<uint32_t> h_vinfo_, h_slice_base_, h_slice_graph_, h_col_;
     std::vector<uint64_t> h_jb_;
+    std::vector<uint32_t> h_up_base_, h_up_col_;  // upper entries (energy measurement)
+    std::vector<uint64_t> h_up_jb_;
     // plain host layout
     std::vector<int32_t> colour_begin_, new_of_, h_row_ptr_, h_col_i_;
     std::vector<uint32_t> h_orig_;

@@ -51,37 +51,74 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, int kw) {
            (layout << 61);
 }
 
-// Persistent sweep (sk_persist.cu): one cooperative launch per sweep, field CTAs holding row
-// tiles of H in tensor memory, chain CTAs running the sequential decisions (block = 128 spins).
-// Blocks of 32 * (W + 1) threads: a field CTA uses warps 0..3 and W, a chain CTA all.
+constexpr int kSkPersistSlots = 8;  // spin-change ring slots of the persistent sweeps (Q)
+
+// Persistent sweeps (sk_persist.cu): one cooperative launch runs n_sweeps sweeps; field CTAs
+// hold row tiles of H in tensor memory, chain CTAs run the sequential decisions (block = 128
+// spins).  Blocks of 32 * (W + 1) threads: a chain CTA uses warps 0..W (W replica warps and a
+// staging warp); a field CTA uses warps 0..3 (tensor-memory epilogue, thread 0 issues the MMAs)
+// and warp W (operand loads).
+constexpr int kSkPersistMaxSweeps = 64;  // sweeps of one launch (the K* buffer holds them)
 struct SkPersistArgs {
     uint8_t* Dring;   // [Q][R][128] e4m3 spin changes 2 D = s' - s of the last Q blocks
     int32_t* Hpub;    // [R][Np] fields of a tile's rows, published for its chain block
     uint32_t* sync;   // [2Q + nb] D_count[Q], D_free[Q], H_ready[nb]; zeroed before each launch
+    int16_t* kst16;   // [kSkPersistMaxSweeps][R][Np] K* of the launch's sweeps
+    const uint32_t* clock;  // device sweep clock: the launch runs sweeps *clock + t_off + s
+    uint32_t t_off;
+    int n_sweeps;     // sweeps in this launch, 1..kSkPersistMaxSweeps
     int nb;           // blocks = row tiles, Np / 128
     int nG;           // field CTAs; CTA j owns tiles j, j + nG, ...
     int TPC;          // tiles per field CTA (TPC * R <= 512 tensor-memory columns)
     int nC;           // chain CTAs, R / W
     int W;            // replica warps per chain CTA (4 or 8)
-    int L;            // blocks of flips a chain warp folds in itself (lookahead)
-    int Q;            // spin-change ring slots
+    int L;            // blocks of flips a chain warp folds in itself (lookahead), L < nb
+    int Q;            // spin-change ring slots: kSkPersistSlots
     int nst;          // shared-memory stages of a field CTA (2..4)
 };
-// 2-D tensor maps (32-bit elements, no swizzle) of the chain CTAs' staging, boxes of 128 rows:
-// jb: JbT as [Np/32 column words][Np rows], box 128 x (L+1)*4; kst, h, hpub: [R][Np], box 128 x W
+// 2-D tensor maps (no swizzle) of the chain CTAs' staging, boxes of 128 rows: jb: JbT as
+// [Np/32 column words][Np rows] of 32-bit words, box 128 x 4 (one block's column words);
+// kst: kst16 as [kSkPersistMaxSweeps R][Np] 16-bit words, box 128 x W; h, hpub: [R][Np] of
+// 32-bit words, box 128 x W
 struct SkPersistMaps {
     CUtensorMap jb, kst, h, hpub;
 };
 size_t sk_persist_smem_bytes(const SkDev& d, const SkPersistArgs& a);
 // 1 if the configuration can be launched with every CTA resident on num_sms SMs
 int sk_persist_fits(const SkDev& d, const SkPersistArgs& a, int num_sms);
-// queue one sweep (counter reset + one cooperative launch); mapJ: J8 boxes of 128 x 128,
-// mapD: Dring as [Q R rows][128] with boxes of 128 x R
-int sk_persist_sweep(const SkDev& d, const SkPersistArgs& a, const CUtensorMap& mapJ,
-                     const CUtensorMap& mapD, const SkPersistMaps& maps, cudaStream_t st);
+// the lookaheads L the persistent kernel is compiled for
+int sk_persist_lookahead_supported(int L);
+// queue a.n_sweeps sweeps: K* of all of them (k_sk_kstar16), counter reset, one cooperative
+// launch; mapJ: J8 boxes of 128 x 128, mapD: Dring as [Q R rows][128] with boxes of 128 x R.
+// Returns the kernel launches queued (2) or -1.
+int sk_persist_sweeps(const SkDev& d, const SkPersistArgs& a, const CUtensorMap& mapJ,
+                      const CUtensorMap& mapD, const SkPersistMaps& maps, cudaStream_t st);
+// K* of n consecutive sweeps from index *clock + t_off, int16, into dst[(s R + r) Np + i]
+int sk_kstar16_sweeps(const SkDev& d, const uint32_t* clock, uint32_t t_off, int n, int16_t* dst,
+                      cudaStream_t st);
+
+// --------------------------------------------------------------------------------------------
+// K* for a replica: largest k in [0, N-1] with k == 0 or r32 < thr[k].  A logarithmic estimate
+// (thr[k] ~ 2^32 exp(-k / coef), coef = sqrt(N) T / 2) is corrected exactly on the table.
+// --------------------------------------------------------------------------------------------
+__device__ __forceinline__ int sk_kstar(uint32_t r32, const uint32_t* __restrict__ thr, int n,
+                                        float coef) {
+    const float u = ((float)r32 + 0.5f) * 2.3283064365386963e-10f;
+    const float est = -__logf(u) * coef;
+    int k;
+    if (!(est < (float)(n - 1))) k = n - 1;
+    else if (!(est > 0.f)) k = 0;
+    else k = (int)est;
+    while (k + 1 <= n - 1 && r32 < __ldg(thr + k + 1)) ++k;
+    while (k >= 1 && !(r32 < __ldg(thr + k))) --k;
+    return k;
+}
 
 int sk_init(const SkDev& d, cudaStream_t st);
 int sk_kstar_sweep(const SkDev& d, const uint32_t* clock, uint32_t t_off, cudaStream_t st);
+// the same into even[] or odd[] by the parity of the sweep index
+int sk_kstar_sweep_into(const SkDev& d, const uint32_t* clock, uint32_t t_off, int32_t* even,
+                        int32_t* odd, cudaStream_t st);
 // prev_b0 < 0: no previous-block update folded in (the caller's field GEMM covered those rows)
 // after_inblock: the launch directly follows the previous block's in-block kernel in stream
 // order (programmatic dependent launch); otherwise a plain launch

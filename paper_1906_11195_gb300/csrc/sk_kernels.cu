@@ -32,23 +32,6 @@
 
 namespace sg {
 
-// --------------------------------------------------------------------------------------------
-// K* for a replica: largest k in [0, N-1] with k == 0 or r32 < thr[k].  A logarithmic estimate
-// (thr[k] ~ 2^32 exp(-k / coef), coef = sqrt(N) T / 2) is corrected exactly on the table.
-// --------------------------------------------------------------------------------------------
-__device__ __forceinline__ int sk_kstar(uint32_t r32, const uint32_t* __restrict__ thr, int n,
-                                        float coef) {
-    const float u = ((float)r32 + 0.5f) * 2.3283064365386963e-10f;
-    const float est = -__logf(u) * coef;
-    int k;
-    if (!(est < (float)(n - 1))) k = n - 1;
-    else if (!(est > 0.f)) k = 0;
-    else k = (int)est;
-    while (k + 1 <= n - 1 && r32 < __ldg(thr + k + 1)) ++k;
-    while (k >= 1 && !(r32 < __ldg(thr + k))) --k;
-    return k;
-}
-
 __device__ __forceinline__ uint8_t e4m3_of_sign(int v) {  // v in {-1, 0, 1}
     return v > 0 ? (uint8_t)0x38 : (v < 0 ? (uint8_t)0xB8 : (uint8_t)0x00);
 }
@@ -83,25 +66,71 @@ int sk_init(const SkDev& d, cudaStream_t st) {
 // K* of every (replica, spin) for one sweep: depends only on the random numbers and the tables,
 // so it is computed for the whole sweep at once, off the sequential chain.
 // --------------------------------------------------------------------------------------------
-__global__ void k_sk_kstar(SkDev d, const uint32_t* __restrict__ clock, uint32_t t_off) {
+// dst: even[] for an even sweep index t, odd[] for an odd one (the same array for the
+// launch-per-block sequence; the persistent sweep double-buffers)
+__global__ void k_sk_kstar(SkDev d, const uint32_t* __restrict__ clock, uint32_t t_off,
+                           int32_t* even, int32_t* odd) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over R * Np
     if (idx >= (int64_t)d.R * d.Np) return;
     const int r = (int)(idx / d.Np);
     const int i = (int)(idx % d.Np);
+    const uint32_t t = __ldg(clock) + t_off;
     int k = -0x7FFFFFFF;  // padding never flips
     if (i < d.N) {
-        const uint32_t t = __ldg(clock) + t_off;
         const uint4 rnd = philox4x32_10(make_uint4((uint32_t)i, t, (uint32_t)(r >> 2), 0u),
                                         (uint32_t)d.seed, (uint32_t)(d.seed >> 32));
         k = sk_kstar(uint4_word(rnd, r & 3), d.thr + (int64_t)d.temp_index[r] * d.N, d.N,
                      d.coef[r]);
     }
-    d.kst[idx] = k;
+    ((t & 1u) ? odd : even)[idx] = k;
+}
+
+int sk_kstar_sweep_into(const SkDev& d, const uint32_t* clock, uint32_t t_off, int32_t* even,
+                        int32_t* odd, cudaStream_t st) {
+    const int64_t total = (int64_t)d.R * d.Np;
+    k_sk_kstar<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(d, clock, t_off, even, odd);
+    return 1;
 }
 
 int sk_kstar_sweep(const SkDev& d, const uint32_t* clock, uint32_t t_off, cudaStream_t st) {
-    const int64_t total = (int64_t)d.R * d.Np;
-    k_sk_kstar<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(d, clock, t_off);
+    return sk_kstar_sweep_into(d, clock, t_off, d.kst, d.kst, st);
+}
+
+// K* of n consecutive sweeps as int16 (|K*| < N <= 32768; padding gets -32768, which no k
+// reaches): one thread per (sweep, replica group of 4, spin), one Philox block per thread for
+// the group's four replicas.  dst[(s R + r) Np + i].
+__global__ void k_sk_kstar16(SkDev d, const uint32_t* __restrict__ clock, uint32_t t_off, int n,
+                             int16_t* __restrict__ dst) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int groups = d.R / 4;
+    const int64_t per_sweep = (int64_t)groups * d.Np;
+    if (idx >= per_sweep * n) return;
+    const int s = (int)(idx / per_sweep);
+    const int64_t rem = idx - (int64_t)s * per_sweep;
+    const int g = (int)(rem / d.Np);
+    const int i = (int)(rem - (int64_t)g * d.Np);
+    int16_t* out = dst + ((int64_t)s * d.R + 4 * g) * d.Np + i;
+    if (i >= d.N) {
+#pragma unroll
+        for (int w = 0; w < 4; ++w) out[(int64_t)w * d.Np] = (int16_t)-32768;
+        return;
+    }
+    const uint32_t t = __ldg(clock) + t_off + (uint32_t)s;
+    const uint4 rnd = philox4x32_10(make_uint4((uint32_t)i, t, (uint32_t)g, 0u), (uint32_t)d.seed,
+                                    (uint32_t)(d.seed >> 32));
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const int r = 4 * g + w;
+        out[(int64_t)w * d.Np] = (int16_t)sk_kstar(uint4_word(rnd, w),
+                                                   d.thr + (int64_t)__ldg(d.temp_index + r) * d.N,
+                                                   d.N, __ldg(d.coef + r));
+    }
+}
+
+int sk_kstar16_sweeps(const SkDev& d, const uint32_t* clock, uint32_t t_off, int n, int16_t* dst,
+                      cudaStream_t st) {
+    const int64_t total = (int64_t)(d.R / 4) * d.Np * n;
+    k_sk_kstar16<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(d, clock, t_off, n, dst);
     return 1;
 }
 

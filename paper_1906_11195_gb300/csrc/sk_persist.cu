@@ -1,38 +1,41 @@
-// sk_persist.cu -- one persistent launch per Sherrington-Kirkpatrick sweep, with the local fields
-// resident in tensor memory (sm_103a).
+// sk_persist.cu -- persistent Sherrington-Kirkpatrick sweeps with the local fields resident in
+// tensor memory (sm_103a): one cooperative launch runs several consecutive sweeps.
 //
-// The sweep visits i = 0..N-1 in order (SI section 1).  It is cut into blocks of 128 spins, and
-// the fields H[i][r] = sum_j J_ij s_j^r into the same 128-row tiles.  Two kinds of CTA share one
-// cooperative launch (all CTAs resident):
+// Every sweep visits i = 0..N-1 in order (SI section 1).  The spins are cut into blocks of 128,
+// and the fields H[i][r] = sum_j J_ij s_j^r into the same 128-row tiles.  Blocks are numbered
+// k = s nb + b over the sweeps s of the launch (nb blocks per sweep).  Two kinds of CTA share
+// the launch (all CTAs resident):
 //
 //   field CTAs (the first nG): CTA j owns the row tiles t = j, j + nG, ... (TPC of them).  Their
 //     fields live in tensor memory as FP32 accumulators for the whole launch (loaded from H at
-//     the start, written back at the end).  For every block b, once the spin changes
-//     D_b = (s' - s)/2 of all replicas are published (stored as 2 D_b), the CTA loads
-//     J[tile rows][block b] and 2 D_b with TMA and adds J (2 D_b) to each of its tiles with
+//     the start, written back at the end).  For every block k, once the spin changes
+//     D_k = (s' - s)/2 of all replicas are published (stored as 2 D_k), the CTA loads
+//     J[tile rows][block b] and 2 D_k with TMA and adds J (2 D_k) to each of its tiles with
 //     tcgen05.mma (kind::f8f6f4, e4m3 operands: J = +-1 and 2 D in {-2, 0, +2} are exact, and so
-//     is every partial sum, because
-//     |H| < N <= 2^15 stays far below 2^24).  When block b has been applied to a tile t with
-//     t = b + L + 1, the CTA copies that tile's fields to Hpub and raises H_ready[t].
+//     is every partial sum, because |H| < N <= 2^15 stays far below 2^24).  When block k has
+//     been applied, the tile of chain block k + L + 1 (if the CTA owns it) is copied to Hpub and
+//     H_ready of that tile is raised to k + L + 2.
 //
 //   chain CTAs (the next nC): CTA c owns replicas W c .. W c + W - 1, one warp per replica, plus
-//     a helper warp.  For block b the helper stages (three 2-D TMA copies into a ring of
-//     shared-memory stages) the block's couplings as bits (its own columns and those of the L blocks before
-//     it), the replicas' K* values (largest accepted k of the sweep's random numbers) and the
-//     fields of the block's rows: from H itself when b <= L (nothing of this sweep has reached
-//     them through the tensor cores yet), else from Hpub once H_ready[b] is up, which then holds
-//     every block before b - L.  The replica warp adds the flips of blocks b - L .. b - 1 (its
-//     own, kept in shared memory) with popcounts over the coupling bits, then takes the 128
-//     sequential decisions (ballot per accepted flip, as in the in-block kernel) and writes D_b
-//     into ring slot b mod Q.  The helper raises D_count[slot] once every replica warp of the
-//     CTA is done with the block.
+//     a staging warp.  For block k the staging warp loads (TMA, into a ring of shared-memory
+//     stages) the couplings of block b's rows with the columns of blocks k - L .. k (as bits),
+//     the replicas' K* (the largest accepted k of each spin's random number, computed for all
+//     sweeps of the launch before it starts) and the fields of block b's rows: from H itself
+//     for k <= L (nothing of
+//     this launch has reached them through the tensor cores yet), else from Hpub once H_ready
+//     says it holds every block before k - L.  The replica warp adds the flips of blocks
+//     k - L .. k - 1 of this launch (its own, kept in shared memory) with popcounts over the
+//     coupling bits, then takes the 128 sequential decisions (ballot per accepted flip, as in
+//     the in-block kernel) and writes 2 D_k into ring slot k mod Q.  The staging warp raises
+//     D_count[slot] once every replica warp of the CTA is done with the block.
 //
 // So the sequential chain of a replica never waits for a launch or for the tensor cores, as
-// long as the field CTAs publish a tile within L chain blocks.  Ring slots are reused only after
-// every field CTA has read them (D_free).  Every wait is bounded (global timer); a CTA that
-// gives up flags d.err, drains its copies and tensor-core work in flight with the normal bound,
-// releases its tensor memory and exits, and the other CTAs notice the flag and do the same.
-// The counters (D_count, D_free, H_ready) are zero at the start of every launch.
+// long as the field CTAs publish a tile within L chain blocks; it needs L < nb so that a fold
+// window never holds a block twice.  Ring slots are reused only after every field CTA has read
+// them (D_free).  Every wait is bounded (global timer); a CTA that gives up flags d.err, drains
+// its copies and tensor-core work in flight with the normal bound, releases its tensor memory
+// and exits, and the other CTAs notice the flag and do the same.  The counters are zero at the
+// start of every launch.
 #include <cuda.h>
 
 #include "sg_internal.cuh"
@@ -44,7 +47,7 @@ namespace {
 
 constexpr uint64_t kPersistWaitNs = 2000000000ull;  // 2 s: only a broken launch waits that long
 constexpr uint32_t kTileBytes = 128 * 128;          // one e4m3 128 x 128 coupling tile
-constexpr int kChainStages = 2;
+constexpr int kChainStages = 2;  // a power of two
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
     uint32_t v;
@@ -135,7 +138,7 @@ __host__ __device__ __forceinline__ size_t chain_words_bytes(int W, int Np) {
     return (size_t)2 * W * (Np / 32) * 4;
 }
 __host__ __device__ __forceinline__ size_t chain_stage_bytes(int W, int L) {
-    return (size_t)((L + 1) * 4 + 2 * W) * 128 * 4;  // coupling words, K*, fields
+    return (size_t)(L + 1) * 4 * 128 * 4 + (size_t)W * 128 * (2 + 4);  // coupling words, K*, fields
 }
 
 }  // namespace
@@ -152,7 +155,9 @@ __device__ void persist_field_cta(const CUtensorMap* mapJ, const CUtensorMap* ma
                                   uint32_t* tslot, volatile int* abort_flag) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int j = blockIdx.x;
-    const int R = d.R, Np = d.Np, nb = a.nb, nst = a.nst, Q = a.Q, L = a.L;
+    const int R = d.R, Np = d.Np, nb = a.nb, nst = a.nst, L = a.L;
+    constexpr int Q = kSkPersistSlots;
+    const int nk = a.n_sweeps * nb;  // blocks of the launch
     const bool nowait = d.test_nowait != 0;
     int ntl = 0;  // tiles owned
     for (int u = 0; u < a.TPC; ++u)
@@ -211,8 +216,9 @@ __device__ void persist_field_cta(const CUtensorMap* mapJ, const CUtensorMap* ma
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(mapD)) : "memory");
             int blk[4] = {-1, -1, -1, -1};     // latest block issued into each stage
             bool b_in[4] = {false, false, false, false};
-            for (int k = 0; k < nb; ++k) {
+            for (int k = 0; k < nk; ++k) {
                 const int s = k % nst;
+                const int b = k % nb;
                 if (k >= nst && !mbar_wait_or_abort(&mdone[s], (uint32_t)(k / nst - 1) & 1u, d.err, nowait,
                                                     abort_flag)) {
                     atomicOr(d.err, 64);
@@ -223,7 +229,7 @@ __device__ void persist_field_cta(const CUtensorMap* mapJ, const CUtensorMap* ma
                 // the couplings depend on nothing of the sweep: issued before the wait below
                 mbar_expect_tx(&full[s], (uint32_t)ntl * kTileBytes);
                 for (int u = 0; u < ntl; ++u)
-                    tma_load_2d(st + (size_t)u * kTileBytes, mapJ, k * 128, (j + u * a.nG) * 128, &full[s], pol);
+                    tma_load_2d(st + (size_t)u * kTileBytes, mapJ, b * 128, (j + u * a.nG) * 128, &full[s], pol);
                 blk[s] = k;
                 b_in[s] = false;
                 if (!wait_at_least(&D_count[k % Q], (uint32_t)(k / Q + 1) * (uint32_t)a.nC, d.err, nowait)) {
@@ -249,7 +255,7 @@ __device__ void persist_field_cta(const CUtensorMap* mapJ, const CUtensorMap* ma
         // ---------------- MMA issue (thread 0) and epilogue (warps 0..3) ----------------
         const uint32_t idesc = (1u << 4) | ((uint32_t)(R >> 3) << 17) | ((128u >> 4) << 24);
         int last_commit = -1;
-        for (int k = 0; k < nb; ++k) {
+        for (int k = 0; k < nk; ++k) {
             const int s = k % nst;
             const uint32_t ph = (uint32_t)(k / nst) & 1u;
             if (tid == 0 && !*abort_flag) {
@@ -282,16 +288,21 @@ __device__ void persist_field_cta(const CUtensorMap* mapJ, const CUtensorMap* ma
                     last_commit = k;
                 }
             }
-            // publish tile t = k + L + 1 once block k is in it (its chain block needs exactly that)
+            // publish the tile of chain block kc = k + L + 1 once block k is in it (its chain
+            // block needs exactly that)
+            const int kc = k + L + 1;
             int pub_u = -1;
-            for (int u = 0; u < ntl; ++u)
-                if (j + u * a.nG == k + L + 1) pub_u = u;
+            if (kc < nk)
+                for (int u = 0; u < ntl; ++u)
+                    if (j + u * a.nG == kc % nb) pub_u = u;
             if (pub_u >= 0) {
                 bar_epilogue();
                 if (!*abort_flag) {
                     if (mbar_wait_or_abort(&mdone[s], ph, d.err, nowait, abort_flag)) {
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const int row = (k + L + 1) * 128 + 32 * warp + lane;
+                        // Hpub is [replica][row]: a warp's 32 rows of one replica are 128
+                        // contiguous bytes
+                        const int row = (kc % nb) * 128 + 32 * warp + lane;
                         for (int c = 0; c < R / 32; ++c) {
                             uint32_t v[32];
                             tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(pub_u * R + 32 * c), v);
@@ -300,6 +311,7 @@ __device__ void persist_field_cta(const CUtensorMap* mapJ, const CUtensorMap* ma
                                 __stcg(a.Hpub + (int64_t)(32 * c + q) * Np + row,
                                        __float2int_rn(__uint_as_float(v[q])));
                         }
+                        fence_proxy_async_global();  // read by the chains' TMA copies
                     } else {
                         atomicOr(d.err, 128);
                         *abort_flag = 1;
@@ -308,13 +320,17 @@ __device__ void persist_field_cta(const CUtensorMap* mapJ, const CUtensorMap* ma
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 bar_epilogue();
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                if (tid == 0 && !*abort_flag) red_release_add(&H_ready[k + L + 1], 1u);
+                // H_ready[tile] = kc + 1: the tile holds every block before kc - L
+                if (tid == 0 && !*abort_flag)
+                    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&H_ready[kc % nb]),
+                                 "r"((uint32_t)(kc + 1))
+                                 : "memory");
             }
         }
         bar_epilogue();
         // final fields back to H once the last MMAs are done
         if (!*abort_flag) {
-            const int kl = nb - 1;
+            const int kl = nk - 1;
             if (mbar_wait_or_abort(&mdone[kl % nst], (uint32_t)(kl / nst) & 1u, d.err, nowait, abort_flag)) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 for (int u = 0; u < ntl; ++u) {
@@ -346,20 +362,22 @@ __device__ void persist_field_cta(const CUtensorMap* mapJ, const CUtensorMap* ma
 // ------------------------------------------------------------------------------------------
 // chain CTA: warp W (lane 0) stages the blocks, warps 0..W-1 are the replicas' chains
 // ------------------------------------------------------------------------------------------
-template <int W>
+template <int W, int L>
 __device__ void persist_chain_cta(const SkDev& d, const SkPersistArgs& a, const SkPersistMaps& m,
                                   uint8_t* smem, uint64_t* bars, volatile int* abort_flag) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int c = blockIdx.x - a.nG;
     const int r0 = c * W;
-    const int Np = d.Np, R = d.R, nb = a.nb, Q = a.Q, L = a.L;
+    const int Np = d.Np, R = d.R, nb = a.nb;
+    constexpr int Q = kSkPersistSlots;
+    const int nk = a.n_sweeps * nb;
     const int words = Np / 32;
     const bool nowait = d.test_nowait != 0;
     uint32_t* Ssm = reinterpret_cast<uint32_t*>(smem);          // [W][words] spin words
-    uint32_t* Fsm = Ssm + (size_t)W * words;                     // [W][words] flips of this sweep
+    uint32_t* Fsm = Ssm + (size_t)W * words;                     // [W][words] latest flips
     uint8_t* ring = smem + chain_words_bytes(W, Np);
     const size_t stb = chain_stage_bytes(W, L);
-    uint64_t* fullc = bars;                   // [kChainStages]: the stage's three copies landed
+    uint64_t* fullc = bars;                   // [kChainStages]: the stage's copies landed
     uint64_t* emptyc = bars + kChainStages;   // [kChainStages]: W replica warps done
     uint32_t* D_count = a.sync;
     uint32_t* D_free = a.sync + Q;
@@ -382,52 +400,56 @@ __device__ void persist_chain_cta(const SkDev& d, const SkPersistArgs& a, const 
     __syncthreads();
 
     if (warp == W) {
-        // ---------------- helper: stage block b (couplings, K*, fields) ----------------
+        // ---------------- staging warp: block k (couplings, K*, fields) ----------------
         if (lane == 0) {
-            const uint32_t stage_tx = (uint32_t)((L + 1) * 4 + 2 * W) * 512u;
+            const uint32_t stage_tx = (uint32_t)chain_stage_bytes(W, L);
             const uint64_t pol = l2_evict_last();
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&m.jb)) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&m.hpub)) : "memory");
             int last_fill[kChainStages] = {-1, -1};
-            auto prefetch = [&](int b) -> bool {
-                const int s = b % kChainStages;
-                // ring slot b mod Q: its previous contents (block b - Q) read by every field CTA
-                if (b >= Q && !wait_at_least(&D_free[b % Q], (uint32_t)(b / Q) * (uint32_t)a.nG, d.err, nowait)) {
+            auto prefetch = [&](int k) -> bool {
+                const int s = k % kChainStages;
+                const int b = k % nb, sw = k / nb;
+                // ring slot k mod Q: its previous contents (block k - Q) read by every field CTA
+                if (k >= Q && !wait_at_least(&D_free[k % Q], (uint32_t)(k / Q) * (uint32_t)a.nG, d.err, nowait)) {
                     atomicOr(d.err, 512);
                     return false;
                 }
-                const bool pub = b > L;
-                if (pub) {
-                    if (!wait_at_least(&H_ready[b], 1u, d.err, nowait)) {
-                        atomicOr(d.err, 1024);
-                        return false;
-                    }
-                    fence_proxy_async_global();  // the fields were written by generic stores
+                const bool pub = k > L;
+                if (pub && !wait_at_least(&H_ready[b], (uint32_t)(k + 1), d.err, nowait)) {
+                    atomicOr(d.err, 1024);
+                    return false;
                 }
+                if (pub) fence_proxy_async_global();  // the fields were written by generic stores
                 uint8_t* st = ring + (size_t)s * stb;
                 uint32_t* Jw = reinterpret_cast<uint32_t*>(st);                    // [(L+1)*4][128]
-                int32_t* ks = reinterpret_cast<int32_t*>(Jw + (L + 1) * 4 * 128);  // [W][128]
-                int32_t* hs = ks + W * 128;                                         // [W][128]
-                const int p0 = b > L ? b - L : 0;
+                int16_t* ks = reinterpret_cast<int16_t*>(Jw + (L + 1) * 4 * 128);  // [W][128]
+                int32_t* hs = reinterpret_cast<int32_t*>(ks + W * 128);           // [W][128]
                 mbar_expect_tx(&fullc[s], stage_tx);
-                tma_load_2d(Jw, &m.jb, b * 128, p0 * 4, &fullc[s], pol);
-                tma_load_2d(ks, &m.kst, b * 128, r0, &fullc[s], pol);
+                // couplings of block b's rows with the columns of blocks k - L .. k (cyclic in
+                // the sweep; a block before the launch's first is never folded, any rows do)
+                for (int i = 0; i <= L; ++i) {
+                    int bi = b - L + i;
+                    if (bi < 0) bi += nb;  // L < nb
+                    tma_load_2d(Jw + i * 4 * 128, &m.jb, b * 128, bi * 4, &fullc[s], pol);
+                }
+                tma_load_2d(ks, &m.kst, b * 128, sw * R + r0, &fullc[s], pol);
                 tma_load_2d(hs, pub ? &m.hpub : &m.h, b * 128, r0, &fullc[s], pol);
-                last_fill[s] = b;
+                last_fill[s] = k;
                 return true;
             };
             bool ok = true;
-            for (int b = 0; b < kChainStages && b < nb && ok; ++b) ok = prefetch(b);
-            for (int b = 0; b < nb && ok; ++b) {
-                const int s = b % kChainStages;
-                if (!mbar_wait_or_abort(&emptyc[s], (uint32_t)(b / kChainStages) & 1u, d.err, nowait,
+            for (int k = 0; k < kChainStages && k < nk && ok; ++k) ok = prefetch(k);
+            for (int k = 0; k < nk && ok; ++k) {
+                const int s = k % kChainStages;
+                if (!mbar_wait_or_abort(&emptyc[s], (uint32_t)(k / kChainStages) & 1u, d.err, nowait,
                                         abort_flag)) {
                     atomicOr(d.err, 2048);
                     ok = false;
                     break;
                 }
-                red_release_add(&D_count[b % Q], 1u);
-                if (b + kChainStages < nb) ok = prefetch(b + kChainStages);
+                red_release_add(&D_count[k % Q], 1u);
+                if (k + kChainStages < nk) ok = prefetch(k + kChainStages);
             }
             if (!ok) {
                 *abort_flag = 1;
@@ -443,9 +465,9 @@ __device__ void persist_chain_cta(const SkDev& d, const SkPersistArgs& a, const 
         uint32_t* Sw = Ssm + warp * words;
         uint32_t* Fw = Fsm + warp * words;
         const uint32_t lane_bit = 1u << lane;
-        for (int b = 0; b < nb; ++b) {
-            const int s = b % kChainStages;
-            if (!mbar_wait_or_abort(&fullc[s], (uint32_t)(b / kChainStages) & 1u, d.err, nowait,
+        for (int k = 0, b = 0; k < nk; ++k, b = (b + 1 == nb) ? 0 : b + 1) {
+            const int s = k & (kChainStages - 1);
+            if (!mbar_wait_or_abort(&fullc[s], (uint32_t)(k / kChainStages) & 1u, d.err, nowait,
                                     abort_flag)) {
                 if (lane == 0) atomicOr(d.err, 4096);
                 *abort_flag = 1;
@@ -453,38 +475,56 @@ __device__ void persist_chain_cta(const SkDev& d, const SkPersistArgs& a, const 
             }
             const uint8_t* st = ring + (size_t)s * stb;
             const uint32_t* Jw = reinterpret_cast<const uint32_t*>(st);
-            const int32_t* ks = reinterpret_cast<const int32_t*>(Jw + (L + 1) * 4 * 128) + warp * 128;
-            const int32_t* hs = reinterpret_cast<const int32_t*>(Jw + (L + 1) * 4 * 128) + W * 128 + warp * 128;
-            const int p0 = b > L ? b - L : 0;
-            const uint32_t* Jown = Jw + (b - p0) * 4 * 128;  // [4 column words][128 rows]
+            const int16_t* ks16 = reinterpret_cast<const int16_t*>(Jw + (L + 1) * 4 * 128);
+            const int16_t* ks = ks16 + warp * 128;
+            const int32_t* hs = reinterpret_cast<const int32_t*>(ks16 + W * 128) + warp * 128;
+            const uint32_t* Jown = Jw + L * 4 * 128;  // [4 column words][128 rows] of block b
             int h[4], kst[4];
-            uint32_t sw[4];
+            uint32_t sw[4], jd[4], jl[6];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 h[q] = hs[32 * q + lane];
                 kst[q] = ks[32 * q + lane];
                 sw[q] = Sw[b * 4 + q];
+                jd[q] = Jown[q * 128 + 32 * q + lane];  // couplings inside chunk q
             }
-            // flips of blocks p0 .. b - 1 (this sweep) not yet in the staged fields
-            for (int p = p0; p < b; ++p) {
-                const uint32_t* Jp = Jw + (p - p0) * 4 * 128;
+            // couplings of chunk q's columns with the rows of a later chunk q2
+            jl[0] = Jown[0 * 128 + 32 * 1 + lane];
+            jl[1] = Jown[0 * 128 + 32 * 2 + lane];
+            jl[2] = Jown[0 * 128 + 32 * 3 + lane];
+            jl[3] = Jown[1 * 128 + 32 * 2 + lane];
+            jl[4] = Jown[1 * 128 + 32 * 3 + lane];
+            jl[5] = Jown[2 * 128 + 32 * 3 + lane];
+            // flips of blocks k - L .. k - 1 of this launch, which the staged fields do not
+            // hold yet (each block's latest flips: L < nb); all loads first, then the popcounts
+#pragma unroll
+            for (int i = 0; i < L; ++i) {
+                const int kp = k - L + i;
+                int bp = b - L + i;
+                if (bp < 0) bp += nb;  // L < nb
+                const uint32_t* Jp = Jw + i * 4 * 128;
+                uint32_t Fv[4], sv[4], jv[4][4];
 #pragma unroll
                 for (int cp = 0; cp < 4; ++cp) {
-                    const uint32_t F = Fw[p * 4 + cp];
-                    if (!F) continue;
-                    const uint32_t sn = Sw[p * 4 + cp];
-                    const int pf = __popc(F);
+                    Fv[cp] = kp >= 0 ? Fw[bp * 4 + cp] : 0u;
+                    sv[cp] = Sw[bp * 4 + cp];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) jv[cp][q] = Jp[cp * 128 + 32 * q + lane];
+                }
+#pragma unroll
+                for (int cp = 0; cp < 4; ++cp) {
+                    const int pf = __popc(Fv[cp]);
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
-                        h[q] += 2 * (pf - 2 * __popc(F & (Jp[cp * 128 + 32 * q + lane] ^ sn)));
+                        h[q] += 2 * (pf - 2 * __popc(Fv[cp] & (jv[cp][q] ^ sv[cp])));
                 }
             }
-            uint8_t* Dslot = a.Dring + ((int64_t)(b % Q) * R + r) * 128;
+            uint8_t* Dslot = a.Dring + ((int64_t)(k % Q) * R + r) * 128;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const uint32_t sbit = (sw[q] >> lane) & 1u;
                 const int x = sbit ? -h[q] : h[q];
-                const uint32_t neg = Jown[q * 128 + 32 * q + lane] ^ sw[q] ^ (sbit ? 0xFFFFFFFFu : 0u);
+                const uint32_t neg = jd[q] ^ sw[q] ^ (sbit ? 0xFFFFFFFFu : 0u);
                 uint32_t F = 0, last = 0;
                 int cur = x;
                 for (;;) {
@@ -502,16 +542,18 @@ __device__ void persist_chain_cta(const SkDev& d, const SkPersistArgs& a, const 
                     Sw[b * 4 + q] = nsw;
                     Fw[b * 4 + q] = F;
                 }
-                if (F) {
+                {
                     const int pf = __popc(F);
 #pragma unroll
-                    for (int q2 = q + 1; q2 < 4; ++q2)
-                        h[q2] += 2 * (pf - 2 * __popc(F & (Jown[q * 128 + 32 * q2 + lane] ^ nsw)));
+                    for (int q2 = q + 1; q2 < 4; ++q2) {
+                        const uint32_t jw = jl[q == 0 ? q2 - 1 : (q == 1 ? q2 + 1 : 5)];
+                        h[q2] += 2 * (pf - 2 * __popc(F & (jw ^ nsw)));
+                    }
                 }
                 sw[q] = nsw;
             }
-            // D_b of this replica is written: order it for the tensor-core readers, then
-            // release the stage (the helper publishes the block once every warp is done)
+            // D_k of this replica is written: order it for the tensor-core readers, then
+            // release the stage (the staging warp publishes the block once every warp is done)
             fence_proxy_async_global();
             __syncwarp();
             if (lane == 0) mbar_arrive(&emptyc[s]);
@@ -524,7 +566,7 @@ __device__ void persist_chain_cta(const SkDev& d, const SkPersistArgs& a, const 
     }
 }
 
-template <int W>
+template <int W, int L>
 __global__ void __launch_bounds__(32 * (W + 1), 1)
     k_sk_persist(const __grid_constant__ CUtensorMap mapJ, const __grid_constant__ CUtensorMap mapD,
                  const __grid_constant__ SkPersistMaps maps, SkDev d, SkPersistArgs a) {
@@ -538,7 +580,7 @@ __global__ void __launch_bounds__(32 * (W + 1), 1)
     if ((int)blockIdx.x < a.nG)
         persist_field_cta<W>(&mapJ, &mapD, d, a, smem, bars, &tslot, &abort_flag);
     else
-        persist_chain_cta<W>(d, a, maps, smem, bars, &abort_flag);
+        persist_chain_cta<W, L>(d, a, maps, smem, bars, &abort_flag);
 }
 
 size_t sk_persist_smem_bytes(const SkDev& d, const SkPersistArgs& a) {
@@ -549,19 +591,25 @@ size_t sk_persist_smem_bytes(const SkDev& d, const SkPersistArgs& a) {
     return need > floor_one_per_sm ? need : floor_one_per_sm;
 }
 
-static void* persist_kernel(int W) {
-    if (W == 4) return (void*)k_sk_persist<4>;
-    if (W == 8) return (void*)k_sk_persist<8>;
+// lookaheads compiled in (the fold of L blocks is unrolled)
+#define SG_PERSIST_KERNELS(X) X(4, 2) X(4, 4) X(4, 6) X(4, 8) X(8, 2) X(8, 4) X(8, 6) X(8, 8)
+
+static void* persist_kernel(int W, int L) {
+#define SG_PERSIST_PICK(w, l) if (W == w && L == l) return (void*)k_sk_persist<w, l>;
+    SG_PERSIST_KERNELS(SG_PERSIST_PICK)
+#undef SG_PERSIST_PICK
     return nullptr;
 }
 
+int sk_persist_lookahead_supported(int L) { return L == 2 || L == 4 || L == 6 || L == 8; }
+
 int sk_persist_fits(const SkDev& d, const SkPersistArgs& a, int num_sms) {
-    void* kern = persist_kernel(a.W);
+    void* kern = persist_kernel(a.W, a.L);
     // R: whole 32-column chunks of tensor memory, at most one TMA box of spin changes; L >= 1
     // whenever a tile is published (the helper stages two blocks ahead of the chain)
-    if (!kern || d.R < 32 || d.R > 256 || d.R % 32 || a.nst < 2 || a.nst > 4 || a.Q < 2 ||
-        a.L < 0 || (a.nb > 1 && a.L < 1) || (a.L + 1) * 4 > 256 || a.TPC * d.R > 512 ||
-        a.nC * a.W != d.R)
+    if (!kern || d.R < 32 || d.R > 256 || d.R % 32 || a.nst < 2 || a.nst > 4 || a.Q != kSkPersistSlots ||
+        a.L < 1 || a.L >= a.nb || a.TPC * d.R > 512 || a.nC * a.W != d.R || a.n_sweeps < 1 ||
+        a.n_sweeps > kSkPersistMaxSweeps)
         return 0;
     const size_t smem = sk_persist_smem_bytes(d, a);
     if (smem > 227 * 1024) return 0;
@@ -579,11 +627,13 @@ int sk_persist_fits(const SkDev& d, const SkPersistArgs& a, int num_sms) {
     return per_sm >= 1 && a.nG + a.nC <= per_sm * num_sms;
 }
 
-int sk_persist_sweep(const SkDev& d, const SkPersistArgs& a, const CUtensorMap& mapJ,
-                     const CUtensorMap& mapD, const SkPersistMaps& maps, cudaStream_t st) {
-    void* kern = persist_kernel(a.W);
-    if (!kern) return -1;
-    if (cudaMemsetAsync(a.sync, 0, (size_t)(2 * a.Q + a.nb) * 4, st) != cudaSuccess) return -1;
+int sk_persist_sweeps(const SkDev& d, const SkPersistArgs& a, const CUtensorMap& mapJ,
+                      const CUtensorMap& mapD, const SkPersistMaps& maps, cudaStream_t st) {
+    if (!persist_kernel(a.W, a.L) || a.n_sweeps < 1 || a.n_sweeps > kSkPersistMaxSweeps) return -1;
+    // K* of every sweep of the launch, with the whole GPU
+    sk_kstar16_sweeps(d, a.clock, a.t_off, a.n_sweeps, a.kst16, st);
+    if (cudaMemsetAsync(a.sync, 0, (size_t)(2 * kSkPersistSlots + a.nb) * 4, st) != cudaSuccess)
+        return -1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(a.nG + a.nC));
     cfg.blockDim = dim3((unsigned)(32 * (a.W + 1)));
@@ -594,10 +644,12 @@ int sk_persist_sweep(const SkDev& d, const SkPersistArgs& a, const CUtensorMap& 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e;
-    if (a.W == 4) e = cudaLaunchKernelEx(&cfg, k_sk_persist<4>, mapJ, mapD, maps, d, a);
-    else e = cudaLaunchKernelEx(&cfg, k_sk_persist<8>, mapJ, mapD, maps, d, a);
-    return e == cudaSuccess ? 1 : -1;
+    cudaError_t e = cudaErrorInvalidValue;
+#define SG_PERSIST_LAUNCH(w, l) \
+    if (a.W == w && a.L == l) e = cudaLaunchKernelEx(&cfg, k_sk_persist<w, l>, mapJ, mapD, maps, d, a);
+    SG_PERSIST_KERNELS(SG_PERSIST_LAUNCH)
+#undef SG_PERSIST_LAUNCH
+    return e == cudaSuccess ? 2 : -1;
 }
 
 }  // namespace sg

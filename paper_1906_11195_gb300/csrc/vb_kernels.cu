@@ -806,9 +806,12 @@ __device__ __forceinline__ void count_flush(uint64_t (&p)[NQ][PW], const VbCount
             c1 |= (uint32_t)((p[q][b] >> (lane + 32)) & 1ull) << b;
         }
         int64_t* base = job.dst + g * job.stride_g + q * job.stride_r;
-        if (c0) atomicAdd((unsigned long long*)(base + lane * job.stride_k), (unsigned long long)c0);
+        if (c0)
+            atomicAdd((unsigned long long*)(base + lane * job.stride_k),
+                      (unsigned long long)c0 << job.shift);
         if (c1)
-            atomicAdd((unsigned long long*)(base + (lane + 32) * job.stride_k), (unsigned long long)c1);
+            atomicAdd((unsigned long long*)(base + (lane + 32) * job.stride_k),
+                      (unsigned long long)c1 << job.shift);
 #pragma unroll
         for (int b = 0; b < PW; ++b) p[q][b] = 0ull;
     }
@@ -884,23 +887,33 @@ __global__ void __launch_bounds__(256, EN ? (R <= 2 ? 2 : 1) : (R <= 2 ? 3 : 2))
     }
 }
 
-int vb_packed_count(const VbPackedDev& d, const VbCountJob& job, cudaStream_t st) {
+// The energy job (kind 2) runs over the upper entries when the layout has them: each edge once,
+// from its lower-colour endpoint (the higher slot), counted twice (shift 1).
+int vb_packed_count(const VbPackedDev& d, const VbCountJob& job_in, cudaStream_t st) {
+    VbCountJob job = job_in;
+    VbPackedDev dd = d;
+    if (job.kind == 2 && d.up_slice_base) {
+        dd.slice_base = d.up_slice_base;
+        dd.col = d.up_col;
+        dd.jb = d.up_jb;
+        job.shift = 1;
+    }
     const int bs = 256;
     const int64_t warps = (d.n_slices + kCountSlicesPerWarp - 1) / kCountSlicesPerWarp;
     const unsigned nb = (unsigned)((warps + (bs / 32) - 1) / (bs / 32));
     const bool en = job.kind == 2;
     switch (d.R) {
         case 1:
-            if (en) k_vb_packed_count<1, true><<<nb, bs, 0, st>>>(d, job);
-            else k_vb_packed_count<1, false><<<nb, bs, 0, st>>>(d, job);
+            if (en) k_vb_packed_count<1, true><<<nb, bs, 0, st>>>(dd, job);
+            else k_vb_packed_count<1, false><<<nb, bs, 0, st>>>(dd, job);
             break;
         case 2:
-            if (en) k_vb_packed_count<2, true><<<nb, bs, 0, st>>>(d, job);
-            else k_vb_packed_count<2, false><<<nb, bs, 0, st>>>(d, job);
+            if (en) k_vb_packed_count<2, true><<<nb, bs, 0, st>>>(dd, job);
+            else k_vb_packed_count<2, false><<<nb, bs, 0, st>>>(dd, job);
             break;
         case 4:
-            if (en) k_vb_packed_count<4, true><<<nb, bs, 0, st>>>(d, job);
-            else k_vb_packed_count<4, false><<<nb, bs, 0, st>>>(d, job);
+            if (en) k_vb_packed_count<4, true><<<nb, bs, 0, st>>>(dd, job);
+            else k_vb_packed_count<4, false><<<nb, bs, 0, st>>>(dd, job);
             break;
         default: return -1;
     }

@@ -11,20 +11,23 @@ random interleavings with the kernel's waits as blocking conditions and checks:
   * the fields a chain block starts from, plus the blocks it folds in itself, are exactly the
     blocks before it, each once (the sequential order of the sweep),
   * a field CTA reads every ring slot before it is overwritten, and reads the block it expects.
-Planted mistakes (no lookahead with a two-deep staging ring, a fold window one block short, no
-D_free wait) are each caught.
+Several sweeps run in one launch (blocks k = s nb + b; the fold window and the publishes run
+across sweep boundaries).  Planted mistakes (no lookahead with a two-deep staging ring, a fold
+window one block short, no D_free wait) are each caught.
 """
 import random
 
 import pytest
 
 
-def run_protocol(nb, nC, nG, TPC, L, Q, S_C=2, seed=0, fold_short=False, skip_free=False,
-                 max_steps=200000):
+def run_protocol(nb, nC, nG, TPC, L, Q, S_C=2, n_sweeps=1, seed=0, fold_short=False,
+                 skip_free=False, max_steps=400000):
+    """One launch of n_sweeps sweeps; blocks are numbered k = s nb + b over the launch."""
     rng = random.Random(seed)
+    nk = n_sweeps * nb
     D_count = [0] * Q
     D_free = [0] * Q
-    H_ready = [False] * nb
+    H_ready = [0] * nb          # chain block + 1 of the latest publish of each tile
     slot = [None] * Q           # block held by each ring slot (per chain CTA: same schedule)
     slot_writes = [[0] * Q for _ in range(nC)]
     published = {}              # tile -> set of blocks applied when published
@@ -32,29 +35,30 @@ def run_protocol(nb, nC, nG, TPC, L, Q, S_C=2, seed=0, fold_short=False, skip_fr
     applied = {t: set() for t in range(nb)}
     errors = []
 
-    # chain CTA state: the helper runs its operations in program order, as the kernel does:
-    # stage blocks 0 .. S_C - 1, then for every block b: publish D(b), stage b + S_C
-    ops = [("stage", b) for b in range(min(S_C, nb))]
-    for b in range(nb):
-        ops.append(("publish", b))
-        if b + S_C < nb:
-            ops.append(("stage", b + S_C))
+    # chain CTA state: the staging warp runs its operations in program order, as the kernel
+    # does: stage blocks 0 .. S_C - 1, then for every block k: publish D(k), stage k + S_C
+    ops = [("stage", k) for k in range(min(S_C, nk))]
+    for k in range(nk):
+        ops.append(("publish", k))
+        if k + S_C < nk:
+            ops.append(("stage", k + S_C))
     helper_pc = [0] * nC
     staged = [dict() for _ in range(nC)]   # block -> fields (set of blocks included)
-    chain_b = [0] * nC          # next block the replica warps process
+    chain_k = [0] * nC          # next block the replica warps process
     done_chain = [set() for _ in range(nC)]
-    # field CTA state
+    # field CTA state: the MMA issuer walks the blocks
     gemm_k = [0] * nG
 
     def helper_ready(c):
         if helper_pc[c] >= len(ops):
             return False
-        op, b = ops[helper_pc[c]]
+        op, k = ops[helper_pc[c]]
         if op == "publish":
-            return b in done_chain[c]
-        if b >= Q and not skip_free and D_free[b % Q] < (b // Q) * nG:
+            return k in done_chain[c]
+        b = k % nb
+        if k >= Q and not skip_free and D_free[k % Q] < (k // Q) * nG:
             return False
-        return b <= L or H_ready[b]
+        return k <= L or H_ready[b] >= k + 1
 
     steps = 0
     while True:
@@ -66,73 +70,73 @@ def run_protocol(nb, nC, nG, TPC, L, Q, S_C=2, seed=0, fold_short=False, skip_fr
         for c in range(nC):
             if helper_ready(c):
                 actions.append(("helper", c))
-            cb = chain_b[c]
-            if cb < nb and cb in staged[c]:
+            ck = chain_k[c]
+            if ck < nk and ck in staged[c]:
                 actions.append(("chain", c))
         for j in range(nG):
             k = gemm_k[j]
-            if k < nb and D_count[k % Q] >= (k // Q + 1) * nC:
+            if k < nk and D_count[k % Q] >= (k // Q + 1) * nC:
                 actions.append(("gemm", j))
         if not actions:
             break
         kind, x = rng.choice(actions)
         if kind == "helper":
-            op, b = ops[helper_pc[x]]
+            op, k = ops[helper_pc[x]]
             if op == "publish":
-                D_count[b % Q] += 1
+                D_count[k % Q] += 1
             else:
-                staged[x][b] = set() if b <= L else set(published[b])
+                staged[x][k] = set() if k <= L else set(published[k % nb])
             helper_pc[x] += 1
         elif kind == "chain":
-            c, b = x, chain_b[x]
-            fields = staged[c].pop(b)
-            p0 = b - L if b > L else 0
-            if fold_short and b > L:
+            c, k = x, chain_k[x]
+            fields = staged[c].pop(k)
+            p0 = max(0, k - L)
+            if fold_short and k > L:
                 p0 += 1
-            folded = set(range(p0, b))
-            if fields & folded or (fields | folded) != set(range(b)):
-                errors.append(f"chain {c} block {b}: fields {sorted(fields)} folded {sorted(folded)}")
-            # write ring slot b mod Q
-            s = b % Q
-            if slot_writes[c][s] != b // Q:
+            folded = set(range(p0, k))
+            if fields & folded or (fields | folded) != set(range(k)):
+                errors.append(f"chain {c} block {k}: fields {sorted(fields)} folded {sorted(folded)}")
+            s = k % Q
+            if slot_writes[c][s] != k // Q:
                 errors.append(f"chain {c}: slot {s} written out of order")
             slot_writes[c][s] += 1
             if c == 0:
-                slot[s] = b
-            done_chain[c].add(b)
-            chain_b[c] += 1
+                slot[s] = k
+            done_chain[c].add(k)
+            chain_k[c] += 1
         else:  # field CTA issuer
             j, k = x, gemm_k[x]
             if slot[k % Q] != k:
                 errors.append(f"field CTA {j}: slot {k % Q} holds {slot[k % Q]}, expected block {k}")
             D_free[k % Q] += 1
+            b = k % nb
             for t in tiles[j]:
-                applied[t].add(k)
-            for t in tiles[j]:
-                if t == k + L + 1:
-                    published[t] = set(applied[t])
-                    H_ready[t] = True
+                applied[t].add(k)  # block k (block b of its sweep) reaches every tile
+            kc = k + L + 1
+            if kc < nk and kc % nb in tiles[j]:
+                published[kc % nb] = set(applied[kc % nb])
+                H_ready[kc % nb] = kc + 1
             gemm_k[j] += 1
-    finished = all(cb == nb for cb in chain_b) and all(k == nb for k in gemm_k)
+    finished = all(ck == nk for ck in chain_k) and all(k == nk for k in gemm_k)
     return finished, errors
 
 
 CONFIGS = [
-    # nb, nC, nG, TPC, L, Q
-    (64, 64, 64, 1, 6, 8),    # N = 8192, R = 256
-    (128, 32, 64, 2, 6, 8),   # N = 16384, R = 128
-    (4, 4, 4, 1, 3, 8),       # N = 512: no tile is ever published (L >= nb - 1)
-    (5, 8, 3, 2, 1, 2),       # smallest lookahead and ring
-    (17, 3, 9, 2, 2, 3),      # ragged tile ownership
-    (1, 4, 1, 1, 0, 8),       # one block
+    # nb, nC, nG, TPC, L, Q, sweeps
+    (64, 64, 64, 1, 6, 8, 1),    # N = 8192, R = 256, one sweep
+    (64, 64, 64, 1, 6, 8, 3),    # the same, three sweeps in one launch
+    (128, 32, 64, 2, 6, 8, 2),   # N = 16384, R = 128
+    (7, 8, 3, 3, 6, 8, 4),       # L = nb - 1: the largest window
+    (5, 8, 3, 2, 2, 2, 3),       # smallest lookahead and ring
+    (17, 3, 9, 2, 4, 3, 2),      # ragged tile ownership
 ]
 
 
 @pytest.mark.parametrize("cfg", CONFIGS)
 def test_protocol_finishes_and_keeps_the_sequential_order(cfg):
-    nb, nC, nG, TPC, L, Q = cfg
-    for seed in range(12):
-        finished, errors = run_protocol(nb, nC, nG, TPC, L, Q, seed=seed)
+    nb, nC, nG, TPC, L, Q, S = cfg
+    for seed in range(8):
+        finished, errors = run_protocol(nb, nC, nG, TPC, L, Q, n_sweeps=S, seed=seed)
         assert not errors, errors[:3]
         assert finished, f"deadlock with seed {seed}"
 
@@ -143,7 +147,7 @@ def test_no_lookahead_with_two_staged_blocks_deadlocks():
 
 
 def test_fold_window_one_block_short_is_caught():
-    _, errors = run_protocol(16, 4, 8, 2, 3, 4, seed=2, fold_short=True)
+    _, errors = run_protocol(16, 4, 8, 2, 3, 4, n_sweeps=2, seed=2, fold_short=True)
     assert errors
 
 
