@@ -780,10 +780,13 @@ __device__ __forceinline__ void count_add(uint64_t (&p)[NQ][PW], int q, uint64_t
 }
 
 // Sum the bit-sliced counters of the 32 lanes with a butterfly of bit-sliced additions, then
-// lane l writes the totals of spin lanes l and l + 32.
+// lane l adds the totals of spin lanes l and l + 32.  With a CTA-shared accumulator (cta_acc,
+// [NQ][64], one graph per CTA run) the warp adds there and the CTA flushes once; otherwise
+// straight into global memory.
 template <int NQ, int PW>
 __device__ __forceinline__ void count_flush(uint64_t (&p)[NQ][PW], const VbCountJob& job,
-                                            uint32_t g, int nq, uint32_t lane) {
+                                            uint32_t g, int nq, uint32_t lane,
+                                            unsigned long long* cta_acc = nullptr) {
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         if (q >= nq) break;
@@ -805,13 +808,18 @@ __device__ __forceinline__ void count_flush(uint64_t (&p)[NQ][PW], const VbCount
             c0 |= (uint32_t)((p[q][b] >> lane) & 1ull) << b;
             c1 |= (uint32_t)((p[q][b] >> (lane + 32)) & 1ull) << b;
         }
-        int64_t* base = job.dst + g * job.stride_g + q * job.stride_r;
-        if (c0)
-            atomicAdd((unsigned long long*)(base + lane * job.stride_k),
-                      (unsigned long long)c0 << job.shift);
-        if (c1)
-            atomicAdd((unsigned long long*)(base + (lane + 32) * job.stride_k),
-                      (unsigned long long)c1 << job.shift);
+        if (cta_acc) {
+            if (c0) atomicAdd(cta_acc + q * 64 + lane, (unsigned long long)c0);
+            if (c1) atomicAdd(cta_acc + q * 64 + lane + 32, (unsigned long long)c1);
+        } else {
+            int64_t* base = job.dst + g * job.stride_g + q * job.stride_r;
+            if (c0)
+                atomicAdd((unsigned long long*)(base + lane * job.stride_k),
+                          (unsigned long long)c0 << job.shift);
+            if (c1)
+                atomicAdd((unsigned long long*)(base + (lane + 32) * job.stride_k),
+                          (unsigned long long)c1 << job.shift);
+        }
 #pragma unroll
         for (int b = 0; b < PW; ++b) p[q][b] = 0ull;
     }
@@ -832,6 +840,16 @@ __global__ void __launch_bounds__(256, EN ? (R <= 2 ? 2 : 1) : (R <= 2 ? 3 : 2))
     // kind 3: one pass per snapshot over this warp's slices; the current spins of the slices
     // (a few KB) stay in L1 after the first pass
     const int passes = job.kind == 3 ? job.w : 1;
+    // The CTA's slices belong to one graph (the common case: a single instance, or slices of
+    // one graph in a batch): the warps add into a shared accumulator and the CTA flushes it once,
+    // so the global counters see one atomic per CTA instead of one per warp.
+    __shared__ unsigned long long acc[NQ * 64];
+    __shared__ int one_graph;
+    const int64_t cta_lo = (int64_t)blockIdx.x * (blockDim.x / 32) * kCountSlicesPerWarp;
+    int64_t cta_hi = cta_lo + (int64_t)(blockDim.x / 32) * kCountSlicesPerWarp;
+    if (cta_hi > d.n_slices) cta_hi = d.n_slices;
+    if (threadIdx.x == 0)
+        one_graph = cta_lo < cta_hi && __ldg(d.slice_graph + cta_lo) == __ldg(d.slice_graph + cta_hi - 1);
     for (int pass = 0; pass < passes; ++pass) {
         VbCountJob jb = job;
         if (job.kind == 3) {
@@ -848,13 +866,16 @@ __global__ void __launch_bounds__(256, EN ? (R <= 2 ? 2 : 1) : (R <= 2 ? 3 : 2))
             for (int b = 0; b < PW; ++b) p[q][b] = 0ull;
         const uint64_t* snap = d.snap + (int64_t)(kind == 0 ? jb.w : 0) * words;
         int64_t cur_g = -1;
+        for (int q = threadIdx.x; q < NQ * 64; q += blockDim.x) acc[q] = 0ull;
+        __syncthreads();
+        unsigned long long* cta_acc = one_graph ? acc : nullptr;
         // padding slots hold zero words and zero couplings, so they add nothing: no vinfo test,
         // and the loads of several slices can be in flight together
 #pragma unroll 4
         for (int64_t s = s_lo; s < s_hi; ++s) {
             const uint32_t g = __ldg(d.slice_graph + s);  // warp-uniform
             if ((int64_t)g != cur_g) {
-                if (cur_g >= 0) count_flush<NQ, PW>(p, jb, (uint32_t)cur_g, nq, lane);
+                if (cur_g >= 0) count_flush<NQ, PW>(p, jb, (uint32_t)cur_g, nq, lane, cta_acc);
                 cur_g = g;
             }
             const int64_t slot = s * 32 + lane;
@@ -883,7 +904,19 @@ __global__ void __launch_bounds__(256, EN ? (R <= 2 ? 2 : 1) : (R <= 2 ? 3 : 2))
                 }
             }
         }
-        if (cur_g >= 0) count_flush<NQ, PW>(p, jb, (uint32_t)cur_g, nq, lane);
+        if (cur_g >= 0) count_flush<NQ, PW>(p, jb, (uint32_t)cur_g, nq, lane, cta_acc);
+        if (cta_acc) {
+            __syncthreads();
+            const int64_t g = (int64_t)__ldg(d.slice_graph + cta_lo);
+            for (int q = threadIdx.x; q < nq * 64; q += blockDim.x) {
+                const unsigned long long v = acc[q];
+                if (v)
+                    atomicAdd((unsigned long long*)(jb.dst + g * jb.stride_g + (q >> 6) * jb.stride_r +
+                                                    (q & 63) * jb.stride_k),
+                              v << jb.shift);
+            }
+            __syncthreads();
+        }
     }
 }
 
