@@ -400,11 +400,13 @@ def _e2e(create, steps, updates_per_step, dev, stream, sg):
     sg.sg_sweep(h, steps)
     C, q, E = sg.sg_read_results(h)
     dt = time.perf_counter() - t0
+    h2d, d2h = sg.sg_transfer_bytes(h)
     sg.sg_destroy(h)
     del buf
     return {"value": updates_per_step * steps / (dt * 1e9), "unit": "spin updates/ns",
-            "h2d_bytes_per_step": nb // steps, "d2h_bytes_per_step": (C.nbytes + q.nbytes + E.nbytes) // steps,
-            "note": f"attach (H2D of the {nb} B device image) + {steps} sweeps + D2H of all counts"}
+            "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
+            "note": f"attach (H2D of the {h2d} B instance image into a {nb} B workspace) + {steps} "
+                    f"sweeps + D2H of all counts ({d2h} B), counted by the library"}
 
 
 def measure_sk(args, dev, stream, steps, warmup, cpu=True):
@@ -1031,25 +1033,26 @@ def run_gpu(args):
         nb = sg.sg_workspace_bytes(h)
         handles.append((h, nb))
         bufs.append(torch.empty(nb, dtype=torch.uint8, device=dev))
-    h2d = sum(nb for _, nb in handles)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for (h, nb), buf in zip(handles, bufs):
         sg.sg_attach(h, buf.data_ptr(), nb, stream.cuda_stream)
     for h, _ in handles:
         sg.sg_sweep(h, args.warmup + args.steps)
-    d2h = 0
     for h, _ in handles:
         C, q, E = sg.sg_read_results(h)
-        d2h += C.nbytes + q.nbytes + E.nbytes
     e2e_s = time.perf_counter() - t0
+    h2d = d2h = 0
     for h, _ in handles:
+        a, b = sg.sg_transfer_bytes(h)
+        h2d += a
+        d2h += b
         sg.sg_destroy(h)
     e2e_steps = args.warmup + args.steps
     e2e = {"value": ws * updates_per_step * e2e_steps / (e2e_s * 1e9), "unit": "spin updates/ns",
            "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
-           "note": "H2D of the device image of both instances + sweeps + D2H of all counts, "
-                   "bytes spread over the steps"}
+           "note": "H2D of both instances' images at attach + sweeps + D2H of all counts (bytes "
+                   "counted by the library), spread over the steps"}
 
     # the other configurations of the metric, each with its own value, roofline, e2e, clocks
     # and CPU baseline (one GPU only; each is a separate JSON object inside the line)

@@ -242,6 +242,11 @@ int sg_destroy(sg_handle h);
  * Library service; no counterpart in the paper. */
 int sg_launch_count(sg_handle h, int64_t *count);
 
+/* Bytes the handle has copied host -> device (the instance image at attach, a loaded checkpoint)
+ * and device -> host (results, spins, checkpoints) since creation (for transfer accounting).
+ * Library service; no counterpart in the paper. */
+int sg_transfer_bytes(sg_handle h, int64_t *h2d, int64_t *d2h);
+
 /* SK local fields h[r][i] = sum_j J_ij s[r][j] computed on the tensor cores without allocating
  * any device memory.  The paper has no counterpart: this is a service for callers that cannot
  * allocate device memory where they need the fields -- a host application that fixes the

@@ -37,7 +37,7 @@ EXPORTED = [
     "sg_sweep", "sg_time", "sg_synchronize", "sg_result_shape", "sg_read_results", "sg_measure",
     "sg_get_spins", "sg_get_thresholds", "sg_state_bytes", "sg_save_state", "sg_load_state",
     "sg_destroy", "sg_launch_count", "sg_sk_fields_noalloc", "sg_set_windows", "sg_read_windows",
-    "sg_set_schedule",
+    "sg_set_schedule", "sg_transfer_bytes",
 ]
 
 
@@ -100,6 +100,7 @@ def _load():
                 "sg_set_windows": (ctypes.c_int, [H, P, i32]),
                 "sg_read_windows": (ctypes.c_int, [H, P, P, P, P]),
                 "sg_set_schedule": (ctypes.c_int, [H, P, i32, P, i32]),
+                "sg_transfer_bytes": (ctypes.c_int, [H, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -284,6 +285,13 @@ def sg_launch_count(h) -> int:
     v = ctypes.c_int64()
     _check(_load().sg_launch_count(h, ctypes.byref(v)))
     return int(v.value)
+
+
+def sg_transfer_bytes(h):
+    """(host -> device, device -> host) bytes the handle has copied so far."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(_load().sg_transfer_bytes(h, ctypes.byref(a), ctypes.byref(b)))
+    return int(a.value), int(b.value)
 
 
 def sg_sk_fields_noalloc(J_dev: int, s_dev: int, n: int, n_replicas: int, h_dev: int,

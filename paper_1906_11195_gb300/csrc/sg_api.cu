@@ -459,6 +459,7 @@ int sg_save_state(sg_handle h, void* host_dst, size_t bytes) {
         for (auto& r : regs) {
             sg::check_cuda(cudaMemcpyAsync(p, r.first, r.second, cudaMemcpyDeviceToHost, h->stream),
                            "state copy");
+            h->model->d2h_bytes += (int64_t)r.second;
             p += r.second;
         }
         sg::check_cuda(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
@@ -481,6 +482,7 @@ int sg_load_state(sg_handle h, const void* host_src, size_t bytes) {
         for (auto& r : regs) {
             sg::check_cuda(cudaMemcpyAsync(r.first, p, r.second, cudaMemcpyHostToDevice, h->stream),
                            "state copy");
+            h->model->h2d_bytes += (int64_t)r.second;
             p += r.second;
         }
         sg::check_cuda(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
@@ -495,6 +497,13 @@ int sg_destroy(sg_handle h) {
         if (!h) return;
         if (h->attached) cudaStreamSynchronize(h->stream);
         delete h;
+    });
+}
+
+int sg_transfer_bytes(sg_handle h, int64_t* h2d, int64_t* d2h) {
+    return guarded([&] {
+        if (!h || !h2d || !d2h) sg::fail(SG_EINVAL, "null argument");
+        h->model->transfer_bytes(*h2d, *d2h);
     });
 }
 

@@ -5,6 +5,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <stdlib.h>
+
+#include <new>
 #include <string>
 #include <utility>
 #include <vector>
@@ -21,6 +24,41 @@ struct Error {
 // set the message returned by sg_last_error() on this thread
 void record_error(const std::string& msg);
 void check_cuda(cudaError_t e, const char* what);
+
+// Page-locked host memory for the large host-side images that sg_attach copies to the device
+// (so the copies run at DMA speed); plain heap memory where no CUDA device is present.  A
+// 64-byte header before each block records which of the two it came from.
+template <class T>
+struct PinnedAllocator {
+    using value_type = T;
+    PinnedAllocator() = default;
+    template <class U>
+    PinnedAllocator(const PinnedAllocator<U>&) {}
+    T* allocate(size_t n) {
+        const size_t bytes = n * sizeof(T) + 64;
+        void* p = nullptr;
+        int pinned = 1;
+        if (cudaMallocHost(&p, bytes) != cudaSuccess || !p) {
+            cudaGetLastError();
+            pinned = 0;
+            p = malloc(bytes);
+            if (!p) throw std::bad_alloc();
+        }
+        *static_cast<int*>(p) = pinned;
+        return reinterpret_cast<T*>(static_cast<char*>(p) + 64);
+    }
+    void deallocate(T* q, size_t) {
+        char* p = reinterpret_cast<char*>(q) - 64;
+        if (*reinterpret_cast<int*>(p)) cudaFreeHost(p);
+        else free(p);
+    }
+    template <class U>
+    bool operator==(const PinnedAllocator<U>&) const { return true; }
+    template <class U>
+    bool operator!=(const PinnedAllocator<U>&) const { return false; }
+};
+template <class T>
+using pinned_vector = std::vector<T, PinnedAllocator<T>>;
 
 // 256-byte aligned carving of one caller-provided workspace (a null base only measures).
 struct Carver {
@@ -66,6 +104,11 @@ public:
     virtual std::vector<std::pair<void*, size_t>> state_regions() = 0;
     // device-side error word (0 = fine), read after synchronisation
     virtual int device_status(cudaStream_t st) { (void)st; return 0; }
+    // bytes copied host -> device and device -> host by the model so far
+    virtual void transfer_bytes(int64_t& h2d, int64_t& d2h) const {
+        h2d = h2d_bytes;
+        d2h = d2h_bytes;
+    }
 
     // Window-averaged measurement (set before attach): n_bins windows of sweeps; every sweep
     // inside window m adds its point values into window m's sums.
@@ -91,6 +134,7 @@ public:
     uint32_t* clock_dev = nullptr;  // device word holding the index of the next sweep
     std::vector<int64_t> tw, tm;
     int64_t launches = 0;
+    int64_t h2d_bytes = 0, d2h_bytes = 0;  // bytes copied between host and device so far
 };
 
 Model* make_vb_model(const void* graphs, int n_graphs, int n_lanes, int n_replicas, int kernel,

@@ -164,6 +164,7 @@ public:
         carve(c);
         auto up = [&](void* dst, const void* src, size_t bytes) {
             if (bytes) check_cuda(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), "H2D copy");
+            h2d_bytes += (int64_t)bytes;
         };
         up((void*)d_.JbT, h_JbT_.data(), h_JbT_.size() * 4);
         up((void*)d_.J8, h_J8_.data(), h_J8_.size());
@@ -409,7 +410,8 @@ private:
     size_t nwQ() const { return (size_t)(R / 2) * n_bins; }
     size_t nwE() const { return (size_t)R * n_bins; }
 
-    static void down(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    void down(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+        d2h_bytes += (int64_t)bytes;
         if (bytes) check_cuda(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st), "D2H copy");
     }
 
@@ -596,8 +598,9 @@ private:
     cudaEvent_t side_done_[2] = {}, inblock_done_[2] = {};
     int n_ = 0, Np_ = 0, B_ = 128, kw_ = 128, NT_ = 128;
     uint64_t seed_ = 0;
-    std::vector<uint8_t> h_J8_;
-    std::vector<uint32_t> h_JbT_, h_thr_;
+    pinned_vector<uint8_t> h_J8_;   // the large images copied at attach: page-locked
+    pinned_vector<uint32_t> h_JbT_;
+    std::vector<uint32_t> h_thr_;
     std::vector<int32_t> h_tidx_;
     std::vector<float> h_coef_;
     SkDev d_{};
@@ -799,6 +802,15 @@ private:
         for (auto& m : subs_) {
             launches += m->launches;
             m->launches = 0;
+        }
+    }
+
+    void transfer_bytes(int64_t& h2d, int64_t& d2h) const override {
+        h2d = h2d_bytes;
+        d2h = d2h_bytes;
+        for (auto& m : subs_) {
+            h2d += m->h2d_bytes;
+            d2h += m->d2h_bytes;
         }
     }
 

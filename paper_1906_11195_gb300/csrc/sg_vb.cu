@@ -207,6 +207,7 @@ public:
         carve(c);
         auto up = [&](void* dst, const void* src, size_t bytes) {
             if (bytes) check_cuda(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), "H2D copy");
+            h2d_bytes += (int64_t)bytes;
         };
         up((void*)d_thr_, thr_.data(), thr_.size() * 4);
         if (kernel_ == SG_VB_PACKED) {
@@ -552,7 +553,8 @@ private:
     size_t nmQ() const { return (size_t)n_inst * (R / 2) * Lc_; }
     size_t nmE() const { return (size_t)n_inst * R * Lc_; }
 
-    static void down(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    void down(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+        d2h_bytes += (int64_t)bytes;
         if (bytes) check_cuda(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st), "D2H copy");
     }
 
@@ -859,10 +861,12 @@ private:
     std::vector<uint8_t> h_gtab_;
     std::vector<std::vector<int64_t>> slot_of_;
     int64_t n_slots_ = 0;
-    std::vector<uint32_t> h_vinfo_, h_slice_base_, h_slice_graph_, h_col_;
-    std::vector<uint64_t> h_jb_;
-    std::vector<uint32_t> h_up_base_, h_up_col_;  // upper entries (energy measurement)
-    std::vector<uint64_t> h_up_jb_;
+    std::vector<uint32_t> h_slice_base_, h_slice_graph_;
+    pinned_vector<uint32_t> h_vinfo_, h_col_;  // the large images copied at attach: page-locked
+    pinned_vector<uint64_t> h_jb_;
+    std::vector<uint32_t> h_up_base_;               // upper entries (energy measurement)
+    pinned_vector<uint32_t> h_up_col_;
+    pinned_vector<uint64_t> h_up_jb_;
     // plain host layout
     std::vector<int32_t> colour_begin_, new_of_, h_row_ptr_, h_col_i_;
     std::vector<uint32_t> h_orig_;

@@ -869,6 +869,45 @@ __global__ void __launch_bounds__(256, EN ? (R <= 2 ? 2 : 1) : (R <= 2 ? 3 : 2))
         for (int q = threadIdx.x; q < NQ * 64; q += blockDim.x) acc[q] = 0ull;
         __syncthreads();
         unsigned long long* cta_acc = one_graph ? acc : nullptr;
+        if (cta_acc && s_lo < s_hi) {
+            // every slice of the CTA belongs to one graph: no per-slice graph test, so nothing
+            // but the loads and the counting sits in the loop and the loads of several slices
+            // (or entries) can be in flight together
+            cur_g = __ldg(d.slice_graph + s_lo);
+            if constexpr (!EN) {
+#pragma unroll 4
+                for (int64_t s = s_lo; s < s_hi; ++s) {
+                    const int64_t slot = s * 32 + lane;
+                    const SpinWords<R> si = load_words<R>(d.S + slot * R);
+                    if (kind == 0) {
+                        const SpinWords<R> sw = load_words<R>(snap + slot * R);
+#pragma unroll
+                        for (int r = 0; r < R; ++r) count_add<NQ, PW>(p, r, si.v[r] ^ sw.v[r]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < R / 2; ++q)
+                            count_add<NQ, PW>(p, q, si.v[2 * q] ^ si.v[2 * q + 1]);
+                    }
+                }
+            } else {
+                uint32_t base = __ldg(d.slice_base + s_lo);
+                for (int64_t s = s_lo; s < s_hi; ++s) {
+                    const uint32_t next = __ldg(d.slice_base + s + 1);
+                    const SpinWords<R> si = load_words<R>(d.S + (s * 32 + lane) * R);
+                    const uint32_t width = (next - base) >> 5;
+                    uint32_t idx = base + lane;
+#pragma unroll 4
+                    for (uint32_t e = 0; e < width; ++e, idx += 32) {
+                        const uint32_t j = __ldg(d.col + idx);
+                        const uint64_t J = __ldg(d.jb + idx);
+                        const SpinWords<R> sj = gather_words<R>(d.S + (int64_t)j * R);
+#pragma unroll
+                        for (int r = 0; r < R; ++r) count_add<NQ, PW>(p, r, si.v[r] ^ sj.v[r] ^ J);
+                    }
+                    base = next;
+                }
+            }
+        } else
         // padding slots hold zero words and zero couplings, so they add nothing: no vinfo test,
         // and the loads of several slices can be in flight together
 #pragma unroll 4

@@ -230,3 +230,10 @@ def test_noalloc_rejects_host_pointers_before_launching(lib):
         rc = L.sg_sk_fields_noalloc(J.ctypes.data, s.ctypes.data, n, R, h.ctypes.data, None)
         assert rc == sg.SG_EINVAL, (n, R)
         assert sg.sg_last_error()
+
+
+def test_transfer_bytes_start_at_zero(lib):
+    g = _graph()
+    h = sg.sg_create_vb([g], 64, 2, sg.SG_VB_PACKED, [0], [0, 1])
+    assert sg.sg_transfer_bytes(h) == (0, 0)
+    sg.sg_destroy(h)

@@ -242,6 +242,8 @@ def test_sweep_chunking_and_measure_now():
     for x, y in zip(a[:4], b[:4]):
         assert np.array_equal(np.asarray(x), np.asarray(y))
     run = sg.VBRun([g], n_lanes=64, n_replicas=2, kernel=sg.SG_VB_PACKED, tw=tw, tm=tm)
+    h2d, d2h = sg.sg_transfer_bytes(run.h)
+    assert h2d >= g["col"].nbytes + g["jbits"].nbytes  # at least the graph's image went up
     run.sweep(10)
     assert sg.sg_workspace_bytes(run.h) == run.workspace.numel()  # querying must not disturb it
     run.sweep(11)
