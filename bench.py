@@ -144,13 +144,79 @@ def recorded_traffic():
     return float(d["dram_bytes_per_sweep"])
 
 
+class _Nvml:
+    """The few NVML queries the clock record needs (SM clock, its maximum, the active clock
+    event reasons), called through ctypes on the driver's libnvidia-ml.  Reads only."""
+    REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
+               0x4: "sw_power_cap", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, index):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        found = False
+        try:  # the CUDA device by its PCI address (NVML numbers every GPU of the host)
+            import torch
+            p = torch.cuda.get_device_properties(index)
+            bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0".encode()
+            found = self.lib.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(self.h)) == 0
+        except Exception:
+            found = False
+        if not found and self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("no NVML handle")
+        try:
+            self.reasons_fn = self.lib.nvmlDeviceGetCurrentClocksEventReasons
+        except AttributeError:
+            self.reasons_fn = self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        v = ctypes.c_uint()
+        if self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(v)) != 0:
+            raise RuntimeError("no max clock")
+        self.max_mhz = float(v.value)
+
+    def sample(self):
+        ct = self.ct
+        v, r = ct.c_uint(), ct.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(v)) != 0:
+            return None
+        if self.reasons_fn(self.h, ct.byref(r)) != 0:
+            return None
+        return float(v.value), int(r.value)
+
+
 class ClockSampler:
+    """SM clock and throttle reasons sampled every millisecond from a thread between start()
+    and stop(), so that even a timed region of a few milliseconds holds several samples (NVML
+    through ctypes; nvidia-smi at 200 ms where NVML cannot be loaded)."""
+
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.thread = None
         self.path = None
 
     def start(self):
+        import threading
+        try:
+            self.nvml = _Nvml(self.index)
+        except Exception:
+            self.nvml = None
+        if self.nvml is not None:
+            self.samples = []
+            self.stop_ev = threading.Event()
+
+            def loop():
+                while not self.stop_ev.is_set():
+                    s = self.nvml.sample()
+                    if s is not None:
+                        self.samples.append(s)
+                    time.sleep(0.001)
+
+            self.thread = threading.Thread(target=loop, daemon=True)
+            self.thread.start()
+            return
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
@@ -166,6 +232,20 @@ class ClockSampler:
             self.proc = None
 
     def stop(self):
+        if self.thread is not None:
+            self.stop_ev.set()
+            self.thread.join(timeout=5)
+            self.thread = None
+            if not self.samples:
+                return None
+            reasons = set()
+            for _, r in self.samples:
+                for bit, nm in _Nvml.REASONS.items():
+                    if r & bit:
+                        reasons.add(nm)
+            return {"sm_mhz": statistics.median(m for m, _ in self.samples),
+                    "sm_max_mhz": self.nvml.max_mhz, "reasons": sorted(reasons),
+                    "samples": len(self.samples), "source": "nvml, 1 ms"}
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -193,7 +273,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, 200 ms"}
 
 
 def cpu_baseline_sample(rp, col, jb, budget_lanes=16):

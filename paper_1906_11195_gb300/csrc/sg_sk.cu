@@ -420,8 +420,8 @@ private:
     // Persistent sweep (B = 128): field CTAs with TPC row tiles each in tensor memory, chain CTAs
     // of W replica warps; the smallest TPC and then W for which every CTA is resident.
     // SG_SK_PERSISTENT=0 keeps the launch-per-block sequence (results are the same);
-    // SG_SK_LOOKAHEAD=<L> (2, 4, 6 or 8; default 4, lowered below the number of blocks) sets the
-    // blocks of flips a chain warp folds in itself.
+    // SG_SK_LOOKAHEAD=<L> (4, 6 or 8; default 6, lowered below the number of blocks) sets the
+    // blocks of flips folded on chip (L - 1 of them by the fold warps).
     bool plan_persist() {
         const char* e = getenv("SG_SK_PERSISTENT");
         if (e && e[0] == '0' && !e[1]) return false;
@@ -429,14 +429,14 @@ private:
         int dev = 0, sms = 0;
         check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
         check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
-        int L = 4;
+        int L = 6;
         if (const char* l = getenv("SG_SK_LOOKAHEAD")) L = atoi(l);
         if (!sk_persist_lookahead_supported(L)) return false;
         SkPersistArgs a = pa_;
         a.nb = Np_ / 128;
         // a fold window never holds a block twice: the largest compiled L below nb
         while (L >= a.nb && L > 0) L -= 2;
-        if (L < 2) return false;
+        if (L < 4) return false;  // the smallest compiled window (the staging needs L >= 2)
         a.L = L;
         a.n_sweeps = 1;
         a.Q = kPersistSlots;

@@ -47,7 +47,7 @@ namespace {
 
 constexpr uint64_t kPersistWaitNs = 2000000000ull;  // 2 s: only a broken launch waits that long
 constexpr uint32_t kTileBytes = 128 * 128;          // one e4m3 128 x 128 coupling tile
-constexpr int kChainStages = 2;  // a power of two
+constexpr int kChainStages = 3;  // staged blocks ahead of the chain
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
     uint32_t v;
@@ -62,6 +62,7 @@ __device__ __forceinline__ void red_release_add(uint32_t* p, uint32_t v) {
 __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
+
 
 __device__ __forceinline__ int err_raised(const int* err) {
     return *reinterpret_cast<const volatile int*>(err);
@@ -133,9 +134,10 @@ __host__ __device__ __forceinline__ size_t field_stage_bytes(int TPC, int R) {
     return (size_t)TPC * kTileBytes + (size_t)R * 128;
 }
 
-// shared memory of a chain CTA: spin and flip words of its replicas, then the staged ring
+// shared memory of a chain CTA: spin and flip words of its replicas, the fold warps' fields
+// for two blocks, then the staged ring
 __host__ __device__ __forceinline__ size_t chain_words_bytes(int W, int Np) {
-    return (size_t)2 * W * (Np / 32) * 4;
+    return (size_t)2 * W * (Np / 32) * 4 + (size_t)2 * W * 128 * 4;
 }
 __host__ __device__ __forceinline__ size_t chain_stage_bytes(int W, int L) {
     return (size_t)(L + 1) * 4 * 128 * 4 + (size_t)W * 128 * (2 + 4);  // coupling words, K*, fields
@@ -149,10 +151,26 @@ __host__ __device__ __forceinline__ size_t chain_stage_bytes(int W, int L) {
 // ------------------------------------------------------------------------------------------
 __device__ __forceinline__ void bar_epilogue() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
+// barrier of the 128 epilogue threads that also returns whether all of them passed v: every
+// decision that leads into or around a barrier is taken uniformly
+__device__ __forceinline__ bool epilogue_all(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0u;
+}
+
 template <int W>
-__device__ void persist_field_cta(const CUtensorMap* mapJ, const CUtensorMap* mapD, const SkDev& d,
-                                  const SkPersistArgs& a, uint8_t* smem, uint64_t* bars,
-                                  uint32_t* tslot, volatile int* abort_flag) {
+__device__ void persist_field_cta(const CUtensorMap* mapJ, const CUtensorMap* mapD,
+                                  const SkPersistMaps& m, const SkDev& d, const SkPersistArgs& a,
+                                  uint8_t* smem, uint64_t* bars, uint32_t* tslot,
+                                  volatile int* abort_flag) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int j = blockIdx.x;
     const int R = d.R, Np = d.Np, nb = a.nb, nst = a.nst, L = a.L;
@@ -296,32 +314,31 @@ __device__ void persist_field_cta(const CUtensorMap* mapJ, const CUtensorMap* ma
                 for (int u = 0; u < ntl; ++u)
                     if (j + u * a.nG == kc % nb) pub_u = u;
             if (pub_u >= 0) {
-                bar_epilogue();
-                if (!*abort_flag) {
-                    if (mbar_wait_or_abort(&mdone[s], ph, d.err, nowait, abort_flag)) {
-                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        // Hpub is [replica][row]: a warp's 32 rows of one replica are 128
-                        // contiguous bytes
-                        const int row = (kc % nb) * 128 + 32 * warp + lane;
-                        for (int c = 0; c < R / 32; ++c) {
-                            uint32_t v[32];
-                            tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(pub_u * R + 32 * c), v);
+                bool ok = epilogue_all(!*abort_flag);
+                if (ok) ok = mbar_wait_or_abort(&mdone[s], ph, d.err, nowait, abort_flag);
+                ok = epilogue_all(ok);
+                if (ok) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    // Hpub is [replica][row]: a warp's 32 rows of one replica are 128 contiguous
+                    // bytes
+                    const int row = (kc % nb) * 128 + 32 * warp + lane;
+                    for (int c = 0; c < R / 32; ++c) {
+                        uint32_t v[32];
+                        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(pub_u * R + 32 * c), v);
 #pragma unroll
-                            for (int q = 0; q < 32; ++q)
-                                __stcg(a.Hpub + (int64_t)(32 * c + q) * Np + row,
-                                       __float2int_rn(__uint_as_float(v[q])));
-                        }
-                        fence_proxy_async_global();  // read by the chains' TMA copies
-                    } else {
-                        atomicOr(d.err, 128);
-                        *abort_flag = 1;
+                        for (int q = 0; q < 32; ++q)
+                            __stcg(a.Hpub + (int64_t)(32 * c + q) * Np + row, __float2int_rn(__uint_as_float(v[q])));
                     }
+                    fence_proxy_async_global();  // read by the chains' TMA copies
+                } else if (tid == 0) {
+                    atomicOr(d.err, 128);
+                    *abort_flag = 1;
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 bar_epilogue();
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 // H_ready[tile] = kc + 1: the tile holds every block before kc - L
-                if (tid == 0 && !*abort_flag)
+                if (tid == 0 && ok)
                     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&H_ready[kc % nb]),
                                  "r"((uint32_t)(kc + 1))
                                  : "memory");
@@ -360,8 +377,30 @@ __device__ void persist_field_cta(const CUtensorMap* mapJ, const CUtensorMap* ma
 }
 
 // ------------------------------------------------------------------------------------------
-// chain CTA: warp W (lane 0) stages the blocks, warps 0..W-1 are the replicas' chains
+// chain CTA: warps 0..W-1 are the replicas' chains, warps W..2W-1 their fold warps, warp 2W
+// (lane 0) stages the blocks.  For block k the fold warp of replica w adds to the staged fields
+// the flips of blocks k - L .. k - 2 (complete while the chain runs block k - 1) and hands the
+// result over in shared memory; the chain warp adds block k - 1's flips itself (16 popcounts
+// per lane) and takes the decisions.  So only one block's fold sits on the chain.
 // ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void fold_block(int (&h)[4], const uint32_t* Jp, const uint32_t* Fw,
+                                           const uint32_t* Sw, int bp, bool live, uint32_t lane) {
+    uint32_t Fv[4], sv[4], jv[4][4];
+#pragma unroll
+    for (int cp = 0; cp < 4; ++cp) {
+        Fv[cp] = live ? Fw[bp * 4 + cp] : 0u;
+        sv[cp] = Sw[bp * 4 + cp];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) jv[cp][q] = Jp[cp * 128 + 32 * q + lane];
+    }
+#pragma unroll
+    for (int cp = 0; cp < 4; ++cp) {
+        const int pf = __popc(Fv[cp]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) h[q] += 2 * (pf - 2 * __popc(Fv[cp] & (jv[cp][q] ^ sv[cp])));
+    }
+}
+
 template <int W, int L>
 __device__ void persist_chain_cta(const SkDev& d, const SkPersistArgs& a, const SkPersistMaps& m,
                                   uint8_t* smem, uint64_t* bars, volatile int* abort_flag) {
@@ -375,10 +414,13 @@ __device__ void persist_chain_cta(const SkDev& d, const SkPersistArgs& a, const 
     const bool nowait = d.test_nowait != 0;
     uint32_t* Ssm = reinterpret_cast<uint32_t*>(smem);          // [W][words] spin words
     uint32_t* Fsm = Ssm + (size_t)W * words;                     // [W][words] latest flips
+    int32_t* hb = reinterpret_cast<int32_t*>(Fsm + (size_t)W * words);  // [2][W][128] folded fields
     uint8_t* ring = smem + chain_words_bytes(W, Np);
     const size_t stb = chain_stage_bytes(W, L);
     uint64_t* fullc = bars;                   // [kChainStages]: the stage's copies landed
-    uint64_t* emptyc = bars + kChainStages;   // [kChainStages]: W replica warps done
+    uint64_t* emptyc = bars + kChainStages;   // [kChainStages]: chain and fold warps done
+    uint64_t* cdone = bars + 2 * kChainStages;    // [W][2]: the chain finished block k (k & 1)
+    uint64_t* hrdy = cdone + 2 * W;               // [W][2]: folded fields of block k (k & 1)
     uint32_t* D_count = a.sync;
     uint32_t* D_free = a.sync + Q;
     uint32_t* H_ready = a.sync + 2 * Q;
@@ -386,8 +428,9 @@ __device__ void persist_chain_cta(const SkDev& d, const SkPersistArgs& a, const 
     if (tid == 0) {
         for (int s = 0; s < kChainStages; ++s) {
             mbar_init(&fullc[s], 1);
-            mbar_init(&emptyc[s], W);
+            mbar_init(&emptyc[s], 2 * W);
         }
+        for (int i = 0; i < 4 * W; ++i) mbar_init(&cdone[i], 1);  // cdone and hrdy
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp < W) {
@@ -399,14 +442,15 @@ __device__ void persist_chain_cta(const SkDev& d, const SkPersistArgs& a, const 
     }
     __syncthreads();
 
-    if (warp == W) {
+    if (warp == 2 * W) {
         // ---------------- staging warp: block k (couplings, K*, fields) ----------------
         if (lane == 0) {
             const uint32_t stage_tx = (uint32_t)chain_stage_bytes(W, L);
             const uint64_t pol = l2_evict_last();
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&m.jb)) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&m.hpub)) : "memory");
-            int last_fill[kChainStages] = {-1, -1};
+            int last_fill[kChainStages];
+            for (int s = 0; s < kChainStages; ++s) last_fill[s] = -1;
             auto prefetch = [&](int k) -> bool {
                 const int s = k % kChainStages;
                 const int b = k % nb, sw = k / nb;
@@ -459,31 +503,73 @@ __device__ void persist_chain_cta(const SkDev& d, const SkPersistArgs& a, const 
                         mbar_wait_timed(&fullc[s], (uint32_t)(last_fill[s] / kChainStages) & 1u, kPersistWaitNs);
             }
         }
-    } else if (warp < W) {
+    } else if (warp >= W) {
+        // ---------------- fold warp of replica w ----------------
+        const int w = warp - W;
+        const uint32_t* Sw = Ssm + w * words;
+        const uint32_t* Fw = Fsm + w * words;
+        for (int k = 0, b = 0; k < nk; ++k, b = (b + 1 == nb) ? 0 : b + 1) {
+            const int s = k % kChainStages;
+            bool ok = mbar_wait_or_abort(&fullc[s], (uint32_t)(k / kChainStages) & 1u, d.err, nowait,
+                                         abort_flag);
+            // the chain has finished block k - 2 (its flips and spins are in shared memory)
+            if (ok && k >= 2)
+                ok = mbar_wait_or_abort(&cdone[w * 2 + (k & 1)], (uint32_t)((k - 2) >> 1) & 1u, d.err,
+                                        nowait, abort_flag);
+            if (!ok) {
+                if (lane == 0) atomicOr(d.err, 32768);
+                *abort_flag = 1;
+                break;
+            }
+            const uint32_t* Jw = reinterpret_cast<const uint32_t*>(ring + (size_t)s * stb);
+            const int16_t* ks16 = reinterpret_cast<const int16_t*>(Jw + (L + 1) * 4 * 128);
+            const int32_t* hs = reinterpret_cast<const int32_t*>(ks16 + W * 128) + w * 128;
+            int h[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) h[q] = hs[32 * q + lane];
+#pragma unroll
+            for (int i = 0; i < L - 1; ++i) {
+                int bp = b - L + i;
+                if (bp < 0) bp += nb;  // L < nb
+                fold_block(h, Jw + i * 4 * 128, Fw, Sw, bp, k - L + i >= 0, lane);
+            }
+            int32_t* hd = hb + ((k & 1) * W + w) * 128;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) hd[32 * q + lane] = h[q];
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&hrdy[w * 2 + (k & 1)]);
+                mbar_arrive(&emptyc[s]);
+            }
+        }
+    } else {
         // ---------------- replica warp ----------------
         const int r = r0 + warp;
         uint32_t* Sw = Ssm + warp * words;
         uint32_t* Fw = Fsm + warp * words;
         const uint32_t lane_bit = 1u << lane;
         for (int k = 0, b = 0; k < nk; ++k, b = (b + 1 == nb) ? 0 : b + 1) {
-            const int s = k & (kChainStages - 1);
-            if (!mbar_wait_or_abort(&fullc[s], (uint32_t)(k / kChainStages) & 1u, d.err, nowait,
-                                    abort_flag)) {
+            const int s = k % kChainStages;
+            bool ok = mbar_wait_or_abort(&fullc[s], (uint32_t)(k / kChainStages) & 1u, d.err, nowait,
+                                         abort_flag);
+            if (ok)
+                ok = mbar_wait_or_abort(&hrdy[warp * 2 + (k & 1)], (uint32_t)(k >> 1) & 1u, d.err,
+                                        nowait, abort_flag);
+            if (!ok) {
                 if (lane == 0) atomicOr(d.err, 4096);
                 *abort_flag = 1;
                 break;
             }
             const uint8_t* st = ring + (size_t)s * stb;
             const uint32_t* Jw = reinterpret_cast<const uint32_t*>(st);
-            const int16_t* ks16 = reinterpret_cast<const int16_t*>(Jw + (L + 1) * 4 * 128);
-            const int16_t* ks = ks16 + warp * 128;
-            const int32_t* hs = reinterpret_cast<const int32_t*>(ks16 + W * 128) + warp * 128;
+            const int16_t* ks = reinterpret_cast<const int16_t*>(Jw + (L + 1) * 4 * 128) + warp * 128;
             const uint32_t* Jown = Jw + L * 4 * 128;  // [4 column words][128 rows] of block b
+            const int32_t* hd = hb + ((k & 1) * W + warp) * 128;
             int h[4], kst[4];
             uint32_t sw[4], jd[4], jl[6];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                h[q] = hs[32 * q + lane];
+                h[q] = hd[32 * q + lane];
                 kst[q] = ks[32 * q + lane];
                 sw[q] = Sw[b * 4 + q];
                 jd[q] = Jown[q * 128 + 32 * q + lane];  // couplings inside chunk q
@@ -495,29 +581,11 @@ __device__ void persist_chain_cta(const SkDev& d, const SkPersistArgs& a, const 
             jl[3] = Jown[1 * 128 + 32 * 2 + lane];
             jl[4] = Jown[1 * 128 + 32 * 3 + lane];
             jl[5] = Jown[2 * 128 + 32 * 3 + lane];
-            // flips of blocks k - L .. k - 1 of this launch, which the staged fields do not
-            // hold yet (each block's latest flips: L < nb); all loads first, then the popcounts
-#pragma unroll
-            for (int i = 0; i < L; ++i) {
-                const int kp = k - L + i;
-                int bp = b - L + i;
-                if (bp < 0) bp += nb;  // L < nb
-                const uint32_t* Jp = Jw + i * 4 * 128;
-                uint32_t Fv[4], sv[4], jv[4][4];
-#pragma unroll
-                for (int cp = 0; cp < 4; ++cp) {
-                    Fv[cp] = kp >= 0 ? Fw[bp * 4 + cp] : 0u;
-                    sv[cp] = Sw[bp * 4 + cp];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) jv[cp][q] = Jp[cp * 128 + 32 * q + lane];
-                }
-#pragma unroll
-                for (int cp = 0; cp < 4; ++cp) {
-                    const int pf = __popc(Fv[cp]);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        h[q] += 2 * (pf - 2 * __popc(Fv[cp] & (jv[cp][q] ^ sv[cp])));
-                }
+            // the flips of block k - 1, just taken: the one fold left on the chain
+            {
+                int bp = b - 1;
+                if (bp < 0) bp += nb;
+                fold_block(h, Jw + (L - 1) * 4 * 128, Fw, Sw, bp, k >= 1, lane);
             }
             uint8_t* Dslot = a.Dring + ((int64_t)(k % Q) * R + r) * 128;
 #pragma unroll
@@ -552,11 +620,15 @@ __device__ void persist_chain_cta(const SkDev& d, const SkPersistArgs& a, const 
                 }
                 sw[q] = nsw;
             }
-            // D_k of this replica is written: order it for the tensor-core readers, then
-            // release the stage (the staging warp publishes the block once every warp is done)
+            // D_k of this replica is written: order it for the tensor-core readers; tell the
+            // fold warp that block k is done; release the stage (the staging warp publishes
+            // the block once every warp is done)
             fence_proxy_async_global();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&emptyc[s]);
+            if (lane == 0) {
+                mbar_arrive(&cdone[warp * 2 + (k & 1)]);
+                mbar_arrive(&emptyc[s]);
+            }
         }
     }
     __syncthreads();
@@ -567,18 +639,18 @@ __device__ void persist_chain_cta(const SkDev& d, const SkPersistArgs& a, const 
 }
 
 template <int W, int L>
-__global__ void __launch_bounds__(32 * (W + 1), 1)
+__global__ void __launch_bounds__(32 * (2 * W + 1), 1)
     k_sk_persist(const __grid_constant__ CUtensorMap mapJ, const __grid_constant__ CUtensorMap mapD,
                  const __grid_constant__ SkPersistMaps maps, SkDev d, SkPersistArgs a) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t bars[16];
+    __shared__ __align__(8) uint64_t bars[2 * kChainStages + 4 * 8];  // chain CTA: W <= 8
     __shared__ uint32_t tslot;
     __shared__ int abort_flag;
     if (threadIdx.x == 0) abort_flag = 0;
     __syncthreads();
     if ((int)blockIdx.x < a.nG)
-        persist_field_cta<W>(&mapJ, &mapD, d, a, smem, bars, &tslot, &abort_flag);
+        persist_field_cta<W>(&mapJ, &mapD, maps, d, a, smem, bars, &tslot, &abort_flag);
     else
         persist_chain_cta<W, L>(d, a, maps, smem, bars, &abort_flag);
 }
@@ -592,7 +664,7 @@ size_t sk_persist_smem_bytes(const SkDev& d, const SkPersistArgs& a) {
 }
 
 // lookaheads compiled in (the fold of L blocks is unrolled)
-#define SG_PERSIST_KERNELS(X) X(4, 2) X(4, 4) X(4, 6) X(4, 8) X(8, 2) X(8, 4) X(8, 6) X(8, 8)
+#define SG_PERSIST_KERNELS(X) X(4, 4) X(4, 6) X(4, 8) X(8, 4) X(8, 6) X(8, 8)
 
 static void* persist_kernel(int W, int L) {
 #define SG_PERSIST_PICK(w, l) if (W == w && L == l) return (void*)k_sk_persist<w, l>;
@@ -601,14 +673,16 @@ static void* persist_kernel(int W, int L) {
     return nullptr;
 }
 
-int sk_persist_lookahead_supported(int L) { return L == 2 || L == 4 || L == 6 || L == 8; }
+int sk_persist_lookahead_supported(int L) { return L == 4 || L == 6 || L == 8; }
 
 int sk_persist_fits(const SkDev& d, const SkPersistArgs& a, int num_sms) {
     void* kern = persist_kernel(a.W, a.L);
-    // R: whole 32-column chunks of tensor memory, at most one TMA box of spin changes; L >= 1
-    // whenever a tile is published (the helper stages two blocks ahead of the chain)
+    // R: whole 32-column chunks of tensor memory, at most one TMA box of spin changes; the
+    // staging warp, kChainStages blocks ahead, needs L >= kChainStages - 1 (fields published in
+    // time) and a ring of at least kChainStages slots (slots freed in time)
     if (!kern || d.R < 32 || d.R > 256 || d.R % 32 || a.nst < 2 || a.nst > 4 || a.Q != kSkPersistSlots ||
-        a.L < 1 || a.L >= a.nb || a.TPC * d.R > 512 || a.nC * a.W != d.R || a.n_sweeps < 1 ||
+        a.L < kChainStages - 1 || a.L >= a.nb || a.TPC * d.R > 512 || a.nC * a.W != d.R ||
+        a.n_sweeps < 1 || kSkPersistSlots < kChainStages ||
         a.n_sweeps > kSkPersistMaxSweeps)
         return 0;
     const size_t smem = sk_persist_smem_bytes(d, a);
@@ -619,7 +693,7 @@ int sk_persist_fits(const SkDev& d, const SkPersistArgs& a, int num_sms) {
         return 0;
     }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * (a.W + 1), smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * (2 * a.W + 1), smem) !=
         cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -636,7 +710,7 @@ int sk_persist_sweeps(const SkDev& d, const SkPersistArgs& a, const CUtensorMap&
         return -1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(a.nG + a.nC));
-    cfg.blockDim = dim3((unsigned)(32 * (a.W + 1)));
+    cfg.blockDim = dim3((unsigned)(32 * (2 * a.W + 1)));
     cfg.dynamicSmemBytes = sk_persist_smem_bytes(d, a);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];

@@ -122,21 +122,21 @@ def run_protocol(nb, nC, nG, TPC, L, Q, S_C=2, n_sweeps=1, seed=0, fold_short=Fa
 
 
 CONFIGS = [
-    # nb, nC, nG, TPC, L, Q, sweeps
-    (64, 64, 64, 1, 6, 8, 1),    # N = 8192, R = 256, one sweep
-    (64, 64, 64, 1, 6, 8, 3),    # the same, three sweeps in one launch
-    (128, 32, 64, 2, 6, 8, 2),   # N = 16384, R = 128
-    (7, 8, 3, 3, 6, 8, 4),       # L = nb - 1: the largest window
-    (5, 8, 3, 2, 2, 2, 3),       # smallest lookahead and ring
-    (17, 3, 9, 2, 4, 3, 2),      # ragged tile ownership
+    # nb, nC, nG, TPC, L, Q, sweeps, staged blocks
+    (64, 64, 64, 1, 4, 8, 1, 3),    # N = 8192, R = 256, one sweep (the kernel's ring: 3)
+    (64, 64, 64, 1, 6, 8, 3, 3),    # the same, three sweeps in one launch
+    (128, 32, 64, 2, 4, 8, 2, 3),   # N = 16384, R = 128
+    (7, 8, 3, 3, 6, 8, 4, 3),       # L = nb - 1: the largest window
+    (5, 8, 3, 2, 2, 3, 3, 3),       # smallest lookahead and ring (Q >= staged blocks)
+    (17, 3, 9, 2, 4, 3, 2, 2),      # ragged tile ownership, two staged blocks
 ]
 
 
 @pytest.mark.parametrize("cfg", CONFIGS)
 def test_protocol_finishes_and_keeps_the_sequential_order(cfg):
-    nb, nC, nG, TPC, L, Q, S = cfg
+    nb, nC, nG, TPC, L, Q, S, S_C = cfg
     for seed in range(8):
-        finished, errors = run_protocol(nb, nC, nG, TPC, L, Q, n_sweeps=S, seed=seed)
+        finished, errors = run_protocol(nb, nC, nG, TPC, L, Q, S_C=S_C, n_sweeps=S, seed=seed)
         assert not errors, errors[:3]
         assert finished, f"deadlock with seed {seed}"
 
@@ -157,3 +157,12 @@ def test_missing_ring_release_wait_is_caught():
         _, errors = run_protocol(24, 4, 8, 3, 6, 2, seed=seed, skip_free=True)
         caught |= any("holds" in e or "out of order" in e for e in errors)
     assert caught
+
+
+def test_ring_smaller_than_the_staging_depth_deadlocks():
+    """Staging block k + S_C waits for ring slot k + S_C - Q to be read, but that block's spin
+    changes are published only after the staging: Q >= S_C is required (the kernel has Q = 8,
+    three staged blocks)."""
+    finished, _ = run_protocol(5, 8, 3, 2, 2, 2, S_C=3, n_sweeps=3, seed=0)
+    assert not finished
+
