@@ -187,15 +187,21 @@ class _Nvml:
 
 
 class ClockSampler:
-    """SM clock and throttle reasons sampled every millisecond from a thread between start()
-    and stop(), so that even a timed region of a few milliseconds holds several samples (NVML
-    through ctypes; nvidia-smi at 200 ms where NVML cannot be loaded)."""
+    """SM clock and throttle reasons sampled every millisecond from a thread, from enqueued()
+    (the timed work is queued and the GPU runs it) to stop(), so that even a timed region of a
+    few milliseconds holds several samples while the queries cannot delay the launches (NVML
+    through ctypes; nvidia-smi at 200 ms from start() where NVML cannot be loaded)."""
 
     def __init__(self, index):
         self.index = index
         self.proc = None
         self.thread = None
         self.path = None
+        self.go = None
+
+    def enqueued(self):
+        if self.go is not None:
+            self.go.set()
 
     def start(self):
         import threading
@@ -206,12 +212,18 @@ class ClockSampler:
         if self.nvml is not None:
             self.samples = []
             self.stop_ev = threading.Event()
+            self.go = threading.Event()
 
             def loop():
-                while not self.stop_ev.is_set():
+                while not self.go.wait(0.001):
+                    if self.stop_ev.is_set():
+                        return
+                while True:
                     s = self.nvml.sample()
                     if s is not None:
                         self.samples.append(s)
+                    if self.stop_ev.is_set():
+                        return
                     time.sleep(0.001)
 
             self.thread = threading.Thread(target=loop, daemon=True)
@@ -233,6 +245,7 @@ class ClockSampler:
 
     def stop(self):
         if self.thread is not None:
+            self.go.set()
             self.stop_ev.set()
             self.thread.join(timeout=5)
             self.thread = None
@@ -436,7 +449,7 @@ def e4m3_peak():
 SK_TIMED_CHUNK = 8  # sweeps per timed iteration of a workload whose inputs fit in L2
 
 
-def _timed_region(run, steps, stream, flush=None):
+def _timed_region(run, steps, stream, flush=None, sampler=None):
     """CUDA-event time (ms) of `steps` sweeps of `run` on `stream`.  With a flush buffer, the
     sweeps are timed in iterations of SK_TIMED_CHUNK consecutive sweeps (one replayed graph, one
     persistent launch for SK) and the buffer (larger than L2) is rewritten between iterations,
@@ -449,6 +462,8 @@ def _timed_region(run, steps, stream, flush=None):
         run.sweep(steps)
         e1.record(stream)
         nvtx_pop()
+        if sampler is not None:
+            sampler.enqueued()
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
     chunks = [min(SK_TIMED_CHUNK, steps - c) for c in range(0, steps, SK_TIMED_CHUNK)]
@@ -462,6 +477,8 @@ def _timed_region(run, steps, stream, flush=None):
         with torch.cuda.stream(stream):
             flush.fill_(k & 0x7F)
     nvtx_pop()
+    if sampler is not None:
+        sampler.enqueued()
     torch.cuda.synchronize()
     return sum(a.elapsed_time(b) for a, b in evs)
 
@@ -510,7 +527,7 @@ def measure_sk(args, dev, stream, steps, warmup, cpu=True):
         l0 = run.launches
         sampler = ClockSampler(torch.cuda.current_device())
         sampler.start()
-        ms = _timed_region(run, steps, stream, flush)
+        ms = _timed_region(run, steps, stream, flush, sampler)
         clocks = sampler.stop()
         run.synchronize()
         launches = run.launches - l0
@@ -594,7 +611,7 @@ def measure_vb_batch(args, dev, stream, steps, warmup, cpu=True, count=512):
     l0 = run.launches
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
-    ms = _timed_region(run, steps, stream) / steps
+    ms = _timed_region(run, steps, stream, sampler=sampler) / steps
     clocks = sampler.stop()
     run.synchronize()
     launches = run.launches - l0
@@ -664,7 +681,7 @@ def measure_sk_batch(args, dev, stream, steps, warmup, cpu=True):
     l0 = run.launches
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
-    ms = _timed_region(run, steps, stream) / steps
+    ms = _timed_region(run, steps, stream, sampler=sampler) / steps
     clocks = sampler.stop()
     run.synchronize()
     launches = run.launches - l0
@@ -1039,6 +1056,7 @@ def run_gpu(args):
         r.sweep(args.steps)
     ev1.record(stream)
     nvtx_pop()
+    sampler.enqueued()
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()

@@ -33,8 +33,9 @@ __global__ void k_clock_add(uint32_t* c, uint32_t v) { *c += v; }
 
 }  // namespace sg
 
-// Sweeps are replayed from CUDA graphs of 2^k sweeps (k <= kMaxGraphLog), captured lazily on a
-// private stream and launched on the caller's stream; the graph size is also capped in nodes.
+// Sweeps are replayed from CUDA graphs of 2^k sweeps (k <= kMaxGraphLog), all captured on a
+// private stream the first time sweeps run and launched on the caller's stream; the graph size
+// is also capped in nodes.
 static const int kMaxGraphLog = 6;
 static const int64_t kMaxGraphNodes = 4096;
 
@@ -130,14 +131,26 @@ static cudaGraphExec_t sweep_graph(sg_handle h, int k) {
 static void run_sweeps(sg_handle h, int64_t t0, int64_t len) {
     if (len <= 0) return;
     sg::Model& m = *h->model;
-    sg::k_clock_set<<<1, 1, 0, h->stream>>>(m.clock_dev, (uint32_t)t0);
-    m.launches += 1;
+    if (m.has_pending()) {
+        // the first sweep takes the deferred measurement of the state it starts from: the clock
+        // is set past it and the sweep runs at offset -1 (index t0)
+        sg::k_clock_set<<<1, 1, 0, h->stream>>>(m.clock_dev, (uint32_t)(t0 + 1));
+        m.launches += 1;
+        m.sweep_pending(0xFFFFFFFFu, h->stream);
+        ++t0;
+        if (--len == 0) return;
+    } else {
+        sg::k_clock_set<<<1, 1, 0, h->stream>>>(m.clock_dev, (uint32_t)t0);
+        m.launches += 1;
+    }
     if (h->max_graph_log < 0) {
         sweep_graph(h, 0);
         const int64_t per_sweep = std::max<int64_t>(1, h->graph_kernels[0] - 1);
         int k = 0;
         while (k < kMaxGraphLog && ((int64_t)2 << k) * per_sweep <= kMaxGraphNodes) ++k;
         h->max_graph_log = k;
+        // every size now, so that a later call (a timed one) only replays
+        for (int j = 1; j <= k; ++j) sweep_graph(h, j);
     }
     int64_t done = 0;
     for (int k = h->max_graph_log; k >= 0; --k) {
@@ -153,6 +166,13 @@ static void run_sweeps(sg_handle h, int64_t t0, int64_t len) {
 static void require_attached(sg_handle h) {
     if (!h) sg::fail(SG_EINVAL, "null handle");
     if (!h->attached) sg::fail(SG_ESTATE, "handle has no workspace (call sg_attach first)");
+}
+
+// take a measurement the model deferred into its next sweep now (the counts are about to be
+// read, or the state replaced)
+static void settle(sg_handle h) {
+    h->model->flush_pending(h->stream);
+    sg::check_cuda(cudaGetLastError(), "measure launch");
 }
 
 // snapshot/measure at the current tau if the schedule says so
@@ -321,6 +341,7 @@ int sg_read_windows(sg_handle h, int64_t* C, int64_t* q, int64_t* E, int64_t* n_
         require_attached(h);
         if (h->wb.empty()) sg::fail(SG_ESTATE, "no measurement windows were set");
         if (!C || !q || !E || !n_meas) sg::fail(SG_EINVAL, "null output array");
+        settle(h);
         sg::Model& m = *h->model;
         const int64_t nb = (int64_t)h->wb.size() - 1, ntw = (int64_t)h->tw.size();
         // sweeps measured so far in each window: tau' in [wb[m], wb[m+1]) with tau' <= tau
@@ -374,6 +395,7 @@ int sg_read_results(sg_handle h, int64_t* C, size_t C_len, int64_t* q, size_t q_
                     size_t E_len) {
     return guarded([&] {
         require_attached(h);
+        settle(h);
         const sg::Model& m = *h->model;
         const size_t ntw = h->tw.size(), ntm = h->tm.size();
         const size_t nC = (size_t)m.n_inst * m.R * m.L * ntw * ntm;
@@ -447,6 +469,7 @@ int sg_save_state(sg_handle h, void* host_dst, size_t bytes) {
         size_t total = 8 * 5 + 8 * regs.size();
         for (auto& r : regs) total += r.second;
         if (!host_dst || bytes != total) sg::fail(SG_EINVAL, "state buffer has the wrong size");
+        settle(h);
         sg::check_cuda(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
         uint64_t* hdr = static_cast<uint64_t*>(host_dst);
         hdr[0] = kStateMagic;
@@ -473,6 +496,7 @@ int sg_load_state(sg_handle h, const void* host_src, size_t bytes) {
         size_t total = 8 * 5 + 8 * regs.size();
         for (auto& r : regs) total += r.second;
         if (!host_src || bytes != total) sg::fail(SG_EINVAL, "state blob has the wrong size");
+        settle(h);
         const uint64_t* hdr = static_cast<const uint64_t*>(host_src);
         if (hdr[0] != kStateMagic || hdr[1] != regs.size())
             sg::fail(SG_EINVAL, "state blob does not match this handle");

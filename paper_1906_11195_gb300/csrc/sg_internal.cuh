@@ -169,7 +169,8 @@ struct VbPackedDev {
     const uint64_t* seeds;       // [n_graphs]
     const uint32_t* thr;         // [n_graphs][R][64]
     const uint4* groups;         // [n_groups] {first slice, slices, first entry, entries}
-    const uint4* slice_meta;     // [n_slices] {first entry, width, graph, 0}
+    const uint4* slice_meta;     // [n_slices] {first entry, width, graph, upper}: upper =
+                                 // max entries to later colour classes | kind << 16
     const uint32_t* group_graph; // [n_groups] graph of each group (groups never mix graphs)
     const uint8_t* gtab;         // [n_graphs] {uint32 thr[R][64]; uint64 seed; uint64 pad}
     const uint32_t* colour_groups;  // [n_colours+1] first group of each colour class
@@ -221,6 +222,17 @@ struct VbCountJob {
                 // edge once and reports the number of unsatisfied directed entries, twice that)
 };
 
+// slice_meta.w >> 16: how a slice's entries lie relative to its colour class (every entry of
+// every vertex goes to a later class / none does / some do)
+constexpr uint32_t kUpAll = 1u, kUpNone = 0u, kUpMixed = 2u;
+
+// The energy a measuring sweep takes of the state it starts from (one instance): per-lane
+// unsatisfied directed entries added at e_dst[r * stride_r + k * stride_k] (r replica, k lane).
+struct VbSweepMeas {
+    int64_t* e_dst;
+    int64_t stride_r, stride_k;
+};
+
 // launch wrappers (vb_kernels.cu); each returns the number of kernel launches queued
 int vb_packed_init(const VbPackedDev& d, cudaStream_t st);
 // sweep index t = *clock + t_off (the clock lives in device memory so that captured CUDA graphs
@@ -233,8 +245,16 @@ int vb_packed_init(const VbPackedDev& d, cudaStream_t st);
 int vb_packed_sweep(const VbPackedDev& d, const uint32_t* colour_groups, const uint32_t* clock,
                     uint32_t t_off, int variant, bool fused, cudaStream_t st);
 constexpr int kVbColourVariants = 3;
+// The same sweep (same spins, same random numbers) that also adds the energy of the state it
+// starts from (vb_colour_meas.cu); single-instance layouts only.
+int vb_packed_sweep_meas(const VbPackedDev& d, const uint32_t* colour_groups,
+                         const uint32_t* clock, uint32_t t_off, int variant, bool fused,
+                         const VbSweepMeas& meas, cudaStream_t st);
 int vb_packed_snapshot(const VbPackedDev& d, int w, cudaStream_t st);
-int vb_packed_count(const VbPackedDev& d, const VbCountJob& job, cudaStream_t st);
+// also_q (kind 1, with job of kind 0 or 3): the replica overlaps in the same launch, one more
+// pass over the warp's slices (whose current spins are still in L1)
+int vb_packed_count(const VbPackedDev& d, const VbCountJob& job, cudaStream_t st,
+                    const VbCountJob* also_q = nullptr);
 
 int vb_plain_init(const VbPlainDev& d, cudaStream_t st);
 int vb_plain_colour(const VbPlainDev& d, int32_t v_begin, int32_t v_end, const uint32_t* clock,

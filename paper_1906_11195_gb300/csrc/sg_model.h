@@ -87,6 +87,13 @@ public:
     virtual void sweep_many(uint32_t t_off, int n, cudaStream_t st) {
         for (int s = 0; s < n; ++s) sweep(t_off + (uint32_t)s, st);
     }
+    // A measurement a model defers into the next sweep (which takes it from the state it starts
+    // from): has_pending says one is waiting; sweep_pending runs that next sweep (index
+    // *clock_dev + t_off) with it; flush_pending takes it with the standalone kernels instead,
+    // before anything reads the counts or changes the state.
+    virtual bool has_pending() const { return false; }
+    virtual void sweep_pending(uint32_t t_off, cudaStream_t st) { sweep(t_off, st); }
+    virtual void flush_pending(cudaStream_t st) { (void)st; }
     // snapshot w <- current spins
     virtual void snapshot(int w, cudaStream_t st) = 0;
     // scheduled measurement column u at time tau (snapshots with tw <= tau exist)

@@ -193,6 +193,10 @@ public:
             }
         if (kernel == SG_VB_PACKED) build_packed();
         else build_plain();
+        // the energy of a measured state taken by the next sweep (one instance, packed);
+        // SG_VB_FUSED_MEAS=0 keeps the standalone energy kernel (the results are the same)
+        const char* fm = getenv("SG_VB_FUSED_MEAS");
+        fuse_e_ = kernel == SG_VB_PACKED && n_graphs == 1 && !(fm && fm[0] == '0' && !fm[1]);
         Carver c;
         carve(c);
         ws_bytes_ = c.off;
@@ -242,6 +246,17 @@ public:
             } else {
                 tune_variant(st, pinned ? *pin - '0' : -1, pinned_f ? *pin_f - '0' : -1);
             }
+            if (fuse_e_) {
+                // one measuring sweep (into the scratch energy counts of sg_measure, cleared
+                // before each use) sets its kernel up before the first measurement; the initial
+                // spins are drawn again afterwards
+                check_cuda(cudaMemsetAsync(clock_dev, 0, 4, st), "memset");
+                const VbSweepMeas m{mE_, (int64_t)Lc_, 1};
+                const int n = vb_packed_sweep_meas(pk_, colour_group_.data(), clock_dev, 0, variant_,
+                                                   fused_, m, st);
+                if (n < 0) fail(SG_ECUDA, "measuring colour kernel launch failed");
+                launches += n + vb_packed_init(pk_, st);
+            }
         } else {
             up((void*)pl_.row_ptr, h_row_ptr_.data(), h_row_ptr_.size() * 4);
             up((void*)pl_.col, h_col_i_.data(), h_col_i_.size() * 4);
@@ -275,6 +290,7 @@ public:
         int best_v = -1;
         bool best_f = false;
         const bool can_fuse = R != 1 && colour_group_.size() > 2;
+        if (!can_fuse) only_f = -1;  // a fused request runs per class (as the sweep does)
         for (int f = 0; f < (can_fuse ? 2 : 1); ++f) {
             if (only_f >= 0 && f != only_f) continue;
             for (int v = 0; v < kVbColourVariants; ++v) {
@@ -325,6 +341,24 @@ public:
         }
     }
 
+    bool has_pending() const override { return pend_; }
+
+    void sweep_pending(uint32_t t_off, cudaStream_t st) override {
+        if (!pend_) return sweep(t_off, st);
+        pend_ = false;
+        const VbSweepMeas m{pend_job_.dst, pend_job_.stride_r, pend_job_.stride_k};
+        const int n = vb_packed_sweep_meas(pk_, colour_group_.data(), clock_dev, t_off, variant_,
+                                           fused_, m, st);
+        if (n < 0) fail(SG_ECUDA, "measuring colour kernel launch failed");
+        launches += n;
+    }
+
+    void flush_pending(cudaStream_t st) override {
+        if (!pend_) return;
+        pend_ = false;
+        run_job(pend_job_, st);
+    }
+
     void snapshot(int w, cudaStream_t st) override {
         if (kernel_ == SG_VB_PACKED) launches += vb_packed_snapshot(pk_, w, st);
         else if (vb_plain_snapshot(pl_, w, st) < 0) fail(SG_ECUDA, "snapshot copy failed");
@@ -336,24 +370,28 @@ public:
         const int64_t ntw = (int64_t)tw.size();
         int64_t active = 0;
         while (active < ntw && tw[active] <= tau) ++active;
-        if (kernel_ == SG_VB_PACKED && active > 1) {
-            // every active snapshot in one pass over the current spins
+        const VbCountJob qj{1, 0, Qb + u, (int64_t)(R / 2) * Lc_ * ncol, (int64_t)Lc_ * ncol, ncol, 0, 0};
+        if (kernel_ == SG_VB_PACKED && active > 0) {
+            // every active snapshot and the replica overlaps in one pass over the current spins
             VbCountJob j{3, (int)active, Cb + u, (int64_t)R * Lc_ * ntw * ncol,
-                         (int64_t)Lc_ * ntw * ncol, ntw * ncol, ncol};
-            run_job(j, st);
+                         (int64_t)Lc_ * ntw * ncol, ntw * ncol, ncol, 0};
+            launches += vb_packed_count(pk_, j, st, R >= 2 ? &qj : nullptr);
         } else {
             for (int64_t w = 0; w < active; ++w) {
                 VbCountJob j{0, (int)w, Cb + w * ncol + u, (int64_t)R * Lc_ * ntw * ncol,
-                             (int64_t)Lc_ * ntw * ncol, ntw * ncol, 0};
+                             (int64_t)Lc_ * ntw * ncol, ntw * ncol, 0, 0};
                 run_job(j, st);
             }
+            if (R >= 2) run_job(qj, st);
         }
-        if (R >= 2) {
-            VbCountJob j{1, 0, Qb + u, (int64_t)(R / 2) * Lc_ * ncol, (int64_t)Lc_ * ncol, ncol, 0};
-            run_job(j, st);
+        const VbCountJob ej{2, 0, Eb + u, (int64_t)R * Lc_ * ncol, (int64_t)Lc_ * ncol, ncol, 0, 0};
+        if (fuse_e_) {
+            flush_pending(st);  // two measurements of one state (a schedule and a window)
+            pend_ = true;
+            pend_job_ = ej;
+        } else {
+            run_job(ej, st);
         }
-        VbCountJob j{2, 0, Eb + u, (int64_t)R * Lc_ * ncol, (int64_t)Lc_ * ncol, ncol, 0};
-        run_job(j, st);
     }
 
     void measure_scheduled(int u, int64_t tau, cudaStream_t st) override {
@@ -402,6 +440,7 @@ public:
     }
 
     void measure_now(int64_t tau, cudaStream_t st) override {
+        flush_pending(st);
         const int64_t ntw = (int64_t)tw.size();
         check_cuda(cudaMemsetAsync(mC_, 0, nmC() * 8, st), "memset");
         check_cuda(cudaMemsetAsync(mQ_, 0, nmQ() * 8, st), "memset");
@@ -751,11 +790,13 @@ private:
         // upper entries (energy measurement): neighbours in later colour classes only
         h_up_base_.assign(n_slices + 1, 0);
         std::vector<int32_t> up_width(n_slices, 0);
+        std::vector<uint32_t> up_kind(n_slices, kUpNone);
         parallel_ranges(n_slices, [&](int64_t s0, int64_t s1) {
             for (int64_t s = s0; s < s1; ++s) {
                 const int b = (int)h_slice_graph_[s];
                 const Graph& g = graphs_[b];
                 int w = 0;
+                bool all = true;
                 for (int l = 0; l < 32; ++l) {
                     const int64_t slot = s * 32 + l;
                     const int32_t i = slot_graph_vertex[slot];
@@ -764,8 +805,10 @@ private:
                     for (int32_t k = g.row_ptr[i]; k < g.row_ptr[i + 1]; ++k)
                         n_up += slot_of_[b][g.col[k]] > slot;
                     w = std::max(w, n_up);
+                    all = all && n_up == g.row_ptr[i + 1] - g.row_ptr[i];
                 }
                 up_width[s] = w;
+                up_kind[s] = w == 0 ? kUpNone : all ? kUpAll : kUpMixed;
             }
         });
         int64_t up_entries = 0;
@@ -807,7 +850,7 @@ private:
             m.x = h_slice_base_[s];
             m.y = (h_slice_base_[s + 1] - h_slice_base_[s]) / 32;
             m.z = h_slice_graph_[s];
-            m.w = 0;
+            m.w = (uint32_t)up_width[s] | up_kind[s] << 16;
             h_slice_meta_[s] = m;
         }
         // staging groups: consecutive slices of one colour, <= 8 slices and <= 1024 entries;
@@ -848,6 +891,9 @@ private:
     }
 
     int kernel_ = SG_VB_PACKED;
+    bool fuse_e_ = false;  // the energy of a measured state is taken by the next sweep
+    bool pend_ = false;    // such a measurement is waiting for that sweep (pend_job_ its target)
+    VbCountJob pend_job_{};
     int variant_ = 0;     // colour-kernel pipeline shape chosen by the autotuner at attach
     bool fused_ = false;  // one cooperative launch per sweep (else one launch per colour class)
     int Lc_ = 64;

@@ -139,6 +139,57 @@ def test_packed_fused_small_and_batched(monkeypatch, fused):
         assert_matches_oracle(g, 64, 2, sg.SG_VB_PACKED, 40, tw, tm, spins, C, q, E, b=b)
 
 
+def hub_instance(n, c, gseed, temps, seed, hub_degree=63):
+    """A Poisson graph plus one vertex joined to hub_degree others (a wide slice)."""
+    rp, col, _ = sg_inputs.poisson_graph(n, c, gseed)
+    deg = np.diff(rp)
+    rows = np.repeat(np.arange(n), deg)
+    keep = rows < col
+    ei, ej = rows[keep], col[keep]
+    rng = np.random.default_rng(gseed)
+    cand = np.flatnonzero(deg < 63)
+    leaves = rng.choice(cand, size=hub_degree, replace=False)
+    ei = np.concatenate([ei, np.full(hub_degree, n)])
+    ej = np.concatenate([ej, leaves])
+    rp, col, eid = sg_inputs.csr_from_edges(n + 1, ei, ej)
+    jb = sg_inputs.vb_lane_couplings(eid, eid.max() + 1, gseed)
+    return dict(row_ptr=rp, col=col, jbits=jb, seed=seed, temps=list(temps))
+
+
+@pytest.mark.parametrize("fused", [0, 1])
+@pytest.mark.parametrize("R,temps", [(1, [0.8]), (2, [1.0, 0.6]), (4, [1.0, 1.0, 0.6, 0.6])])
+def test_energy_taken_by_the_next_sweep(monkeypatch, fused, R, temps):
+    """The energy of a measured state is counted by the sweep after it (from the words it
+    starts from; the neighbours in later colour classes are not updated yet when a vertex is),
+    or by the standalone kernel when a read or a checkpoint comes first.  Every sweep measured,
+    results read and a checkpoint taken right after a measurement, a vertex of degree 63;
+    equal to the oracle and to the standalone kernel alone (SG_VB_FUSED_MEAS=0)."""
+    monkeypatch.setenv("SG_VB_FUSED", str(fused))
+    g = hub_instance(5000, 4.0, 41 + R, temps, 2**35 + R)
+    S = 24
+    tw = np.array([0, 3, 10], dtype=np.int64)
+    tm = np.arange(0, S + 1, dtype=np.int64)
+    monkeypatch.setenv("SG_VB_FUSED_MEAS", "0")
+    ref_run = run_gpu([g], 64, R, sg.SG_VB_PACKED, S, tw, tm)
+    monkeypatch.delenv("SG_VB_FUSED_MEAS")
+    run = sg.VBRun([g], n_lanes=64, n_replicas=R, kernel=sg.SG_VB_PACKED, tw=tw, tm=tm)
+    run.sweep(5)
+    run.results()              # deferred energy of tau = 5 taken now ...
+    run.sweep(6)               # ... and not again by the next sweep
+    blob = run.save_state()    # tau = 11, a measurement time
+    run.close()
+    run = sg.VBRun([g], n_lanes=64, n_replicas=R, kernel=sg.SG_VB_PACKED, tw=tw, tm=tm)
+    run.load_state(blob)
+    run.sweep(S - 11)
+    run.synchronize()
+    C, q, E = run.results()
+    spins = run.spins()
+    run.close()
+    for x, y in zip((spins, C, q, E), ref_run[:4]):
+        assert np.array_equal(np.asarray(x), np.asarray(y))
+    assert_matches_oracle(g, 64, R, sg.SG_VB_PACKED, S, tw, tm, spins, C, q, E)
+
+
 def test_packed_isolated_vertices_and_max_degree():
     # a star with 63 leaves (maximum degree), a path, and isolated vertices (always flip: dE = 0)
     n = 100
