@@ -122,7 +122,7 @@ def kernel_source_hash():
     not invalidate the recorded traffic, while any code change does)."""
     import re
     h = hashlib.sha256()
-    for f in ("vb_kernels.cu", "sg_internal.cuh"):
+    for f in ("vb_colour.cuh", "sg_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1906_11195_gb300", "csrc", f)) as fh:
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
