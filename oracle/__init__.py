@@ -50,6 +50,8 @@ def _bind(lib):
     lib.orc_sk_thresholds.restype = None
     lib.orc_greedy_colour.argtypes = [i32, P, P, P]
     lib.orc_greedy_colour.restype = i32
+    lib.orc_recolour.argtypes = [i32, P, P, P]
+    lib.orc_recolour.restype = i32
     lib.orc_vb_run.argtypes = [i32, P, P, P, i32, i32, P, u64, i64,
                                P, i32, P, i32, P, P, P, P, P]
     lib.orc_vb_run.restype = i32
@@ -135,6 +137,25 @@ def greedy_colour(row_ptr, col):
     if nc < 0:
         raise MemoryError("oracle colouring failed")
     return colour, int(nc)
+
+
+def recolour(row_ptr, col, colour):
+    """One recolouring pass: greedy again in the order (decreasing colour, increasing label)
+    -> (colour int32[N], number of colours)."""
+    lib = _load()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    out = np.array(colour, dtype=np.int32, copy=True)
+    nc = lib.orc_recolour(rp.size - 1, _ptr(rp), _ptr(cl), _ptr(out))
+    if nc < 0:
+        raise MemoryError("oracle recolouring failed")
+    return out, int(nc)
+
+
+def vb_colouring(row_ptr, col):
+    """The colour classes a VB sweep visits in turn: greedy_colour, then one recolour pass."""
+    colour, _ = greedy_colour(row_ptr, col)
+    return recolour(row_ptr, col, colour)
 
 
 def _sched(a):

@@ -29,8 +29,11 @@
  *     counter (i, 0, r, 1); bit = 1 means s = -1.  SK uses lane bit 0.
  *   - Acceptance: flip iff dE <= 0 or r32 < thr, with thr = min(2^32 - 1,
  *     floor(2^32 * exp(-beta * dE))) evaluated in double precision.
- *   - A colour class is updated in increasing vertex order (irrelevant: it is an independent
- *     set and the random number is keyed by the vertex).
+ *   - The colour classes come from a greedy colouring in vertex order followed by one
+ *     recolouring pass (greedy again, in the order of decreasing colour and increasing label),
+ *     which never adds a colour and removes the thin last classes of the first pass; a sweep
+ *     updates class 0, 1, ... in turn.  A colour class is updated in increasing vertex order
+ *     (irrelevant: it is an independent set and the random number is keyed by the vertex).
  *   - Time tau = number of completed sweeps; snapshots for C are taken at tau = t_w before the
  *     measurement at the same tau.
  *
@@ -146,6 +149,51 @@ int32_t orc_greedy_colour(int32_t N, const int32_t *row_ptr, const int32_t *col,
     return ncol;
 }
 
+/* One recolouring pass: the vertices are coloured greedily again, in the order of decreasing
+ * colour and, within a colour, increasing label.  The vertices of one old class form an
+ * independent set, so the new colouring uses no more colours than the old one (the iterated
+ * greedy argument).  colour[] is replaced.  Returns the number of colours, or a negative
+ * error. */
+int32_t orc_recolour(int32_t N, const int32_t *row_ptr, const int32_t *col, int32_t *colour)
+{
+    int32_t maxdeg = 0, ncol_in = 0;
+    for (int32_t i = 0; i < N; ++i) {
+        int32_t d = row_ptr[i + 1] - row_ptr[i];
+        if (d > maxdeg) maxdeg = d;
+        if (colour[i] + 1 > ncol_in) ncol_in = colour[i] + 1;
+    }
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+    int32_t *fresh = (int32_t *)malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+    char *used = (char *)calloc((size_t)maxdeg + 2, 1);
+    if (!order || !fresh || !used) return ORC_ENOMEM;
+    int32_t pos = 0;
+    for (int32_t c = ncol_in - 1; c >= 0; --c)
+        for (int32_t i = 0; i < N; ++i)
+            if (colour[i] == c) order[pos++] = i;
+    for (int32_t i = 0; i < N; ++i) fresh[i] = -1;
+    int32_t ncol = 0;
+    for (int32_t k = 0; k < N; ++k) {
+        int32_t i = order[k];
+        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            int32_t c = fresh[col[e]];
+            if (c >= 0 && c <= maxdeg + 1) used[c] = 1;
+        }
+        int32_t c = 0;
+        while (used[c]) ++c;
+        fresh[i] = c;
+        if (c + 1 > ncol) ncol = c + 1;
+        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            int32_t cj = fresh[col[e]];
+            if (cj >= 0 && cj <= maxdeg + 1) used[cj] = 0;
+        }
+    }
+    for (int32_t i = 0; i < N; ++i) colour[i] = fresh[i];
+    free(order);
+    free(fresh);
+    free(used);
+    return ncol;
+}
+
 static int32_t index_of(const int64_t *list, int32_t n, int64_t v)
 {
     for (int32_t k = 0; k < n; ++k)
@@ -185,6 +233,8 @@ int32_t orc_vb_run(int32_t N, const int32_t *row_ptr, const int32_t *col, const 
     int8_t **snap = (int8_t **)calloc((size_t)(n_tw > 0 ? n_tw : 1), sizeof(int8_t *));
     if (!colour || !s || !thr || !snap) return ORC_ENOMEM;
     int32_t ncol = orc_greedy_colour(N, row_ptr, col, colour);
+    if (ncol >= 0) ncol = orc_recolour(N, row_ptr, col, colour);
+    if (ncol < 0) return ncol;
     for (int32_t r = 0; r < R; ++r) orc_vb_thresholds(T[r], dmax, thr + (size_t)r * (dmax + 1));
 
     /* quench: random initial configuration */

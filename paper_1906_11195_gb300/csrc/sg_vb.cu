@@ -2,7 +2,8 @@
 // (plain colour-major CSR and packed sliced-ELL), measurement bookkeeping.
 //
 // Update order: the vertices of a graph are coloured greedily in vertex order (each vertex gets
-// the smallest colour not used by an already-coloured neighbour); a sweep updates colour class
+// the smallest colour not used by an already-coloured neighbour), then greedily once more in the
+// order of decreasing colour (increasing label inside a colour); a sweep updates colour class
 // 0, then 1, ...  Each class is an independent set, so its vertices can be updated in parallel;
 // this generalises the bipartite half-updates of SI section 3 to the Poissonian graphs of the
 // Viana-Bray ensemble (Eq. 3).  The random number of a vertex is keyed by its original label,
@@ -107,7 +108,31 @@ void load_graph(const sg_vb_graph& in, int R, int idx, Graph& g) {
             if (cj >= 0) used[cj] = 0;
         }
     }
-    g.n_colours = nc;
+    // one recolouring pass: greedy again, visiting the classes from the last to the first
+    // (vertex order inside a class).  Each old class is an independent set, so no colour is
+    // added, and the thin last classes of the first pass are folded into the others.
+    std::vector<int32_t> start(nc + 1, 0), order(n);
+    for (int32_t i = 0; i < n; ++i) ++start[nc - g.colour[i]];
+    for (int c = 0; c < nc; ++c) start[c + 1] += start[c];
+    for (int32_t i = 0; i < n; ++i) order[start[nc - 1 - g.colour[i]]++] = i;
+    std::vector<int32_t> fresh(n, -1);
+    int nc2 = 0;
+    for (int32_t i : order) {
+        for (int32_t e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e) {
+            const int c = fresh[g.col[e]];
+            if (c >= 0) used[c] = 1;
+        }
+        int c = 0;
+        while (used[c]) ++c;
+        fresh[i] = c;
+        nc2 = std::max(nc2, c + 1);
+        for (int32_t e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e) {
+            const int cj = fresh[g.col[e]];
+            if (cj >= 0) used[cj] = 0;
+        }
+    }
+    g.colour.swap(fresh);
+    g.n_colours = nc2;
 }
 
 // Validate and colour every graph of a batch, one graph per task on the host's cores (the

@@ -24,6 +24,9 @@ VB_MUTATIONS = {
     "colour_flags_never_cleared": ("if (cj >= 0 && cj <= maxdeg + 1) used[cj] = 0;", ";"),
     "colour_skips_last_neighbour": ("for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {\n            int32_t c = colour[col[e]];",
                                     "for (int32_t e = row_ptr[i]; e + 1 < row_ptr[i + 1]; ++e) {\n            int32_t c = colour[col[e]];"),
+    # ... and the recolouring pass after it
+    "recolour_skipped": ("if (ncol >= 0) ncol = orc_recolour(N, row_ptr, col, colour);", ";"),
+    "recolour_in_increasing_colour": ("for (int32_t c = ncol_in - 1; c >= 0; --c)", "for (int32_t c = 0; c < ncol_in; ++c)"),
 }
 
 SK_MUTATIONS = {

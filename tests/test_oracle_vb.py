@@ -3,7 +3,7 @@
 * Brute force: an independent Python restatement that takes each single-spin Metropolis
   decision from the full Hamiltonian H = -sum_{(ij)} J_ij s_i s_j (Eq. 3), i.e. from
   H(s with s_i flipped) - H(s), with acceptance thresholds computed in arbitrary precision and
-  its own greedy colouring.  Trajectories must agree bit for bit.
+  its own colouring (greedy, then one recolouring pass).  Trajectories must agree bit for bit.
 * Exact Boltzmann enumeration on N = 6: the long-run state histogram of the oracle's chain.
 * T = 0 (energy never rises) and T = infinity (every spin flips every sweep) limits.
 * Measurements: C(t_w, t_w) = N, |C| <= N, C = N (mod 2), energies recomputed from spins.
@@ -66,6 +66,15 @@ def brute_vb(rp, col, jbits, L, temps, seed, n_sweeps):
         while c in used:
             c += 1
         colour[i] = c
+    # one recolouring pass: greedy again over (decreasing colour, increasing label)
+    fresh = [-1] * n
+    for i in sorted(range(n), key=lambda i: (-colour[i], i)):
+        used = {fresh[j] for j in col[rp[i]:rp[i + 1]] if fresh[j] >= 0}
+        c = 0
+        while c in used:
+            c += 1
+        fresh[i] = c
+    colour = fresh
     order = sorted(range(n), key=lambda i: (colour[i], i))
     s = np.zeros((R, L, n), dtype=np.int8)
     for r in range(R):
