@@ -1133,13 +1133,20 @@ def run_gpu(args):
         bufs.append(torch.empty(nb, dtype=torch.uint8, device=dev))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    each = []
     for (h, nb), buf in zip(handles, bufs):
+        ta = time.perf_counter()
         sg.sg_attach(h, buf.data_ptr(), nb, stream.cuda_stream)
+        each.append((time.perf_counter() - ta) * 1e3)
+    t1 = time.perf_counter()
     for h, _ in handles:
         sg.sg_sweep(h, args.warmup + args.steps)
+    t2 = time.perf_counter()
     for h, _ in handles:
         C, q, E = sg.sg_read_results(h)
     e2e_s = time.perf_counter() - t0
+    phases = {"attach_ms": (t1 - t0) * 1e3, "attach_ms_each": each, "sweep_calls_ms": (t2 - t1) * 1e3,
+              "read_ms": (time.perf_counter() - t2) * 1e3}
     h2d = d2h = 0
     for h, _ in handles:
         a, b = sg.sg_transfer_bytes(h)
@@ -1149,8 +1156,11 @@ def run_gpu(args):
     e2e_steps = args.warmup + args.steps
     e2e = {"value": ws * updates_per_step * e2e_steps / (e2e_s * 1e9), "unit": "spin updates/ns",
            "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
+           "phases": phases,
            "note": "H2D of both instances' images at attach + sweeps + D2H of all counts (bytes "
-                   "counted by the library), spread over the steps"}
+                   "counted by the library), spread over the steps; phases: host time of the "
+                   "attach calls (copies, autotuner), the sweep calls (queued) and the reads "
+                   "(which wait for the sweeps)"}
 
     # the other configurations of the metric, each with its own value, roofline, e2e, clocks
     # and CPU baseline (one GPU only; each is a separate JSON object inside the line)

@@ -14,7 +14,9 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -268,8 +270,11 @@ public:
             if (pinned && pinned_f) {
                 variant_ = *pin - '0';
                 fused_ = *pin_f == '1';
+            } else if (!pinned && !pinned_f && tuned_before()) {
+                // an instance of the same layout was tuned in this process: its choice holds
             } else {
                 tune_variant(st, pinned ? *pin - '0' : -1, pinned_f ? *pin_f - '0' : -1);
+                if (!pinned && !pinned_f) remember_tuning();
             }
             if (fuse_e_) {
                 // one measuring sweep (into the scratch energy counts of sg_measure, cleared
@@ -299,6 +304,38 @@ public:
         }
         check_cuda(cudaGetLastError(), "init launch");
         check_cuda(cudaStreamSynchronize(st), "attach");
+    }
+
+    // The autotuner's choice per layout shape (slots, entries, colour classes, groups, replicas,
+    // device), kept for the process: the timings depend on nothing else.
+    using TuneKey = std::vector<int64_t>;
+    static std::mutex& tune_mutex() {
+        static std::mutex m;
+        return m;
+    }
+    static std::map<TuneKey, std::pair<int, bool>>& tune_cache() {
+        static std::map<TuneKey, std::pair<int, bool>> c;
+        return c;
+    }
+    TuneKey tune_key() const {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        TuneKey k{dev, n_slots_, (int64_t)h_col_.size(), (int64_t)colour_group_.size(),
+                  (int64_t)h_groups_.size(), R, n_inst};
+        k.insert(k.end(), colour_group_.begin(), colour_group_.end());
+        return k;
+    }
+    bool tuned_before() {
+        std::lock_guard<std::mutex> g(tune_mutex());
+        auto it = tune_cache().find(tune_key());
+        if (it == tune_cache().end()) return false;
+        variant_ = it->second.first;
+        fused_ = it->second.second;
+        return true;
+    }
+    void remember_tuning() {
+        std::lock_guard<std::mutex> g(tune_mutex());
+        tune_cache()[tune_key()] = {variant_, fused_};
     }
 
     // Autotuner: time two sweeps with each pipeline shape of the colour kernel, launched per
