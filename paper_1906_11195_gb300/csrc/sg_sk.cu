@@ -81,6 +81,9 @@ void make_map_2d_u16(CUtensorMap* map, const void* base, uint64_t inner, uint64_
 
 class SkModel : public Model {
 public:
+    // prefer few CTAs per persistent launch (set before attach by a batch)
+    void set_compact(bool c) { compact_ = c; }
+
     SkModel(int n, const int8_t* J, int n_replicas, const double* temps, uint64_t seed, int kernel,
             int block, const std::vector<int64_t>& tw_, const std::vector<int64_t>& tm_) {
         if (kernel != SG_SK_PLAIN && kernel != SG_SK_BLOCKED) fail(SG_EINVAL, "unknown SK kernel");
@@ -440,10 +443,14 @@ private:
         a.L = L;
         a.n_sweeps = 1;
         a.Q = kPersistSlots;
-        for (int W : {4, 8}) {
+        // alone: the smallest TPC and W whose CTAs all fit (the field work spread widest); in a
+        // batch (compact_): the largest, so that more samples' launches run side by side
+        const int Ws[2] = {compact_ ? 8 : 4, compact_ ? 4 : 8};
+        const int TPCs[3] = {compact_ ? 4 : 1, 2, compact_ ? 1 : 4};
+        for (int W : Ws) {
             if (R % W) continue;
-            for (int TPC : {1, 2, 4}) {
-                if (TPC * R > 512) break;
+            for (int TPC : TPCs) {
+                if (TPC * R > 512) continue;
                 a.W = W;
                 a.nC = R / W;
                 a.TPC = TPC;
@@ -589,6 +596,7 @@ private:
     static constexpr int kPersistSlots = kSkPersistSlots;  // spin-change ring slots
     int kernel_ = SG_SK_BLOCKED;
     bool autotune_ = false;
+    bool compact_ = false;
     bool persist_ = false;   // B = 128 sweeps run as one persistent launch
     SkPersistArgs pa_{};
     CUtensorMap mapDr_{};
@@ -651,6 +659,10 @@ public:
             const sg_sk_sample& x = samples[b];
             try {
                 subs_.emplace_back(new SkModel(x.n, x.J, n_replicas, x.temps, x.seed, kernel, block, tw, tm));
+                // the samples' persistent launches share the GPU: few CTAs each
+                // (SG_SK_BATCH_COMPACT=0: each as if alone; the results are the same)
+                const char* c = getenv("SG_SK_BATCH_COMPACT");
+                subs_.back()->set_compact(!(c && c[0] == '0' && !c[1]));
             } catch (const Error& e) {
                 fail(e.code, "sample " + std::to_string(b) + ": " + e.msg);
             }
