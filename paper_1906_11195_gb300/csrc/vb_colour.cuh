@@ -539,9 +539,9 @@ __device__ __noinline__ void meas_flush(MeasAcc<R>& acc, unsigned long long* s_m
 // MEAS (a graph of one instance): the sweep also adds the energy of the state it starts from
 // into meas.e_dst, two per unsatisfied edge (the directed count), flushed once per CTA.
 template <int R, int NSS, int NG, int L, bool MEAS>
-__global__ void __launch_bounds__(32 * (kGroupSlices + 1), MEAS && R <= 2 ? 2 : 1)
-    k_vb_packed_colour(VbPackedDev d, uint32_t c_begin, uint32_t c_end,
-                       const uint32_t* __restrict__ clock, uint32_t t_off, VbSweepMeas meas) {
+__device__ __forceinline__ void colour_sweep(const VbPackedDev& d, uint32_t c_begin, uint32_t c_end,
+                                             const uint32_t* __restrict__ clock, uint32_t t_off,
+                                             const VbSweepMeas& meas) {
     static_assert(L >= 1 && L < NG && L < NSS, "gathers run L groups ahead inside both rings");
     extern __shared__ __align__(128) uint8_t smem_raw[];
     __shared__ uint32_t s_kc[kVbMaxColours + 1];  // first ring index of each class (this CTA)
@@ -756,6 +756,22 @@ __global__ void __launch_bounds__(32 * (kGroupSlices + 1), MEAS && R <= 2 ? 2 : 
     }
 }
 
+// the kernels: plain sweeps, and the sweep after a measurement (its energy taken on the way;
+// two CTAs per SM for R <= 2 as for the plain sweep, the registers capped to that)
+template <int R, int NSS, int NG, int L>
+__global__ void __launch_bounds__(32 * (kGroupSlices + 1))
+    k_vb_packed_colour(VbPackedDev d, uint32_t c_begin, uint32_t c_end,
+                       const uint32_t* __restrict__ clock, uint32_t t_off, VbSweepMeas meas) {
+    colour_sweep<R, NSS, NG, L, false>(d, c_begin, c_end, clock, t_off, meas);
+}
+
+template <int R, int NSS, int NG, int L>
+__global__ void __launch_bounds__(32 * (kGroupSlices + 1), R <= 2 ? 2 : 1)
+    k_vb_packed_colour_meas(VbPackedDev d, uint32_t c_begin, uint32_t c_end,
+                            const uint32_t* __restrict__ clock, uint32_t t_off, VbSweepMeas meas) {
+    colour_sweep<R, NSS, NG, L, true>(d, c_begin, c_end, clock, t_off, meas);
+}
+
 template <int R, int NSS, int NG>
 static constexpr size_t colour_smem() {
     return NSS * sizeof(VbStream<R>) + NG * sizeof(VbGath<R>) + (2 * NSS + NG) * sizeof(uint64_t);
@@ -781,7 +797,10 @@ static int colour_launch_v(const VbPackedDev& d, uint32_t c_begin, uint32_t c_en
                            int per_sm, cudaStream_t st) {
     constexpr size_t smem = colour_smem<R, NSS, NG>();
     static_assert(smem <= 227 * 1024, "pipeline shape exceeds the shared memory of one CTA");
-    auto kern = k_vb_packed_colour<R, NSS, NG, L, MEAS>;
+    auto kern = [] {
+        if constexpr (MEAS) return k_vb_packed_colour_meas<R, NSS, NG, L>;
+        else return k_vb_packed_colour<R, NSS, NG, L>;
+    }();
     static int resident = -1;
     if (resident < 0) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
