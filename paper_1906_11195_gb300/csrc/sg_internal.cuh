@@ -251,6 +251,9 @@ int vb_packed_sweep_meas(const VbPackedDev& d, const uint32_t* colour_groups,
                          const uint32_t* clock, uint32_t t_off, int variant, bool fused,
                          const VbSweepMeas& meas, cudaStream_t st);
 int vb_packed_snapshot(const VbPackedDev& d, int w, cudaStream_t st);
+// the upper entries (each vertex's neighbours in later colour classes, padded with the vertex
+// itself and J = 0) from col and jb, given up_slice_base
+int vb_packed_build_upper(const VbPackedDev& d, cudaStream_t st);
 // also_q (kind 1, with job of kind 0 or 3): the replica overlaps in the same launch, one more
 // pass over the warp's slices (whose current spins are still in L1)
 int vb_packed_count(const VbPackedDev& d, const VbCountJob& job, cudaStream_t st,

@@ -258,8 +258,7 @@ public:
             for (int b = 0; b < n_inst; ++b) seeds[b] = graphs_[b].seed;
             up((void*)pk_.seeds, seeds.data(), seeds.size() * 8);
             up((void*)pk_.up_slice_base, h_up_base_.data(), h_up_base_.size() * 4);
-            up((void*)pk_.up_col, h_up_col_.data(), h_up_col_.size() * 4);
-            up((void*)pk_.up_jb, h_up_jb_.data(), h_up_jb_.size() * 8);
+            launches += vb_packed_build_upper(pk_, st);  // from col and jb, on the device
             launches += vb_packed_init(pk_, st);
             // SG_VB_COLOUR_VARIANT=<k> and SG_VB_FUSED=<0|1> pin the pipeline shape and the
             // launch form (reproducible timings of one choice); otherwise the autotuner picks
@@ -682,8 +681,8 @@ private:
             pk_.jb = c.take<uint64_t>(h_jb_.size());
             pk_.seeds = c.take<uint64_t>(n_inst);
             pk_.up_slice_base = c.take<uint32_t>(h_up_base_.size());
-            pk_.up_col = c.take<uint32_t>(h_up_col_.size());
-            pk_.up_jb = c.take<uint64_t>(h_up_jb_.size());
+            pk_.up_col = c.take<uint32_t>(up_entries_);
+            pk_.up_jb = c.take<uint64_t>(up_entries_);
             pk_.S = c.take<uint64_t>((size_t)n_slots_ * R);
             pk_.snap = c.take<uint64_t>((size_t)n_slots_ * R * tw.size());
             pk_.thr = d_thr_;
@@ -879,33 +878,7 @@ private:
             up_entries += 32 * (int64_t)up_width[s];
         }
         h_up_base_[n_slices] = (uint32_t)up_entries;
-        h_up_col_.assign(up_entries, 0);
-        h_up_jb_.assign(up_entries, 0);
-        parallel_ranges(n_slices, [&](int64_t s0, int64_t s1) {
-            for (int64_t s = s0; s < s1; ++s) {
-                const int b = (int)h_slice_graph_[s];
-                const Graph& g = graphs_[b];
-                const int64_t base = h_up_base_[s];
-                const int width = up_width[s];
-                for (int l = 0; l < 32; ++l) {
-                    const int64_t slot = s * 32 + l;
-                    const int32_t i = slot_graph_vertex[slot];
-                    int e = 0;
-                    if (i >= 0)
-                        for (int32_t k = g.row_ptr[i]; k < g.row_ptr[i + 1]; ++k) {
-                            const int64_t sj = slot_of_[b][g.col[k]];
-                            if (sj <= slot) continue;
-                            h_up_col_[base + (int64_t)e * 32 + l] = (uint32_t)sj;
-                            h_up_jb_[base + (int64_t)e * 32 + l] = g.jb[k];
-                            ++e;
-                        }
-                    for (; e < width; ++e) {  // padding: the vertex itself, no coupling
-                        h_up_col_[base + (int64_t)e * 32 + l] = (uint32_t)slot;
-                        h_up_jb_[base + (int64_t)e * 32 + l] = 0;
-                    }
-                }
-            }
-        });
+        up_entries_ = up_entries;  // filled on the device at attach (vb_packed_build_upper)
         h_slice_meta_.resize(n_slices);
         for (int64_t s = 0; s < n_slices; ++s) {
             uint4 m;
@@ -972,9 +945,8 @@ private:
     std::vector<uint32_t> h_slice_base_, h_slice_graph_;
     pinned_vector<uint32_t> h_vinfo_, h_col_;  // the large images copied at attach: page-locked
     pinned_vector<uint64_t> h_jb_;
-    std::vector<uint32_t> h_up_base_;               // upper entries (energy measurement)
-    pinned_vector<uint32_t> h_up_col_;
-    pinned_vector<uint64_t> h_up_jb_;
+    std::vector<uint32_t> h_up_base_;  // upper entries (energy measurement): slice bases
+    int64_t up_entries_ = 0;
     // plain host layout
     std::vector<int32_t> colour_begin_, new_of_, h_row_ptr_, h_col_i_;
     std::vector<uint32_t> h_orig_;

@@ -54,6 +54,42 @@ int vb_packed_sweep(const VbPackedDev& d, const uint32_t* colour_groups, const u
 }
 
 // ---------------------------------------------------------------------------------------------
+// upper entries: one thread per slot keeps, in order, the entries whose neighbour lies in a
+// later colour class (a higher slot), and pads the rest of its upper width with itself
+// ---------------------------------------------------------------------------------------------
+__global__ void k_vb_build_upper(VbPackedDev d) {
+    const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= d.n_slots) return;
+    const int64_t s = slot >> 5;
+    const uint32_t l = (uint32_t)(slot & 31);
+    const uint32_t base = d.slice_base[s], width = (d.slice_base[s + 1] - base) >> 5;
+    const uint32_t ub = d.up_slice_base[s], uw = (d.up_slice_base[s + 1] - ub) >> 5;
+    uint32_t* up_col = const_cast<uint32_t*>(d.up_col);
+    uint64_t* up_jb = const_cast<uint64_t*>(d.up_jb);
+    uint32_t e2 = 0;
+    for (uint32_t e = 0; e < width; ++e) {
+        const uint32_t idx = base + 32 * e + l;
+        const uint32_t c = d.col[idx];
+        if ((int64_t)c > slot && e2 < uw) {
+            up_col[ub + 32 * e2 + l] = c;
+            up_jb[ub + 32 * e2 + l] = d.jb[idx];
+            ++e2;
+        }
+    }
+    for (; e2 < uw; ++e2) {
+        up_col[ub + 32 * e2 + l] = (uint32_t)slot;
+        up_jb[ub + 32 * e2 + l] = 0ull;
+    }
+}
+
+int vb_packed_build_upper(const VbPackedDev& d, cudaStream_t st) {
+    if (!d.up_slice_base || d.n_slots == 0) return 0;
+    const int bs = 256;
+    k_vb_build_upper<<<(unsigned)((d.n_slots + bs - 1) / bs), bs, 0, st>>>(d);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------------------------
 // snapshot copy (16-byte vectors; the regions are 256-byte aligned and a multiple of 16 bytes)
 // ---------------------------------------------------------------------------------------------
 __global__ void k_copy16(const uint4* __restrict__ src, uint4* __restrict__ dst, int64_t n16) {
