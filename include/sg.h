@@ -247,6 +247,18 @@ int sg_launch_count(sg_handle h, int64_t *count);
  * Library service; no counterpart in the paper. */
 int sg_transfer_bytes(sg_handle h, int64_t *h2d, int64_t *d2h);
 
+/* The operations of one blocked SK sweep (blocks of 64 .. 512 spins, the launch-per-block
+ * form) for n spins, in the order the library issues them, 6 int32 each: {op, stream, block,
+ * skip0, skip1, event}.  op 0: the K* table; 1: the in-block kernel of block `block`; 2: the
+ * update of every field row by that block; 3: the update of every row tile outside
+ * [skip0, skip1); 4: record event `event` on `stream`; 5: make `stream` wait for it.  Stream 0
+ * is the handle's stream, 1 its side stream; events 0 and 1 are "in-block done" (block parity),
+ * 2 and 3 "side done".  *n_ops receives the number of operations; ops may be NULL with cap 0 to
+ * query it; a smaller cap returns SG_EINVAL.  Needs no device.  Library service (host-side
+ * checking of the launch schedule); no counterpart in the paper, whose SK sweep (SI section 1)
+ * is sequential. */
+int sg_sk_blocked_schedule(int32_t n, int32_t block, int32_t *ops, int32_t cap, int32_t *n_ops);
+
 /* SK local fields h[r][i] = sum_j J_ij s[r][j] computed on the tensor cores without allocating
  * any device memory.  The paper has no counterpart: this is a service for callers that cannot
  * allocate device memory where they need the fields -- a host application that fixes the

@@ -37,7 +37,7 @@ EXPORTED = [
     "sg_sweep", "sg_time", "sg_synchronize", "sg_result_shape", "sg_read_results", "sg_measure",
     "sg_get_spins", "sg_get_thresholds", "sg_state_bytes", "sg_save_state", "sg_load_state",
     "sg_destroy", "sg_launch_count", "sg_sk_fields_noalloc", "sg_set_windows", "sg_read_windows",
-    "sg_set_schedule", "sg_transfer_bytes",
+    "sg_set_schedule", "sg_transfer_bytes", "sg_sk_blocked_schedule",
 ]
 
 
@@ -101,6 +101,7 @@ def _load():
                 "sg_read_windows": (ctypes.c_int, [H, P, P, P, P]),
                 "sg_set_schedule": (ctypes.c_int, [H, P, i32, P, i32]),
                 "sg_transfer_bytes": (ctypes.c_int, [H, P, P]),
+                "sg_sk_blocked_schedule": (ctypes.c_int, [i32, i32, P, i32, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -292,6 +293,17 @@ def sg_transfer_bytes(h):
     a, b = ctypes.c_int64(), ctypes.c_int64()
     _check(_load().sg_transfer_bytes(h, ctypes.byref(a), ctypes.byref(b)))
     return int(a.value), int(b.value)
+
+
+def sg_sk_blocked_schedule(n, block):
+    """The blocked SK sweep's operations in issue order: int32[n_ops][6] rows of
+    (op, stream, block, skip0, skip1, event), as include/sg.h describes."""
+    lib = _load()
+    cnt = ctypes.c_int32(0)
+    lib.sg_sk_blocked_schedule(int(n), int(block), None, 0, ctypes.byref(cnt))
+    out = np.zeros((max(1, cnt.value), 6), dtype=np.int32)
+    _check(lib.sg_sk_blocked_schedule(int(n), int(block), out.ctypes.data, cnt.value, ctypes.byref(cnt)))
+    return out[:cnt.value]
 
 
 def sg_sk_fields_noalloc(J_dev: int, s_dev: int, n: int, n_replicas: int, h_dev: int,

@@ -20,6 +20,51 @@
 #include "sk_internal.cuh"
 
 namespace sg {
+
+// One blocked sweep as the operations SkModel::sweep issues, in host issue order.  B < 128 (a
+// row tile spans two blocks): in-block(b) then the update of every row by block b, on the
+// handle's stream.  B >= 128: in-block(b) on the handle's stream folds block b - 1's flips into
+// its own rows; the tensor-core update of every other row by block b (all rows for the last
+// block, those of block b + 1 left to in-block(b + 1)) runs on the side stream, after in-block(b)
+// (event b & 1 of "in-block done"), and in-block(b + 2), the first to need it, waits for it
+// (event b & 1 of "side done"); the sweep ends by joining both.  The two branches write disjoint
+// rows and the side stream runs its updates in order, so the integers are exact.
+std::vector<SkSchedOp> sk_blocked_schedule(int n, int B, int Np) {
+    std::vector<SkSchedOp> ops;
+    const int ntiles = Np / 128;
+    const int nblocks = (n + B - 1) / B;
+    ops.push_back({kSchedKstar, 0, 0, 0, 0, 0});
+    if (B < 128) {
+        for (int b = 0; b < nblocks; ++b) {
+            ops.push_back({kSchedInblock, 0, b, 0, 0, 0});
+            ops.push_back({kSchedFieldAll, 0, b, 0, 0, 0});
+        }
+        return ops;
+    }
+    bool pending[2] = {false, false};
+    for (int b = 0; b < nblocks; ++b) {
+        const int b0 = b * B;
+        if (pending[b & 1]) {
+            ops.push_back({kSchedWait, 0, b, 0, 0, 2 + (b & 1)});
+            pending[b & 1] = false;
+        }
+        ops.push_back({kSchedInblock, 0, b, 0, 0, 0});
+        int skip0 = 0, skip1 = 0;
+        if (b + 1 < nblocks) {
+            skip0 = (b0 + B) / 128;
+            skip1 = std::min(ntiles, (b0 + 2 * B) / 128);
+        }
+        ops.push_back({kSchedRecord, 0, b, 0, 0, b & 1});
+        ops.push_back({kSchedWait, 1, b, 0, 0, b & 1});
+        ops.push_back({kSchedFieldRows, 1, b, skip0, skip1, 0});
+        ops.push_back({kSchedRecord, 1, b, 0, 0, 2 + (b & 1)});
+        pending[b & 1] = true;
+    }
+    for (int k = 0; k < 2; ++k)
+        if (pending[k]) ops.push_back({kSchedWait, 0, nblocks, 0, 0, 2 + k});
+    return ops;
+}
+
 namespace {
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
@@ -211,49 +256,43 @@ public:
             sweep_many(t_off, 1, st);
             return;
         }
-        launches += sk_kstar_sweep(d_, clock_dev, t_off, st);
-        const int ntiles = Np_ / 128;
-        const int nblocks = (n_ + B_ - 1) / B_;
-        if (B_ < 128) {
-            // a row tile spans two blocks: plain sequence in-block(b) -> full field update
-            for (int b = 0; b < nblocks; ++b) {
-                if (sk_inblock(d_, b * B_, -1, B_, false, st) < 0) fail(SG_ECUDA, "in-block launch failed");
-                ++launches;
-                launches += sk_field_update(d_, mapJ_, mapD_, b * B_, B_, kw_, NT_, 2, st);
-            }
-            return;
+        // the schedule of one blocked sweep (sk_blocked_schedule), issued in order
+        if (sched_B_ != B_) {
+            sched_ = sk_blocked_schedule(n_, B_, Np_);
+            sched_B_ = B_;
         }
-        // Critical path: in-block(b) only.  It folds the previous block's flips into its own
-        // rows; the tensor-core update of all other rows by block b runs on a side stream (a
-        // parallel graph branch) and is joined before in-block(b+2), the first to need it.
-        // Both branches add into disjoint rows or with atomics, so the integers are exact.
-        bool pending[2] = {false, false};
-        for (int b = 0; b < nblocks; ++b) {
-            const int b0 = b * B_;
-            if (pending[b & 1]) {
-                check_cuda(cudaStreamWaitEvent(st, side_done_[b & 1], 0), "cudaStreamWaitEvent");
-                pending[b & 1] = false;
+        for (const SkSchedOp& o : sched_) {
+            cudaStream_t os = o.stream ? side_ : st;
+            const int b0 = o.block * B_;
+            switch (o.op) {
+                case kSchedKstar:
+                    launches += sk_kstar_sweep(d_, clock_dev, t_off, os);
+                    break;
+                case kSchedInblock:
+                {
+                    // B >= 128: the in-block kernel also folds the previous block's flips
+                    const bool fold = B_ >= 128 && o.block > 0;
+                    if (sk_inblock(d_, b0, fold ? b0 - B_ : -1, B_, fold, os) < 0)
+                        fail(SG_ECUDA, "in-block launch failed");
+                }
+                    ++launches;
+                    break;
+                case kSchedFieldAll:
+                    launches += sk_field_update(d_, mapJ_, mapD_, b0, B_, kw_, NT_, 2, os);
+                    break;
+                case kSchedFieldRows:
+                    launches += sk_field_update_rows(d_, mapJ_, mapD_, b0, B_, kw_, NT_, 2, o.skip0,
+                                                     o.skip1, 0, os);
+                    break;
+                case kSchedRecord:
+                    check_cuda(cudaEventRecord(o.event < 2 ? inblock_done_[o.event] : side_done_[o.event - 2], os),
+                               "cudaEventRecord");
+                    break;
+                default:
+                    check_cuda(cudaStreamWaitEvent(os, o.event < 2 ? inblock_done_[o.event] : side_done_[o.event - 2], 0),
+                               "cudaStreamWaitEvent");
             }
-            if (sk_inblock(d_, b0, b > 0 ? b0 - B_ : -1, B_, b > 0, st) < 0)
-                fail(SG_ECUDA, "in-block launch failed");
-            ++launches;
-            // rows of block b+1 are left to in-block(b+1); the last block updates every row.
-            // The rows written here are disjoint from those in-block(b+1) writes concurrently,
-            // and the side stream runs its updates one after another: no atomics needed.
-            int skip0 = 0, skip1 = 0;
-            if (b + 1 < nblocks) {
-                skip0 = (b0 + B_) / 128;
-                skip1 = std::min(ntiles, (b0 + 2 * B_) / 128);
-            }
-            check_cuda(cudaEventRecord(inblock_done_[b & 1], st), "cudaEventRecord");
-            check_cuda(cudaStreamWaitEvent(side_, inblock_done_[b & 1], 0), "cudaStreamWaitEvent");
-            launches += sk_field_update_rows(d_, mapJ_, mapD_, b0, B_, kw_, NT_, 2, skip0, skip1, 0,
-                                             side_);
-            check_cuda(cudaEventRecord(side_done_[b & 1], side_), "cudaEventRecord");
-            pending[b & 1] = true;
         }
-        for (int k = 0; k < 2; ++k)
-            if (pending[k]) check_cuda(cudaStreamWaitEvent(st, side_done_[k], 0), "cudaStreamWaitEvent");
     }
 
     // persistent sweeps: one cooperative launch for all n (fields resident in tensor memory,
@@ -603,6 +642,8 @@ private:
     SkPersistMaps pmaps_{};
     size_t ws_bytes_ = 0;
     cudaStream_t side_ = nullptr;                      // branch for the off-critical-path update
+    std::vector<SkSchedOp> sched_;                     // the blocked sweep's schedule for sched_B_
+    int sched_B_ = 0;
     cudaEvent_t side_done_[2] = {}, inblock_done_[2] = {};
     int n_ = 0, Np_ = 0, B_ = 128, kw_ = 128, NT_ = 128;
     uint64_t seed_ = 0;
@@ -848,3 +889,30 @@ Model* make_sk_model(int n, const int8_t* J, int n_replicas, const double* temps
 }
 
 }  // namespace sg
+
+// the blocked sweep's schedule, for host-side checks (no device needed)
+extern "C" int sg_sk_blocked_schedule(int32_t n, int32_t block, int32_t* ops, int32_t cap,
+                                      int32_t* n_ops) {
+    if (!n_ops || (cap > 0 && !ops)) {
+        sg::record_error("null argument");
+        return SG_EINVAL;
+    }
+    if (n < 2 || n > 32768 || !(block == 64 || block == 128 || block == 256 || block == 512)) {
+        sg::record_error("need 2 <= n <= 32768 and block 64, 128, 256 or 512");
+        return SG_EINVAL;
+    }
+    const int unit = std::max(128, (int)block);
+    const int Np = (n + unit - 1) / unit * unit;
+    const std::vector<sg::SkSchedOp> sched = sg::sk_blocked_schedule(n, block, Np);
+    *n_ops = (int32_t)sched.size();
+    if ((int64_t)sched.size() > (int64_t)cap) {
+        sg::record_error("ops capacity " + std::to_string(cap) + " < " + std::to_string(sched.size()));
+        return SG_EINVAL;
+    }
+    for (size_t i = 0; i < sched.size(); ++i) {
+        const sg::SkSchedOp& o = sched[i];
+        const int32_t v[6] = {o.op, o.stream, o.block, o.skip0, o.skip1, o.event};
+        for (int k = 0; k < 6; ++k) ops[6 * i + k] = v[k];
+    }
+    return SG_OK;
+}

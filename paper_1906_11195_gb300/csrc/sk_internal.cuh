@@ -116,6 +116,15 @@ __device__ __forceinline__ int sk_kstar(uint32_t r32, const uint32_t* __restrict
 
 int sk_init(const SkDev& d, cudaStream_t st);
 int sk_kstar_sweep(const SkDev& d, const uint32_t* clock, uint32_t t_off, cudaStream_t st);
+
+// One operation of a blocked sweep's schedule (sk_blocked_schedule in sg_sk.cu): stream 0 is the
+// handle's stream, 1 the side stream; events 0, 1 are "in-block done" (block parity), 2, 3
+// "side done"; a field update of rows leaves the row tiles [skip0, skip1) out.
+enum { kSchedKstar = 0, kSchedInblock = 1, kSchedFieldAll = 2, kSchedFieldRows = 3,
+       kSchedRecord = 4, kSchedWait = 5 };
+struct SkSchedOp {
+    int32_t op, stream, block, skip0, skip1, event;
+};
 // the same into even[] or odd[] by the parity of the sweep index
 int sk_kstar_sweep_into(const SkDev& d, const uint32_t* clock, uint32_t t_off, int32_t* even,
                         int32_t* odd, cudaStream_t st);

@@ -1,16 +1,18 @@
 """Race check of the blocked SK sweep's launch schedule (`SkModel::sweep` in
 paper_1906_11195_gb300/csrc/sg_sk.cu), on the CPU.
 
-The schedule is rebuilt here from the host code's rules: per sweep, the K* table kernel and then,
-for each block b, an in-block kernel on the handle's stream (folding block b-1's flips into its
-own rows) and the field update of block b on a side stream, which waits for in-block(b) through
-an event and updates every 128-row tile except those of block b+1 (the last block updates all);
-in-block(b+2) waits for field(b) through one of two events, and the sweep ends by joining both.
-Happens-before follows CUDA's rules: stream order, and a stream wait on an event orders after the
-event's latest record issued before the wait.  Every pair of kernels touching the same data (a
-row tile of the fields H, a block's spin changes D, spins and flip masks, the K* table), at least
-one of them writing, must be ordered — over consecutive sweeps, for every block size the blocked
-path takes and for sizes that leave a ragged last block.
+The schedule under test is the library's own: `sg_sk_blocked_schedule` returns the operations
+`SkModel::sweep` issues (it runs them from the same list), with their streams, events and row
+skip ranges.  Each kernel's data is fixed by what the kernel does: the K* table kernel writes the
+table; in-block(b) reads the table, its rows of H and the spins and flips of blocks b - 1 and b,
+and writes its rows of H, block b's spins, flips and spin changes D; the field update of block b
+reads D_b and writes the rows it updates.  Happens-before follows CUDA's rules: stream order,
+and a stream wait on an event orders after the event's latest record issued before the wait.
+Every pair of kernels touching the same data (a row tile of the fields H, a block's spin changes
+D, spins and flip masks, the K* table), at least one of them writing, must be ordered, over
+consecutive sweeps, for every block size and for sizes that leave a ragged last block.  A
+restatement of the schedule from the host code's rules (`build_schedule`) must agree with the
+library's and carries the planted mistakes.
 """
 import itertools
 
@@ -93,12 +95,70 @@ def races(ops):
     return found
 
 
-@pytest.mark.parametrize("B", [128, 256, 512])
+TILE_OPS = {0: "kstar", 1: "inblock", 2: "field_all", 3: "field_rows", 4: "record", 5: "wait"}
+
+
+@pytest.fixture(scope="module")
+def sg():
+    from paper_1906_11195_gb300 import _build
+    _build.build()
+    import paper_1906_11195_gb300 as m
+    return m
+
+
+def recorded_schedule(sg, n, B, sweeps):
+    """The library's schedule of `sweeps` consecutive sweeps, as ops with their data."""
+    unit = max(128, B)
+    Np = -(-n // unit) * unit
+    ntiles = Np // TILE
+    ops = []
+    streams = ("main", "side")
+    events = (("inblock_done", 0), ("inblock_done", 1), ("side_done", 0), ("side_done", 1))
+
+    def tiles_of_block(b):
+        lo, hi = b * B, b * B + B
+        return set(range(lo // TILE, min(ntiles, -(-hi // TILE))))
+
+    for _ in range(sweeps):
+        for op, st, b, s0, s1, ev in sg.sg_sk_blocked_schedule(n, B).tolist():
+            stream = streams[st]
+            kind = TILE_OPS[op]
+            if kind == "kstar":
+                ops.append({"stream": stream, "kind": "kstar", "reads": set(), "writes": {("kst", "all")}})
+            elif kind == "inblock":
+                rows = {("H", t) for t in tiles_of_block(b)}
+                reads = {("kst", "all"), ("S", b)} | rows
+                if b > 0:
+                    reads |= {("S", b - 1), ("flips", b - 1)}
+                ops.append({"stream": stream, "kind": f"inblock{b}", "reads": reads,
+                            "writes": rows | {("S", b), ("flips", b), ("D", b)}})
+            elif kind in ("field_all", "field_rows"):
+                keep = [t for t in range(ntiles) if kind == "field_all" or not (s0 <= t < s1)]
+                rows = {("H", t) for t in keep}
+                ops.append({"stream": stream, "kind": f"field{b}", "reads": {("D", b)} | rows,
+                            "writes": rows})
+            elif kind == "record":
+                ops.append({"stream": stream, "record": events[ev]})
+            else:
+                ops.append({"stream": stream, "wait": events[ev]})
+    return ops
+
+
+@pytest.mark.parametrize("B", [64, 128, 256, 512])
 @pytest.mark.parametrize("n", [1024, 1000, 2176, 4096])
-def test_blocked_sweep_schedule_has_no_race(n, B):
+def test_blocked_sweep_schedule_has_no_race(sg, n, B):
     if n < B:
         pytest.skip("fewer spins than one block")
-    assert races(build_schedule(n, B, sweeps=2)) == []
+    assert races(recorded_schedule(sg, n, B, sweeps=2)) == []
+
+
+@pytest.mark.parametrize("B", [128, 256, 512])
+@pytest.mark.parametrize("n", [1024, 1000, 2176])
+def test_restated_schedule_is_the_librarys(sg, n, B):
+    def shape(ops):
+        return [(op["stream"], op.get("kind"), op.get("record"), op.get("wait"),
+                 sorted(op.get("writes", ()))) for op in ops]
+    assert shape(recorded_schedule(sg, n, B, sweeps=2)) == shape(build_schedule(n, B, sweeps=2))
 
 
 def test_race_check_catches_a_wrong_skip_range():
