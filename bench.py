@@ -146,7 +146,8 @@ def recorded_traffic():
 
 class _Nvml:
     """The few NVML queries the clock record needs (SM clock, its maximum, the active clock
-    event reasons), called through ctypes on the driver's libnvidia-ml.  Reads only."""
+    event reasons), called through ctypes on NVML (libnvidia-ml.so.1, part of the GPU's display
+    driver install).  Reads only."""
     REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
                0x4: "sw_power_cap", 0x80: "hw_power_brake_slowdown"}
 
