@@ -55,9 +55,9 @@ constexpr int kSkPersistSlots = 8;  // spin-change ring slots of the persistent 
 
 // Persistent sweeps (sk_persist.cu): one cooperative launch runs n_sweeps sweeps; field CTAs
 // hold row tiles of H in tensor memory, chain CTAs run the sequential decisions (block = 128
-// spins).  Blocks of 32 * (2W + 1) threads: a chain CTA uses all (W replica warps, W fold warps
-// and a staging warp); a field CTA uses warps 0..3 (tensor-memory epilogue, thread 0 issues the
-// MMAs) and warp W (operand loads).
+// spins).  Blocks of 32 * (2W + 2) threads: a chain CTA uses all (W replica warps, W fold warps,
+// a staging warp and a release warp); a field CTA uses warps 0..3 (tensor-memory epilogue,
+// thread 0 issues the MMAs) and warp W (operand loads).
 constexpr int kSkPersistMaxSweeps = 64;  // sweeps of one launch (the K* buffer holds them)
 struct SkPersistArgs {
     uint8_t* Dring;   // [Q][R][128] e4m3 spin changes 2 D = s' - s of the last Q blocks

@@ -81,6 +81,24 @@ __device__ bool wait_at_least(const uint32_t* p, uint32_t target, const int* err
     }
 }
 
+// the same on a counter in this CTA's shared memory
+__device__ bool wait_smem_at_least(const uint32_t* p, uint32_t target, const int* err, bool nowait,
+                                   const volatile int* abort_flag) {
+    auto load = [&] {
+        uint32_t v;
+        asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
+        return v;
+    };
+    if (load() >= target) return true;
+    if (nowait) return false;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (load() >= target) return true;
+        if ((it & 63) == 0 && (err_raised(err) || *abort_flag || global_ns() - t0 > kPersistWaitNs))
+            return false;
+    }
+}
+
 // mbarrier wait bounded by the global timer that also gives up when an error is flagged; it
 // spins on try_wait (no suspend hint: the waits sit on the sequential chain's critical path)
 __device__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t phase, const int* err, bool nowait,
@@ -378,7 +396,8 @@ __device__ void persist_field_cta(const CUtensorMap* mapJ, const CUtensorMap* ma
 
 // ------------------------------------------------------------------------------------------
 // chain CTA: warps 0..W-1 are the replicas' chains, warps W..2W-1 their fold warps, warp 2W
-// (lane 0) stages the blocks.  For block k the fold warp of replica w adds to the staged fields
+// (lane 0) stages the blocks, warp 2W + 1 (lane 0) tells the field CTAs (D_count) when every
+// replica warp has written a block's spin changes.  For block k the fold warp of replica w adds to the staged fields
 // the flips of blocks k - L .. k - 2 (complete while the chain runs block k - 1) and hands the
 // result over in shared memory; the chain warp adds block k - 1's flips itself (16 popcounts
 // per lane) and takes the decisions.  So only one block's fold sits on the chain.
@@ -403,7 +422,8 @@ __device__ __forceinline__ void fold_block(int (&h)[4], const uint32_t* Jp, cons
 
 template <int W, int L>
 __device__ void persist_chain_cta(const SkDev& d, const SkPersistArgs& a, const SkPersistMaps& m,
-                                  uint8_t* smem, uint64_t* bars, volatile int* abort_flag) {
+                                  uint8_t* smem, uint64_t* bars, uint32_t* done_cnt,
+                                  volatile int* abort_flag) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int c = blockIdx.x - a.nG;
     const int r0 = c * W;
@@ -431,6 +451,7 @@ __device__ void persist_chain_cta(const SkDev& d, const SkPersistArgs& a, const 
             mbar_init(&emptyc[s], 2 * W);
         }
         for (int i = 0; i < 4 * W; ++i) mbar_init(&cdone[i], 1);  // cdone and hrdy
+        for (int w = 0; w < W; ++w) done_cnt[w] = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp < W) {
@@ -492,7 +513,6 @@ __device__ void persist_chain_cta(const SkDev& d, const SkPersistArgs& a, const 
                     ok = false;
                     break;
                 }
-                red_release_add(&D_count[k % Q], 1u);
                 if (k + kChainStages < nk) ok = prefetch(k + kChainStages);
             }
             if (!ok) {
@@ -501,6 +521,23 @@ __device__ void persist_chain_cta(const SkDev& d, const SkPersistArgs& a, const 
                 for (int s = 0; s < kChainStages; ++s)
                     if (last_fill[s] >= 0)
                         mbar_wait_timed(&fullc[s], (uint32_t)(last_fill[s] / kChainStages) & 1u, kPersistWaitNs);
+            }
+        }
+    } else if (warp == 2 * W + 1) {
+        // ---------------- release warp: D_count of block k once every replica wrote D_k ------
+        // (apart from the staging warp, whose next stage does not wait for this gpu-scope
+        // release, about a microsecond)
+        if (lane == 0) {
+            for (int k = 0; k < nk; ++k) {
+                bool ok = true;
+                for (int w = 0; w < W && ok; ++w)
+                    ok = wait_smem_at_least(&done_cnt[w], (uint32_t)(k + 1), d.err, nowait, abort_flag);
+                if (!ok) {
+                    atomicOr(d.err, 65536);
+                    *abort_flag = 1;
+                    break;
+                }
+                red_release_add(&D_count[k % Q], 1u);
             }
         }
     } else if (warp >= W) {
@@ -626,6 +663,9 @@ __device__ void persist_chain_cta(const SkDev& d, const SkPersistArgs& a, const 
             fence_proxy_async_global();
             __syncwarp();
             if (lane == 0) {
+                asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_addr(&done_cnt[warp])),
+                             "r"((uint32_t)(k + 1))
+                             : "memory");
                 mbar_arrive(&cdone[warp * 2 + (k & 1)]);
                 mbar_arrive(&emptyc[s]);
             }
@@ -639,20 +679,21 @@ __device__ void persist_chain_cta(const SkDev& d, const SkPersistArgs& a, const 
 }
 
 template <int W, int L>
-__global__ void __launch_bounds__(32 * (2 * W + 1), 1)
+__global__ void __launch_bounds__(32 * (2 * W + 2), 1)
     k_sk_persist(const __grid_constant__ CUtensorMap mapJ, const __grid_constant__ CUtensorMap mapD,
                  const __grid_constant__ SkPersistMaps maps, SkDev d, SkPersistArgs a) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t bars[2 * kChainStages + 4 * 8];  // chain CTA: W <= 8
     __shared__ uint32_t tslot;
+    __shared__ uint32_t done_cnt[8];  // chain CTA: blocks each replica warp has written D for
     __shared__ int abort_flag;
     if (threadIdx.x == 0) abort_flag = 0;
     __syncthreads();
     if ((int)blockIdx.x < a.nG)
         persist_field_cta<W>(&mapJ, &mapD, maps, d, a, smem, bars, &tslot, &abort_flag);
     else
-        persist_chain_cta<W, L>(d, a, maps, smem, bars, &abort_flag);
+        persist_chain_cta<W, L>(d, a, maps, smem, bars, done_cnt, &abort_flag);
 }
 
 size_t sk_persist_smem_bytes(const SkDev& d, const SkPersistArgs& a) {
@@ -693,7 +734,7 @@ int sk_persist_fits(const SkDev& d, const SkPersistArgs& a, int num_sms) {
         return 0;
     }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * (2 * a.W + 1), smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * (2 * a.W + 2), smem) !=
         cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -710,7 +751,7 @@ int sk_persist_sweeps(const SkDev& d, const SkPersistArgs& a, const CUtensorMap&
         return -1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(a.nG + a.nC));
-    cfg.blockDim = dim3((unsigned)(32 * (2 * a.W + 1)));
+    cfg.blockDim = dim3((unsigned)(32 * (2 * a.W + 2)));
     cfg.dynamicSmemBytes = sk_persist_smem_bytes(d, a);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];

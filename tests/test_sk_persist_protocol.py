@@ -1,19 +1,21 @@
 """The persistent SK sweep's cross-CTA protocol, modelled step by step on the CPU.
 
-The persistent launch (one per sweep) has three kinds of actors: the helper warp of every
-chain CTA (stages block b two ahead, publishes D_count once its replica warps are done with a
-block), the replica warps of every chain CTA (wait for the staged block, fold the flips of the
-blocks not yet in the staged fields, decide, write the ring slot b mod Q), and the issuer of
-every field CTA (waits for D_count[k], reads the slot, releases D_free, applies block k to its
-tiles, publishes a tile t once block t - L - 1 is applied).  The model runs these actors in
+The persistent launch has four kinds of actors: the staging warp of every chain CTA (stages
+block k + S_C once its replica and fold warps are done with block k), the release warp of every
+chain CTA (adds to D_count[k] once its replica warps have written block k, in block order), the
+replica warps of every chain CTA (wait for the staged block, fold the flips of the blocks not
+yet in the staged fields, decide, write the ring slot k mod Q), and the issuer of every field CTA
+(waits for D_count[k], reads the slot, releases D_free, applies block k to its tiles, publishes
+a tile t once block t - L - 1 is applied).  The model runs these actors in
 random interleavings with the kernel's waits as blocking conditions and checks:
   * the launch always finishes (no wait that nothing will satisfy),
   * the fields a chain block starts from, plus the blocks it folds in itself, are exactly the
     blocks before it, each once (the sequential order of the sweep),
   * a field CTA reads every ring slot before it is overwritten, and reads the block it expects.
 Several sweeps run in one launch (blocks k = s nb + b; the fold window and the publishes run
-across sweep boundaries).  Planted mistakes (no lookahead with a two-deep staging ring, a fold
-window one block short, no D_free wait) are each caught.
+across sweep boundaries).  Planted mistakes (a fold window one block short, no D_free wait) are
+each caught, and so are the deadlocks of the earlier form in which the staging warp itself
+released D_count (no lookahead; a ring shallower than the staging).
 """
 import random
 
@@ -21,7 +23,7 @@ import pytest
 
 
 def run_protocol(nb, nC, nG, TPC, L, Q, S_C=2, n_sweeps=1, seed=0, fold_short=False,
-                 skip_free=False, max_steps=400000):
+                 skip_free=False, release_in_staging=False, max_steps=400000):
     """One launch of n_sweeps sweeps; blocks are numbered k = s nb + b over the launch."""
     rng = random.Random(seed)
     nk = n_sweeps * nb
@@ -36,13 +38,17 @@ def run_protocol(nb, nC, nG, TPC, L, Q, S_C=2, n_sweeps=1, seed=0, fold_short=Fa
     errors = []
 
     # chain CTA state: the staging warp runs its operations in program order, as the kernel
-    # does: stage blocks 0 .. S_C - 1, then for every block k: publish D(k), stage k + S_C
+    # does: stage blocks 0 .. S_C - 1, then for every block k: wait until block k is done
+    # ("free"), stage k + S_C; the release warp publishes D(k) in block order once block k is done
+    # (release_in_staging: the earlier form, the staging warp itself publishing D(k) in its
+    # program order, after block k is done and before it stages k + S_C)
     ops = [("stage", k) for k in range(min(S_C, nk))]
     for k in range(nk):
-        ops.append(("publish", k))
+        ops.append(("publish" if release_in_staging else "free", k))
         if k + S_C < nk:
             ops.append(("stage", k + S_C))
     helper_pc = [0] * nC
+    released = [0] * nC         # next block each release warp publishes
     staged = [dict() for _ in range(nC)]   # block -> fields (set of blocks included)
     chain_k = [0] * nC          # next block the replica warps process
     done_chain = [set() for _ in range(nC)]
@@ -53,7 +59,7 @@ def run_protocol(nb, nC, nG, TPC, L, Q, S_C=2, n_sweeps=1, seed=0, fold_short=Fa
         if helper_pc[c] >= len(ops):
             return False
         op, k = ops[helper_pc[c]]
-        if op == "publish":
+        if op in ("free", "publish"):
             return k in done_chain[c]
         b = k % nb
         if k >= Q and not skip_free and D_free[k % Q] < (k // Q) * nG:
@@ -70,6 +76,8 @@ def run_protocol(nb, nC, nG, TPC, L, Q, S_C=2, n_sweeps=1, seed=0, fold_short=Fa
         for c in range(nC):
             if helper_ready(c):
                 actions.append(("helper", c))
+            if not release_in_staging and released[c] < nk and released[c] in done_chain[c]:
+                actions.append(("release", c))
             ck = chain_k[c]
             if ck < nk and ck in staged[c]:
                 actions.append(("chain", c))
@@ -82,11 +90,14 @@ def run_protocol(nb, nC, nG, TPC, L, Q, S_C=2, n_sweeps=1, seed=0, fold_short=Fa
         kind, x = rng.choice(actions)
         if kind == "helper":
             op, k = ops[helper_pc[x]]
-            if op == "publish":
-                D_count[k % Q] += 1
-            else:
+            if op == "stage":
                 staged[x][k] = set() if k <= L else set(published[k % nb])
+            elif op == "publish":
+                D_count[k % Q] += 1
             helper_pc[x] += 1
+        elif kind == "release":
+            D_count[released[x] % Q] += 1
+            released[x] += 1
         elif kind == "chain":
             c, k = x, chain_k[x]
             fields = staged[c].pop(k)
@@ -141,9 +152,14 @@ def test_protocol_finishes_and_keeps_the_sequential_order(cfg):
         assert finished, f"deadlock with seed {seed}"
 
 
-def test_no_lookahead_with_two_staged_blocks_deadlocks():
-    finished, errors = run_protocol(8, 4, 4, 2, 0, 8, seed=1)
+def test_no_lookahead_deadlocks_when_the_staging_warp_releases():
+    """The earlier form (the staging warp publishing D(k) itself, in program order): staging
+    block k + 2 waits for fields that need block k + 1 applied, whose release comes after that
+    staging.  The release warp breaks the cycle."""
+    finished, _ = run_protocol(8, 4, 4, 2, 0, 8, seed=1, release_in_staging=True)
     assert not finished
+    finished, errors = run_protocol(8, 4, 4, 2, 0, 8, seed=1)
+    assert finished and not errors
 
 
 def test_fold_window_one_block_short_is_caught():
@@ -159,10 +175,12 @@ def test_missing_ring_release_wait_is_caught():
     assert caught
 
 
-def test_ring_smaller_than_the_staging_depth_deadlocks():
-    """Staging block k + S_C waits for ring slot k + S_C - Q to be read, but that block's spin
-    changes are published only after the staging: Q >= S_C is required (the kernel has Q = 8,
-    three staged blocks)."""
-    finished, _ = run_protocol(5, 8, 3, 2, 2, 2, S_C=3, n_sweeps=3, seed=0)
+def test_ring_smaller_than_the_staging_depth_deadlocks_when_the_staging_warp_releases():
+    """Earlier form: staging block k + S_C waits for ring slot k + S_C - Q to be read, but that
+    block's spin changes were published only after the staging; with the release warp the
+    launch finishes (the kernel keeps Q = 8 >= three staged blocks all the same)."""
+    finished, _ = run_protocol(5, 8, 3, 2, 2, 2, S_C=3, n_sweeps=3, seed=0, release_in_staging=True)
     assert not finished
-
+    for seed in range(6):
+        finished, errors = run_protocol(5, 8, 3, 2, 2, 2, S_C=3, n_sweeps=3, seed=seed)
+        assert finished and not errors
