@@ -237,3 +237,19 @@ def test_transfer_bytes_start_at_zero(lib):
     h = sg.sg_create_vb([g], 64, 2, sg.SG_VB_PACKED, [0], [0, 1])
     assert sg.sg_transfer_bytes(h) == (0, 0)
     sg.sg_destroy(h)
+
+
+def test_blocked_sk_schedule_is_validated(lib):
+    cnt = ctypes.c_int32(0)
+    for n, block in ((1, 128), (40000, 128), (1024, 100), (1024, 0)):
+        assert lib.sg_sk_blocked_schedule(n, block, None, 0, ctypes.byref(cnt)) == sg.SG_EINVAL
+    # capacity query, then a buffer one operation short
+    assert lib.sg_sk_blocked_schedule(1024, 256, None, 0, ctypes.byref(cnt)) == sg.SG_EINVAL
+    need = cnt.value
+    assert need == len(sg.sg_sk_blocked_schedule(1024, 256)) > 0
+    buf = (ctypes.c_int32 * (6 * need))()
+    assert lib.sg_sk_blocked_schedule(1024, 256, buf, need - 1, ctypes.byref(cnt)) == sg.SG_EINVAL
+    assert lib.sg_sk_blocked_schedule(1024, 256, buf, need, ctypes.byref(cnt)) == sg.SG_OK
+    ops = np.frombuffer(buf, dtype=np.int32).reshape(need, 6)
+    assert ops[0, 0] == 0 and set(ops[:, 0]) <= {0, 1, 2, 3, 4, 5}
+    assert (ops[ops[:, 0] == 1, 2] == np.arange(4)).all()  # in-block kernels of blocks 0..3 in order
