@@ -227,6 +227,13 @@ int sg_get_spins(sg_handle h, void *host_dst, size_t bytes);
  * min(1, exp(-dE/T)) (Methods) as integer thresholds on a 32-bit random number. */
 int sg_get_thresholds(sg_handle h, uint32_t *dst, size_t len);
 
+/* VB: the colour class of every vertex of graph `graph` of the handle (int32[n], original
+ * vertex labels) and the number of classes; a sweep updates class 0, 1, ... in turn.  Available
+ * from creation (no device needed).  SG_EINVAL for an SK handle, a bad graph index or len < n.
+ * Defines: the update order, one independent set at a time (the bipartite half-updates of SI
+ * section 3, generalised by a greedy colouring and one recolouring pass). */
+int sg_vb_colouring(sg_handle h, int32_t graph, int32_t *colour, size_t len, int32_t *n_colours);
+
 /* Checkpoint: the full dynamic state (tau, spins, snapshots, counts) as an opaque host blob.
  * sg_state_bytes gives its size; sg_load_state restores it into an attached handle created
  * from the same instance.  Library service (long runs in pieces, as the paper's campaign of

@@ -37,7 +37,7 @@ EXPORTED = [
     "sg_sweep", "sg_time", "sg_synchronize", "sg_result_shape", "sg_read_results", "sg_measure",
     "sg_get_spins", "sg_get_thresholds", "sg_state_bytes", "sg_save_state", "sg_load_state",
     "sg_destroy", "sg_launch_count", "sg_sk_fields_noalloc", "sg_set_windows", "sg_read_windows",
-    "sg_set_schedule", "sg_transfer_bytes", "sg_sk_blocked_schedule",
+    "sg_set_schedule", "sg_transfer_bytes", "sg_sk_blocked_schedule", "sg_vb_colouring",
 ]
 
 
@@ -91,6 +91,7 @@ def _load():
                 "sg_measure": (ctypes.c_int, [H, P, sz, P, sz, P, sz]),
                 "sg_get_spins": (ctypes.c_int, [H, P, sz]),
                 "sg_get_thresholds": (ctypes.c_int, [H, P, sz]),
+                "sg_vb_colouring": (ctypes.c_int, [H, i32, P, sz, P]),
                 "sg_state_bytes": (ctypes.c_int, [H, P]),
                 "sg_save_state": (ctypes.c_int, [H, P, sz]),
                 "sg_load_state": (ctypes.c_int, [H, P, sz]),
@@ -263,6 +264,14 @@ def sg_get_thresholds(h, n: int):
     out = np.zeros(n, dtype=np.uint32)
     _check(_load().sg_get_thresholds(h, _p(out), out.size))
     return out
+
+
+def sg_vb_colouring(h, graph: int, n: int):
+    """(colour int32[n] of graph `graph`, number of colour classes) of a VB handle."""
+    out = np.zeros(n, dtype=np.int32)
+    nc = ctypes.c_int32(0)
+    _check(_load().sg_vb_colouring(h, int(graph), _p(out), out.size, ctypes.byref(nc)))
+    return out, nc.value
 
 
 def sg_save_state(h) -> bytes:

@@ -448,6 +448,18 @@ int sg_get_thresholds(sg_handle h, uint32_t* dst, size_t len) {
     });
 }
 
+int sg_vb_colouring(sg_handle h, int32_t graph, int32_t* colour, size_t len, int32_t* n_colours) {
+    return guarded([&] {
+        if (!h || !colour || !n_colours) sg::fail(SG_EINVAL, "null argument");
+        int nc = 0;
+        const std::vector<int32_t> c = h->model->colouring(graph, &nc);
+        if (c.empty()) sg::fail(SG_EINVAL, "the handle has no colouring (not a VB handle)");
+        check_len(len, c.size(), "colour");
+        std::copy(c.begin(), c.end(), colour);
+        *n_colours = nc;
+    });
+}
+
 // checkpoint blob: magic, version, tau, next_tw, next_tm, region sizes, region bytes
 static const uint64_t kStateMagic = 0x5347535441544531ull;  // "SGSTATE1"
 

@@ -107,6 +107,13 @@ public:
     virtual size_t spins_bytes() const = 0;
     virtual void get_spins(void* dst, cudaStream_t st) = 0;
     virtual std::vector<uint32_t> thresholds() const = 0;
+    // VB: the colour class of every vertex of graph b (original labels) and the number of
+    // classes; empty for a model without a colouring
+    virtual std::vector<int32_t> colouring(int b, int* n_colours) const {
+        (void)b;
+        *n_colours = 0;
+        return {};
+    }
     // device regions that hold the dynamic state (checkpoint/restore)
     virtual std::vector<std::pair<void*, size_t>> state_regions() = 0;
     // device-side error word (0 = fine), read after synchronisation

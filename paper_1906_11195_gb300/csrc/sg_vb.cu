@@ -612,6 +612,12 @@ public:
 
     std::vector<uint32_t> thresholds() const override { return thr_; }
 
+    std::vector<int32_t> colouring(int b, int* n_colours) const override {
+        if (b < 0 || b >= n_inst) fail(SG_EINVAL, "graph index out of range");
+        *n_colours = graphs_[b].n_colours;
+        return graphs_[b].colour;
+    }
+
     int device_status(cudaStream_t st) override {
         int v = 0;
         if (kernel_ == SG_VB_PACKED && pk_.err) {

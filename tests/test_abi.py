@@ -253,3 +253,36 @@ def test_blocked_sk_schedule_is_validated(lib):
     ops = np.frombuffer(buf, dtype=np.int32).reshape(need, 6)
     assert ops[0, 0] == 0 and set(ops[:, 0]) <= {0, 1, 2, 3, 4, 5}
     assert (ops[ops[:, 0] == 1, 2] == np.arange(4)).all()  # in-block kernels of blocks 0..3 in order
+
+
+@pytest.mark.parametrize("n,c,seed", [(37, 3.0, 1), (5000, 4.0, 2), (200000, 4.0, 7)])
+def test_library_colouring_equals_the_oracles(lib, n, c, seed):
+    """The update order, checked on the host: the library's own greedy colouring and recolouring
+    pass give every vertex the oracle's class (both written separately), for each graph of a
+    batch; the bipartite regular graph keeps its two halves."""
+    import oracle
+    oracle.build()
+    graphs = []
+    for k, (nn, cc, sd) in enumerate([(n, c, seed), (n // 2 + 3, c, seed + 1)]):
+        rp, col, eid = sg_inputs.poisson_graph(nn, cc, sd)
+        jb = sg_inputs.vb_lane_couplings(eid, eid.max() + 1, sd)
+        graphs.append(dict(row_ptr=rp, col=col, jbits=jb, seed=k, temps=[1.0, 1.0]))
+    h = sg.sg_create_vb(graphs, 64, 2, sg.SG_VB_PACKED, [0], [1])
+    try:
+        for b, g in enumerate(graphs):
+            got, nc = sg.sg_vb_colouring(h, b, len(g["row_ptr"]) - 1)
+            want, wnc = oracle.vb_colouring(g["row_ptr"], g["col"])
+            assert nc == wnc and np.array_equal(got, want)
+        with pytest.raises(sg.SGError):
+            sg.sg_vb_colouring(h, 2, 10)
+    finally:
+        sg.sg_destroy(h)
+    rp, col, eid = sg_inputs.random_regular_graph(1000, 4, 3, bipartite=True)
+    jb = sg_inputs.vb_lane_couplings(eid, eid.max() + 1, 3)
+    h = sg.sg_create_vb([dict(row_ptr=rp, col=col, jbits=jb, seed=1, temps=[1.0, 1.0])], 64, 2,
+                        sg.SG_VB_PACKED, [0], [1])
+    try:
+        got, nc = sg.sg_vb_colouring(h, 0, 1000)
+        assert nc == 2 and np.array_equal(got, (np.arange(1000) < 500).astype(np.int32))
+    finally:
+        sg.sg_destroy(h)
