@@ -286,3 +286,34 @@ def test_library_colouring_equals_the_oracles(lib, n, c, seed):
         assert nc == 2 and np.array_equal(got, (np.arange(1000) < 500).astype(np.int32))
     finally:
         sg.sg_destroy(h)
+
+
+def test_library_thresholds_equal_the_oracles_on_the_host(lib):
+    """The Metropolis threshold tables (integer thresholds floor(2^32 exp(-dE/T)) in double
+    precision), computed by the library at creation, equal the oracle's: VB per replica for every
+    degree up to the limit, SK per replica for every k, at finite, zero and infinite T."""
+    import math
+
+    import oracle
+    oracle.build()
+    rp, col, eid = sg_inputs.poisson_graph(300, 4.0, 9)
+    jb = sg_inputs.vb_lane_couplings(eid, eid.max() + 1, 9)
+    temps = [1.0, 0.6, 0.0, math.inf]
+    h = sg.sg_create_vb([dict(row_ptr=rp, col=col, jbits=jb, seed=1, temps=temps)], 64, 4,
+                        sg.SG_VB_PACKED, [0], [1])
+    try:
+        thr = sg.sg_get_thresholds(h, 4 * 64).reshape(4, 64)
+        for r, T in enumerate(temps):
+            assert np.array_equal(thr[r], oracle.vb_thresholds(T, 63))
+    finally:
+        sg.sg_destroy(h)
+    n = 300
+    J = sg_inputs.sk_couplings(n, 4)
+    stemps = [0.4] * 8 + [0.6] * 8
+    h = sg.sg_create_sk(J, 16, stemps, 1, sg.SG_SK_BLOCKED, 128, [0], [1])
+    try:
+        thr = sg.sg_get_thresholds(h, 16 * n).reshape(16, n)
+        assert np.array_equal(thr[0], oracle.sk_thresholds(0.4, n))
+        assert np.array_equal(thr[15], oracle.sk_thresholds(0.6, n))
+    finally:
+        sg.sg_destroy(h)
